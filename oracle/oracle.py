@@ -1,0 +1,236 @@
+"""ctypes front end of the plain FP64 CPU oracle (``tpc_oracle.c``).
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` import this module.  It shares no code with the
+CUDA tracker in the package.
+
+The C file follows the per-sector cellular-automaton track finder and Kalman
+track fit named in the paper's Abstract and Sect. 4 (the steps themselves are
+readings; each C function states its rule).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tpc_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+TIE_CHI2_CUT, TIE_CHI2_PAIR, TIE_SIN, TIE_EDGE = 1, 2, 4, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (binary64, no contraction of a*b+c)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_track_event.restype = C.c_int
+        _lib.orc_transport_packed.restype = C.c_int
+        _lib.orc_update_packed.restype = C.c_double
+        _lib.orc_fit_fixed.restype = C.c_int
+    return _lib
+
+
+class OrcConfig(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "half_angle", "z_max", "bz", "sigma_y", "sigma_z", "chi2_hit", "sin_max", "edge_margin",
+        "seed_var_s", "seed_var_t", "seed_var_q", "tie_chi2", "tie_sin", "tie_edge")] + \
+        [(n, C.c_float) for n in ("slope_win_y", "slope_win_z", "d_max", "pad0")] + \
+        [(n, C.c_int32) for n in ("n_rows", "n_sectors_phi", "split_z", "max_gap", "min_chain",
+                                  "min_tracklet_hits", "min_track_hits", "pad1")]
+
+
+_P = C.c_void_p
+
+
+class OrcResult(C.Structure):
+    _fields_ = [("up", _P), ("dn", _P), ("up64", _P), ("dn64", _P), ("up_c", _P), ("dn_c", _P),
+                ("cap_tracklets", C.c_int64),
+                ("t_start", _P), ("t_sector", _P), ("t_chain_len", _P), ("t_valid", _P),
+                ("t_nhits", _P), ("t_first_row", _P), ("t_last_row", _P), ("t_flags", _P),
+                ("t_ndf", _P), ("t_x", _P), ("t_p", _P), ("t_C", _P), ("t_chi2", _P),
+                ("t_rowhit", _P), ("weight", _P), ("cap_tracks", C.c_int64),
+                ("k_tracklet", _P), ("k_sector", _P), ("k_ndf", _P), ("k_x", _P), ("k_p", _P),
+                ("k_C", _P), ("k_chi2", _P), ("k_hit_off", _P), ("k_hit_cid", _P),
+                ("n_tracklets", C.c_int64), ("n_tracks", C.c_int64), ("n_track_hits", C.c_int64),
+                ("n_links", C.c_int64), ("n_link_flips64", C.c_int64), ("n_starts", C.c_int64)]
+
+
+@dataclass
+class Params:
+    """Tracker parameters (the same defaults as the GPU library's)."""
+    sigma_y: float = 0.1
+    sigma_z: float = 0.1
+    slope_win_y: float = 2.0
+    slope_win_z: float = 2.0
+    d_max: float = 0.36
+    chi2_hit: float = 16.0
+    max_gap: int = 5
+    min_chain: int = 3
+    min_tracklet_hits: int = 10
+    min_track_hits: int = 10
+    sin_max: float = 0.99
+    edge_margin: float = 2.0
+    seed_var_s: float = 1.0
+    seed_var_t: float = 1.0
+    seed_var_q: float = 100.0
+    tie_chi2: float = 0.05
+    tie_sin: float = 1e-4
+    tie_edge: float = 1e-3
+
+
+def make_config(params: Params, *, n_rows: int, n_sectors_phi: int, split_z: int,
+                half_angle: float, z_max: float, bz: float) -> OrcConfig:
+    c = OrcConfig()
+    c.half_angle, c.z_max, c.bz = half_angle, z_max, bz
+    c.sigma_y, c.sigma_z = params.sigma_y, params.sigma_z
+    c.chi2_hit, c.sin_max, c.edge_margin = params.chi2_hit, params.sin_max, params.edge_margin
+    c.seed_var_s, c.seed_var_t, c.seed_var_q = params.seed_var_s, params.seed_var_t, params.seed_var_q
+    c.tie_chi2, c.tie_sin, c.tie_edge = params.tie_chi2, params.tie_sin, params.tie_edge
+    c.slope_win_y, c.slope_win_z, c.d_max = params.slope_win_y, params.slope_win_z, params.d_max
+    c.n_rows, c.n_sectors_phi, c.split_z = n_rows, n_sectors_phi, int(split_z)
+    c.max_gap, c.min_chain = params.max_gap, params.min_chain
+    c.min_tracklet_hits, c.min_track_hits = params.min_tracklet_hits, params.min_track_hits
+    return c
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def track_event(ev, params: Params | None = None, *, shadow64: bool = True) -> dict:
+    """Run C2-C8 on one event; returns every stage's arrays as numpy (cids)."""
+    params = params or Params()
+    n = int(ev.n)
+    R = len(ev.row_x)
+    cfg = make_config(params, n_rows=R, n_sectors_phi=ev.n_sectors_phi, split_z=ev.split_z,
+                      half_angle=ev.half_angle, z_max=ev.z_max, bz=ev.bz)
+    y = np.ascontiguousarray(ev.y, dtype=np.float32)
+    z = np.ascontiguousarray(ev.z, dtype=np.float32)
+    row = np.ascontiguousarray(ev.row, dtype=np.uint16)
+    sector = np.ascontiguousarray(ev.sector, dtype=np.uint16)
+    row_x = np.ascontiguousarray(ev.row_x, dtype=np.float32)
+    cap_t = max(16, n // 2)
+    cap_k = cap_t
+    o = {
+        "up": np.empty(n, np.int32), "dn": np.empty(n, np.int32),
+        "up64": np.empty(n, np.int32) if shadow64 else None,
+        "dn64": np.empty(n, np.int32) if shadow64 else None,
+        "up_c": np.empty(n, np.int32), "dn_c": np.empty(n, np.int32),
+        "t_start": np.empty(cap_t, np.int32), "t_sector": np.empty(cap_t, np.int32),
+        "t_chain_len": np.empty(cap_t, np.int32), "t_valid": np.empty(cap_t, np.int32),
+        "t_nhits": np.empty(cap_t, np.int32), "t_first_row": np.empty(cap_t, np.int32),
+        "t_last_row": np.empty(cap_t, np.int32), "t_flags": np.empty(cap_t, np.int32),
+        "t_ndf": np.empty(cap_t, np.int32), "t_x": np.empty(cap_t, np.float64),
+        "t_p": np.empty((cap_t, 5), np.float64), "t_C": np.empty((cap_t, 15), np.float64),
+        "t_chi2": np.empty(cap_t, np.float64), "t_rowhit": np.empty((cap_t, R), np.int32),
+        "weight": np.empty(n, np.uint64),
+        "k_tracklet": np.empty(cap_k, np.int32), "k_sector": np.empty(cap_k, np.int32),
+        "k_ndf": np.empty(cap_k, np.int32), "k_x": np.empty(cap_k, np.float64),
+        "k_p": np.empty((cap_k, 5), np.float64), "k_C": np.empty((cap_k, 15), np.float64),
+        "k_chi2": np.empty(cap_k, np.float64), "k_hit_off": np.empty(cap_k + 1, np.int32),
+        "k_hit_cid": np.empty(max(n, 1), np.int32),
+    }
+    res = OrcResult()
+    for k, a in o.items():
+        setattr(res, k, _ptr(a) if a is not None else None)
+    res.cap_tracklets, res.cap_tracks = cap_t, cap_k
+    rc = lib().orc_track_event(C.byref(cfg), _ptr(row_x), C.c_int64(n), _ptr(y), _ptr(z),
+                               _ptr(row), _ptr(sector), C.byref(res))
+    if rc != 0:
+        raise RuntimeError(f"oracle returned {rc}")
+    nt, nk, nh = res.n_tracklets, res.n_tracks, res.n_track_hits
+    out = {"status": rc, "n_tracklets": nt, "n_tracks": nk, "n_track_hits": nh,
+           "n_links": res.n_links, "n_link_flips64": res.n_link_flips64,
+           "n_starts": res.n_starts}
+    for k, a in o.items():
+        if a is None:
+            continue
+        if k.startswith("t_"):
+            a = a[:nt]
+        elif k == "k_hit_off":
+            a = a[:nk + 1]
+        elif k == "k_hit_cid":
+            a = a[:nh]
+        elif k.startswith("k_"):
+            a = a[:nk]
+        out[k] = a
+    return out
+
+
+def transport(x0: float, x1: float, p, Ct, *, bz: float = 0.5, sin_max: float = 0.99):
+    """C5 on one state. Returns (rc, p1, C1 packed, J 5x5)."""
+    p = np.array(p, dtype=np.float64)
+    Ct = np.array(Ct, dtype=np.float64)
+    J = np.zeros((5, 5))
+    rc = lib().orc_transport_packed(C.c_double(x0), C.c_double(x1), C.c_double(bz),
+                                    C.c_double(sin_max), _ptr(p), _ptr(Ct), _ptr(J))
+    return rc, p, Ct, J
+
+
+def update(p, Ct, my: float, mz: float, vy: float, vz: float):
+    """C6 on one state. Returns (p1, C1 packed, chi2 increment)."""
+    p = np.array(p, dtype=np.float64)
+    Ct = np.array(Ct, dtype=np.float64)
+    chi2 = lib().orc_update_packed(_ptr(p), _ptr(Ct), C.c_double(my), C.c_double(mz),
+                                   C.c_double(vy), C.c_double(vz))
+    return p, Ct, chi2
+
+
+def fit_fixed(row_x, rows, hy, hz, *, n_iter: int = 0, params: Params | None = None,
+              bz: float = 0.5, n_rows: int | None = None):
+    """C7 passes on a given hit set (no search), then n_iter C9 passes."""
+    params = params or Params()
+    xr = np.ascontiguousarray(row_x, dtype=np.float64)
+    cfg = make_config(params, n_rows=n_rows or len(xr), n_sectors_phi=1, split_z=0,
+                      half_angle=np.radians(10.0), z_max=250.0, bz=bz)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    hy = np.ascontiguousarray(hy, dtype=np.float64)
+    hz = np.ascontiguousarray(hz, dtype=np.float64)
+    p = np.zeros(5)
+    Ct = np.zeros(15)
+    chi2 = C.c_double()
+    ndf = C.c_int32()
+    rc = lib().orc_fit_fixed(C.byref(cfg), _ptr(xr), C.c_int(len(rows)), _ptr(rows), _ptr(hy),
+                             _ptr(hz), C.c_int(n_iter), _ptr(p), _ptr(Ct), C.byref(chi2),
+                             C.byref(ndf))
+    return rc, p, Ct, chi2.value, ndf.value
+
+
+def seed(x0, y0, z0, x1, y1, z1) -> np.ndarray:
+    """C7 seed state from the first and last hit of a chain."""
+    p = np.zeros(5)
+    lib().orc_seed(*[C.c_double(v) for v in (x0, y0, z0, x1, y1, z1)], _ptr(p))
+    return p
+
+
+def unpack_cov(Ct) -> np.ndarray:
+    """15 lower-triangle entries (row order) -> symmetric 5x5."""
+    M = np.zeros((5, 5))
+    k = 0
+    for i in range(5):
+        for j in range(i + 1):
+            M[i, j] = M[j, i] = Ct[k]
+            k += 1
+    return M
+
+
+def pack_cov(M) -> np.ndarray:
+    return np.array([M[i, j] for i in range(5) for j in range(i + 1)], dtype=np.float64)

@@ -1,0 +1,77 @@
+"""Helpers shared by the tests (event fixtures and MC-truth bookkeeping)."""
+import json
+import math
+import os
+
+import numpy as np
+
+from paper_1712_09416_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden_event(name="neighbours_small.json"):
+    g = json.load(open(os.path.join(GOLDEN, name)))
+    h = np.array(g["hits"], dtype=np.float64)
+    order = np.argsort(h[:, 0])
+    h = h[order]
+    assert np.all(h[:, 0] == np.arange(len(h)))
+    ev = synth.Event(y=h[:, 3].astype(np.float32), z=h[:, 4].astype(np.float32),
+                     row=h[:, 2].astype(np.uint16), sector=h[:, 1].astype(np.uint16),
+                     label=np.full(len(h), -1, np.int32),
+                     row_x=np.array(g["row_x"], dtype=np.float32),
+                     n_sectors_phi=g["n_sectors_phi"], split_z=0)
+    return ev, g
+
+
+def track_hits(out, j, prefix="k_"):
+    off = out[prefix + "hit_off"]
+    return out[prefix + "hit_cid"][off[j]:off[j + 1]]
+
+
+def mc_summary(ev, out, min_clusters=30, match_frac=0.9, n_tracks_key="n_tracks"):
+    """Efficiency / fake / clone by MC labels.
+
+    A reco track matches particle P if >= 90% of its hits carry P's label.
+    P is reconstructable if it has >= min_clusters clusters in one sector.
+    """
+    lab = ev.label
+    matched = {}
+    fakes = 0
+    clones = 0
+    for j in range(out[n_tracks_key]):
+        hits = track_hits(out, j)
+        l = lab[hits]
+        vals, cnt = np.unique(l, return_counts=True)
+        b = np.argmax(cnt)
+        if vals[b] >= 0 and cnt[b] >= match_frac * len(hits):
+            if vals[b] in matched:
+                clones += 1
+            matched[vals[b]] = matched.get(vals[b], 0) + 1
+        else:
+            fakes += 1
+    sig = lab >= 0
+    key = lab[sig].astype(np.int64) * 64 + ev.sector[sig]
+    k, c = np.unique(key, return_counts=True)
+    recble = np.unique(k[c >= min_clusters] // 64)
+    pt = ev.particles.pt
+    res = {"n_reco": out[n_tracks_key], "n_reconstructable": len(recble), "fakes": fakes,
+           "clones": clones}
+    for name, lo in (("eff", 0.0), ("eff_pt02", 0.2)):
+        sel = [p for p in recble if pt[p] >= lo]
+        res[name] = float(np.mean([p in matched for p in sel])) if sel else float("nan")
+    res["fake_rate"] = fakes / max(1, out[n_tracks_key])
+    res["clone_rate"] = clones / max(1, out[n_tracks_key])
+    return res
+
+
+def isolated_event(n_tracks=6, seed=11, sigma=0.01, pt_range=(1.0, 5.0)):
+    """A few well separated high-pT tracks in one sector, no noise."""
+    rng = np.random.default_rng(seed)
+    phis = np.linspace(math.radians(4), math.radians(16), n_tracks)
+    p = synth.Particles(q=np.where(np.arange(n_tracks) % 2 == 0, 1.0, -1.0),
+                        pt=rng.uniform(*pt_range, n_tracks),
+                        tanl=np.linspace(-0.8, 0.8, n_tracks), phi0=phis,
+                        vx=np.zeros(n_tracks), vy=np.zeros(n_tracks), vz=np.zeros(n_tracks))
+    return synth.make_event(rng, p, n_sectors_phi=1, split_z=False, sigma=sigma,
+                            noise_frac=0.0)
