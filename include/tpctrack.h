@@ -1,0 +1,216 @@
+/*
+ * tpctrack.h -- C ABI of the B300 TPC sector tracker (libtpctrack.so).
+ *
+ * The library reconstructs particle tracks in the TPC sectors of one or more
+ * events: cellular-automaton track finding followed by a Kalman-filter track
+ * fit, the two parts of the ALICE HLT TPC tracker (paper, Abstract and
+ * Sect. 4).  The tracker consumes the clusters of all TPC links of an event
+ * (Sect. 2: the track reconstruction subscribes to all TPC links), events are
+ * reconstructed one after another or many at a time (Sect. 2: the chain works
+ * as a pipeline with many events in flight), and the tracks with their
+ * parameters and covariances feed the calibration (Sect. 3, item 1).  The
+ * paper's `FitTracks()` wraps one device launch over all tracks (Sect. 4.1,
+ * Listing 2); here every entry point wraps the device pipeline of binning,
+ * neighbour finding and cleaning, start hits, tracklet construction and
+ * selection, all hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every entry point:
+ *   - Sector frame: x along the pad-row normal (outward), y along the row,
+ *     z along the beam.  Pad row r is the plane x = row_x[r].  Sector s_phi
+ *     has its centre at alpha = (s_phi + 0.5) * 2 * half_angle.  With split_z
+ *     the sectors are doubled at z = 0: sector s_phi + n_sectors_phi holds
+ *     z < 0.
+ *   - Track state at x: (y, z, sin(phi), tan(lambda), q/pT), with phi the
+ *     angle of the momentum to the x axis in the xy plane, lambda the dip
+ *     angle, q/pT in (GeV/c)^-1.  Covariance: 15 floats, lower triangle in
+ *     row order (C00, C10, C11, C20, C21, C22, ..., C44).
+ *   - Cluster id (cid): the index of a cluster in its event's input arrays.
+ *   - Every call returns a status code; nothing aborts or prints.  On error
+ *     tpc_track_last_error() gives a one-line reason.
+ *   - Thread safety: one context is driven by one host thread at a time.
+ */
+#ifndef TPCTRACK_H
+#define TPCTRACK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    TPC_OK = 0,
+    TPC_EINVAL = -1,     /* invalid argument or input cluster (bad row/sector, NaN/Inf) */
+    TPC_ENOMEM = -2,     /* device or host allocation failed */
+    TPC_ECUDA = -3,      /* a CUDA call failed */
+    TPC_ECAPACITY = -4,  /* a device buffer would overflow; no partial result is returned */
+    TPC_ETIMEOUT = -5,   /* a bounded device wait gave up */
+    TPC_EBUSY = -6       /* served ticket not finished yet */
+};
+
+/* Detector geometry.  row_x is host memory, read during the call. */
+typedef struct {
+    int n_rows;            /* pad rows, 3..256 (159 for the ALICE TPC) */
+    const float* row_x;    /* [n_rows] cm, strictly ascending */
+    int n_sectors_phi;     /* sectors around phi (18), or 1 for a single wedge */
+    int split_z;           /* 1: sectors doubled at the z = 0 membrane */
+    float half_angle_rad;  /* half opening of a sector (10 deg) */
+    float z_max;           /* drift length, cm (250) */
+} tpc_geometry;
+
+/* One event's clusters, structure of arrays.  With on_device = 1 the four
+ * pointers are device pointers on the context's device (e.g. a torch
+ * tensor's data_ptr); otherwise host memory (pinned memory gives the fastest
+ * copies).  The caller keeps them valid for the duration of the call (for
+ * tpc_track_launch: until tpc_track_results returns; for tpc_track_submit:
+ * until tpc_track_poll has returned TPC_OK for the ticket). */
+typedef struct {
+    int64_t n;
+    const float* y;           /* [n] cm, sector frame */
+    const float* z;           /* [n] cm */
+    const uint16_t* row;      /* [n] pad row, < n_rows */
+    const uint16_t* sector;   /* [n] sector, < n_sectors_phi * (split_z ? 2 : 1) */
+    int on_device;
+} tpc_clusters;
+
+/* Reconstructed tracks of one event, ordered by (sector, row of the first
+ * hit, cid of the start hit).  All arrays are host memory owned by the
+ * context, valid until the next tpc_track_event / tpc_track_batch /
+ * tpc_track_results call on the context, or for served tickets until
+ * tpc_track_release(ticket). */
+typedef struct {
+    int64_t n_tracks;
+    const int32_t* sector;    /* [n_tracks] */
+    const float* x;           /* [n_tracks] cm, plane of the innermost tracklet hit */
+    const float* param;       /* [n_tracks][5] state at x */
+    const float* cov;         /* [n_tracks][15] */
+    const float* chi2;        /* [n_tracks] */
+    const int32_t* ndf;       /* [n_tracks] 2 * (tracklet hits) - 5 */
+    const int32_t* hit_off;   /* [n_tracks + 1] offsets into hit_cid */
+    const int32_t* hit_cid;   /* input cluster indices, ascending row within a track */
+} tpc_tracks;
+
+/* Tracker parameters; tpc_track_default_params() fills the defaults. */
+typedef struct {
+    float meas_sigma_y, meas_sigma_z;  /* cluster errors, cm (0.1, 0.1) */
+    float slope_win_y, slope_win_z;    /* neighbour windows |dy| <= w |dx| (2.0, 2.0) */
+    float d_max;                       /* neighbour kink cut (0.36) */
+    float chi2_hit;                    /* searched-hit chi2 cut (16) */
+    int max_gap;                       /* consecutive missed rows ending a search (5) */
+    int min_chain;                     /* hits of a chain to build a tracklet (3) */
+    int min_tracklet_hits;             /* hits of a valid tracklet (10) */
+    int min_track_hits;                /* owned hits of an emitted track (10) */
+    float sin_max;                     /* transport fails at |sin phi| >= sin_max (0.99) */
+    float edge_margin;                 /* cm beyond the sector edge ending a search (2) */
+    float seed_var_s;                  /* seed variance of the slope dy/dx (1); sin(phi) gets it x cos^6(phi) */
+    float seed_var_t;                  /* seed variance of the slope dz/dx (1); tan(lambda) gets it x cos^2(phi) */
+    float seed_var_q;                  /* seed variance of q/pT (100) */
+} tpc_track_params;
+
+/* Context configuration. */
+typedef struct {
+    int device;                       /* CUDA device ordinal */
+    size_t mem_budget;                /* bytes of device memory the context may hold; 0 = derive */
+    int64_t max_clusters_per_event;   /* capacity of one launch (sum over a batch), > 0 */
+    int max_events_in_flight;         /* served slots (device arenas); >= 1 */
+    void* cuda_stream;                /* cudaStream_t for the launches, NULL = own stream */
+    int max_rows;                     /* largest n_rows of any geometry used (0 = 159) */
+    int max_events_per_launch;        /* events in one batch launch (0 = 64), <= 1024 */
+    tpc_track_params params;
+} tpc_track_config;
+
+typedef struct tpc_track_ctx tpc_track_ctx;
+
+/* Fill p with the default parameters listed above. */
+void tpc_track_default_params(tpc_track_params* p);
+
+/* Create a context: allocates every device arena up front (no allocation
+ * happens on the tracking path).  Returns TPC_EINVAL for a bad config,
+ * TPC_ENOMEM if the arenas do not fit the device or mem_budget, TPC_ECUDA
+ * for other CUDA failures.  *out is NULL on failure. */
+int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out);
+
+/* Track one event: stage inputs (host->device copy unless on_device), run
+ * the device pipeline, copy the tracks back.  Blocks until done.  Inputs are
+ * checked on the device before any result is produced: an invalid cluster
+ * gives TPC_EINVAL, an overflow TPC_ECAPACITY; in both cases out->n_tracks = 0. */
+int tpc_track_event(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geometry* geom,
+                    float bz_tesla, tpc_tracks* out);
+
+/* Track n_ev events in one device pass (sectors of all events side by side,
+ * one launch per stage).  outs[i] receives event i.  The cluster counts
+ * summed over the batch must not exceed max_clusters_per_event.  Each
+ * event's tracks are identical to those of tpc_track_event on it alone. */
+int tpc_track_batch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
+                    const tpc_geometry* geom, float bz_tesla, tpc_tracks* outs);
+
+/* Asynchronous form of tpc_track_batch: enqueue the device pipeline on the
+ * context's stream and return.  With host inputs the copies are enqueued
+ * too (the inputs must stay valid until tpc_track_results).  The tracks
+ * stay in device memory until tpc_track_results, which waits, checks the
+ * device status and copies them out.  A launch with results still pending
+ * first discards them. */
+int tpc_track_launch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
+                     const tpc_geometry* geom, float bz_tesla);
+int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs);
+
+/* Served form: queue one event.  A dispatcher thread admits queued events
+ * into free slots while their device memory fits the budget, batching all
+ * admitted events into the next launch; launches on different slots overlap
+ * on the device.  *ticket identifies the request.  Returns TPC_EINVAL for
+ * an event larger than one slot. */
+int tpc_track_submit(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geometry* geom,
+                     float bz_tesla, uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = just test, < 0 = forever) for a ticket.
+ * TPC_OK fills *out (valid until tpc_track_release); TPC_EBUSY if not done;
+ * the ticket's own error code if its launch failed. */
+int tpc_track_poll(tpc_track_ctx* ctx, uint64_t ticket, int timeout_us, tpc_tracks* out);
+
+/* Free the host memory of a finished ticket. */
+int tpc_track_release(tpc_track_ctx* ctx, uint64_t ticket);
+
+/* Per-launch counters of the last tpc_track_results (for the byte model
+ * of the benchmark and for tests). */
+typedef struct {
+    int64_t n_clusters, n_rows_total, n_bins, n_links, n_starts, n_tracklets,
+            n_valid_tracklets, n_tracklet_hits, n_tracks, n_track_hits;
+} tpc_track_counters;
+int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c);
+
+/* Stream the context launches on (a cudaStream_t). */
+void* tpc_track_stream(const tpc_track_ctx* ctx);
+
+/* Debug dump of an intermediate stage of event 0 of the last completed
+ * launch, for parity tests.  Writes at most cap bytes to host_buf and the
+ * size needed to *used (call with cap = 0 to query).  Stages:
+ *   TPC_DUMP_LINKS      int32 [2][n]: up, down link as cid (or -1), by cid
+ *   TPC_DUMP_CLEAN      int32 [2][n]: links after cleaning, by cid
+ *   TPC_DUMP_STARTS     int32 [n_starts]: start-hit cids, ascending
+ *   TPC_DUMP_TRACKLETS  int32 count, then count records of
+ *                       tpc_dump_tracklet followed by int32 rowhit[n_rows]
+ *                       (cid or -1), ordered by start cid
+ *   TPC_DUMP_WEIGHTS    uint64 [n]: hit weight by cid (0 = none)
+ *   TPC_DUMP_SORTED     int32 [n]: cids in the device's (sector, row, bin) order
+ * Returns TPC_EINVAL for an unknown stage or no completed launch. */
+enum { TPC_DUMP_LINKS = 1, TPC_DUMP_CLEAN = 2, TPC_DUMP_STARTS = 3, TPC_DUMP_TRACKLETS = 4,
+       TPC_DUMP_WEIGHTS = 5, TPC_DUMP_SORTED = 6 };
+typedef struct {
+    int32_t start_cid, sector, valid, nhits, first_row, last_row, ndf, pad;
+    float x, param[5], cov[15], chi2;
+} tpc_dump_tracklet;
+int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t cap,
+                         size_t* used);
+
+/* One-line description of the last error on the context (never NULL). */
+const char* tpc_track_last_error(const tpc_track_ctx* ctx);
+
+/* Release every resource of the context (waits for its device work). */
+void tpc_track_destroy(tpc_track_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPCTRACK_H */

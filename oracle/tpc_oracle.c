@@ -365,13 +365,21 @@ typedef struct {
     double x, p[5], C[5][5], chi2;
 } tracklet_t;
 
-static void seed_cov(const orc_config* cfg, double C[5][5])
+/*
+ * Seed covariance at a state with sin(phi) = s: diagonal, with the cluster
+ * variances for (y, z), the variances seed_var_s and seed_var_t of the slopes
+ * dy/dx and dz/dx carried over to sin(phi) and tan(lambda) at that direction
+ * (d sin(phi)/d(dy/dx) = cos^3 phi, d tan(lambda)/d(dz/dx) = cos phi), and
+ * seed_var_q for q/pT.
+ */
+static void seed_cov(const orc_config* cfg, double C[5][5], double s)
 {
+    const double c2 = 1.0 - s * s;
     memset(C, 0, 25 * sizeof(double));
     C[0][0] = cfg->sigma_y * cfg->sigma_y;
     C[1][1] = cfg->sigma_z * cfg->sigma_z;
-    C[2][2] = cfg->seed_var_s;
-    C[3][3] = cfg->seed_var_t;
+    C[2][2] = cfg->seed_var_s * c2 * c2 * c2;
+    C[3][3] = cfg->seed_var_t * c2;
     C[4][4] = cfg->seed_var_q;
 }
 
@@ -460,7 +468,7 @@ static void build_tracklet(const hits_t* H, const orc_config* cfg, int sec,
     double p[5], C[5][5];
     seed_state(H->xr[r0], H->y[chain[0]], H->z[chain[0]], H->xr[rk], H->y[chain[k1 - 1]],
                H->z[chain[k1 - 1]], p);
-    seed_cov(cfg, C);
+    seed_cov(cfg, C, p[2]);
     double x = H->xr[r0];
     /* forward pass over the chain */
     orc_update(p, C, H->y[chain[0]], H->z[chain[0]], vy, vz);
@@ -505,7 +513,7 @@ static void build_tracklet(const hits_t* H, const orc_config* cfg, int sec,
     /* backward pass */
     for (int r = 0; r < R; ++r) rowhit[r] = -1;
     memcpy(p, pL, sizeof(pL));
-    seed_cov(cfg, C);
+    seed_cov(cfg, C, p[2]);
     x = H->xr[last];
     double chi2 = orc_update(p, C, H->y[fwd[last]], H->z[fwd[last]], vy, vz);
     int nupd = 1;
@@ -780,7 +788,7 @@ int orc_fit_fixed(const orc_config* cfg, const double* xr, int n_hits, const int
     const int r0 = rows[0], rk = rows[n_hits - 1];
     double p[5], C[5][5];
     seed_state(xr[r0], hy[0], hz[0], xr[rk], hy[n_hits - 1], hz[n_hits - 1], p);
-    seed_cov(cfg, C);
+    seed_cov(cfg, C, p[2]);
     double x = xr[r0];
     orc_update(p, C, hy[0], hz[0], vy, vz);
     for (int i = 1; i < n_hits; ++i) {
@@ -796,7 +804,7 @@ int orc_fit_fixed(const orc_config* cfg, const double* xr, int n_hits, const int
                 return -1;
         }
         x = xr[rk];
-        seed_cov(cfg, C);
+        seed_cov(cfg, C, p[2]);
         chi2 = orc_update(p, C, hy[n_hits - 1], hz[n_hits - 1], vy, vz);
         for (int i = n_hits - 2; i >= 0; --i) {
             if (orc_transport(x, xr[rows[i]], cfg->bz, cfg->sin_max, 0.0, p, C, NULL, NULL))

@@ -1,0 +1,212 @@
+// k_selector.cu -- shared-hit resolution and output of the tracks.
+//
+// A hit belongs to the valid tracklet with the largest weight key
+// (nHits << 32 | ~cid(h0)), which the constructor left in weight[] with
+// atomicMax.  A tracklet becomes a track when it owns at least
+// min_track_hits hits and at least half of its hits; the track keeps the
+// owned hits and the tracklet's parameters.  Tracks are emitted in the order
+// (sector, row of the first owned hit, cid of h0).
+//   k_sel_decide  one thread per tracklet: owned hits, decision, sort key;
+//                 also marks the tracklet range of every sector (tracklets
+//                 are ordered by sector because start hits are)
+//   k_sel_sort    one block per sector, in sector order: compacts the
+//                 emitted tracklets with a warp ballot, sorts their keys in
+//                 shared memory (bitonic), scans their hit counts and takes
+//                 the sector's output offsets from a decoupled look-back
+//   k_sel_write   one thread per emitted tracklet: header and owned hit cids
+// Bytes per cluster: rowhit 2 + weight 8 per assigned hit (decide), about
+// 100 B per track header and 4 B per output hit (write).
+#include <cuda_runtime.h>
+
+#include "tpc_internal.cuh"
+
+namespace tpc {
+
+namespace {
+
+constexpr unsigned long long kNone = ~0ULL;
+
+__global__ void k_sel_decide(Launch L)
+{
+    const int n_st = min(L.cnt->n_starts, L.t_cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_st; t += gridDim.x * blockDim.x) {
+        const TrackletHdr& H = L.tl[t];
+        const int gs = L.hrow[H.start] >> 8;
+        if (t == 0 || (L.hrow[L.tl[t - 1].start] >> 8) != gs) L.sec_first[gs] = t;
+        if (t == n_st - 1 || (L.hrow[L.tl[t + 1].start] >> 8) != gs) L.sec_end[gs] = t + 1;
+        unsigned long long out = kNone;
+        int nown = 0;
+        if (H.chain_len >= L.min_chain && H.valid) {
+            const unsigned long long key = ((unsigned long long)H.nhits << 32) |
+                                           (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
+            const int16_t* rowhit = L.tl_rowhit + (size_t)t * L.R;
+            const int gbase = gs * L.R;
+            int first_own = -1;
+            for (int r = H.first; r <= H.last; ++r) {
+                const int k = rowhit[r];
+                if (k >= 0 && L.weight[L.row_off[gbase + r] + k] == key) {
+                    if (first_own < 0) first_own = r;
+                    ++nown;
+                }
+            }
+            if (nown >= L.min_track_hits && 2 * nown >= H.nhits)
+                out = ((unsigned long long)first_own << 32) | (unsigned long long)(unsigned)L.hcid[H.start];
+        }
+        L.tl_key[t] = out;
+        L.tl_nown[t] = nown;
+        L.tl_out[t] = -1;
+    }
+}
+
+constexpr int kSortThreads = 512;
+
+__global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
+{
+    extern __shared__ unsigned long long keys[];         // [kMaxSectorTracks]
+    int* idx = reinterpret_cast<int*>(keys + kMaxSectorTracks);  // [kMaxSectorTracks]
+    __shared__ int m_s, tile_s;
+    __shared__ unsigned long long prefix_s;
+    __shared__ int warp_sum[kSortThreads / 32];
+    if (threadIdx.x == 0) {
+        tile_s = atomicAdd(&L.cnt->ticket_sectors, 1);
+        m_s = 0;
+    }
+    __syncthreads();
+    const int g = tile_s;  // sectors are processed in ticket order
+    const int t0 = L.sec_first[g], t1 = L.sec_end[g];
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const unsigned long long k = L.tl_key[t];
+        if (k != kNone) {
+            const int pos = atomicAdd(&m_s, 1);
+            if (pos < kMaxSectorTracks) {
+                keys[pos] = k;
+                idx[pos] = t;
+            }
+        }
+    }
+    __syncthreads();
+    int m = m_s;
+    if (m > kMaxSectorTracks) {
+        if (threadIdx.x == 0) atomicExch(&L.cnt->ovf_sector, 1);
+        m = kMaxSectorTracks;
+    }
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int i = m + threadIdx.x; i < P; i += blockDim.x) {
+        keys[i] = kNone;
+        idx[i] = -1;
+    }
+    __syncthreads();
+    // bitonic sort, ascending keys (unique)
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const unsigned long long a = keys[i], b = keys[l];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[l] = a;
+                        const int ti = idx[i];
+                        idx[i] = idx[l];
+                        idx[l] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // hit offsets: each thread handles a contiguous chunk of the sorted tracks
+    const int per = (m + blockDim.x - 1) / blockDim.x;
+    const int lo = min(m, (int)threadIdx.x * per), hi = min(m, lo + per);
+    int hsum = 0;
+    for (int i = lo; i < hi; ++i) hsum += L.tl_nown[idx[i]];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = hsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const int v = warp_sum[w];
+            warp_sum[w] = run;
+            run += v;
+        }
+        prefix_s = lookback_exclusive(L.tile_state + L.n_row_tiles + L.n_hit_tiles, g,
+                                      pack2((unsigned)m, (unsigned)run), L.cnt);
+        const int tb = (int)unpack_a(prefix_s), hb = (int)unpack_b(prefix_s);
+        L.sec_trk_off[g] = tb;
+        L.sec_hit_off[g] = hb;
+        if (g == L.S - 1) {
+            L.sec_trk_off[L.S] = tb + m;
+            L.sec_hit_off[L.S] = hb + run;
+            L.cnt->n_tracks = tb + m;
+            L.cnt->n_track_hits = hb + run;
+            L.k_hit_off[tb + m] = hb + run;
+        }
+    }
+    __syncthreads();
+    const int tb = (int)unpack_a(prefix_s), hb = (int)unpack_b(prefix_s);
+    int off = hb + warp_sum[wid] + incl - hsum;
+    for (int i = lo; i < hi; ++i) {
+        const int t = idx[i];
+        L.tl_out[t] = tb + i;
+        L.tl_hitoff[t] = off;
+        off += L.tl_nown[t];
+    }
+}
+
+__global__ void k_sel_write(Launch L)
+{
+    const int n_st = min(L.cnt->n_starts, L.t_cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_st; t += gridDim.x * blockDim.x) {
+        const int j = L.tl_out[t];
+        if (j < 0) continue;
+        const TrackletHdr& H = L.tl[t];
+        const int gs = L.hrow[H.start] >> 8;
+        const int e = L.sec_event[gs];
+        L.k_sector[j] = gs - L.ev[e].sec_base;
+        L.k_x[j] = H.x;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) L.k_param[(size_t)j * 5 + i] = H.p[i];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) L.k_cov[(size_t)j * 15 + i] = H.C[i];
+        L.k_chi2[j] = H.chi2;
+        L.k_ndf[j] = H.ndf;
+        int off = L.tl_hitoff[t];
+        L.k_hit_off[j] = off;
+        const unsigned long long key = ((unsigned long long)H.nhits << 32) |
+                                       (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
+        const int16_t* rowhit = L.tl_rowhit + (size_t)t * L.R;
+        const int gbase = gs * L.R;
+        for (int r = H.first; r <= H.last; ++r) {
+            const int k = rowhit[r];
+            if (k < 0) continue;
+            const int h = L.row_off[gbase + r] + k;
+            if (L.weight[h] == key) L.k_hit_cid[off++] = L.hcid[h];
+        }
+    }
+}
+
+}  // namespace
+
+void launch_selector(const Launch& L, void* stream_)
+{
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int blocks = (L.t_cap + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    if (blocks < 1) blocks = 1;
+    k_sel_decide<<<blocks, 256, 0, stream>>>(L);
+    const size_t sm = kMaxSectorTracks * (sizeof(unsigned long long) + sizeof(int));
+    cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_sel_sort<<<L.S, kSortThreads, sm, stream>>>(L);
+    k_sel_write<<<blocks, 256, 0, stream>>>(L);
+}
+
+}  // namespace tpc

@@ -1,0 +1,197 @@
+// tpc_internal.cuh -- device-side records shared by the tracker's kernels and
+// the host orchestrator of libtpctrack.so.  Not part of the public ABI.
+//
+// Data layout in HBM (one arena per slot, allocated at context creation):
+//   inputs      per-event pointers (EventDesc), host inputs staged as SoA
+//   rows        (global sector, row) records: counts, offsets, y-z grids;
+//               a batch is its events' sectors side by side, so every kernel
+//               sees one flat list of sectors
+//   hits        sorted by (sector, row, bin, cid): hy, hz (f32), hcid (event
+//               cid), hrow (sector << 8 | row); bins hold row-local offsets
+//   links       up/dn/upc/dnc as int16 row-local indices into the adjacent row
+//   tracklets   one per start hit: header + rowhit[R] (int16 row-local index)
+//   outputs     tracks in canonical order, hit cids
+#pragma once
+#include <cstdint>
+
+namespace tpc {
+
+constexpr int kMaxRows = 256;          // pad rows per sector (row index fits 8 bits)
+constexpr int kMaxRowHits = 4096;      // hits of one (sector,row) handled in shared memory
+constexpr int kMaxSectorTracks = 4096; // emitted tracks per sector sorted in shared memory
+constexpr int kMaxBinsPerDim = 512;
+constexpr long long kSpinLimit = 1LL << 22;  // bounded look-back waits
+
+struct EventDesc {
+    const float* y;
+    const float* z;
+    const uint16_t* row;
+    const uint16_t* sec;
+    long long n;
+    long long cl_off;   // first global cluster index of the event
+    int sec_base;       // first global sector of the event
+    int n_sec;
+};
+
+struct RowGrid {        // y-z bin grid of one (sector,row)
+    float y0, z0, idy, idz;
+    int ny, nz, bin_off, pad;
+};
+
+struct TrackletHdr {
+    float x, p[5], C[15], chi2;
+    int start;          // global sorted index of the chain start h0
+    int nhits, first, last, ndf, valid, chain_len, pad;
+};
+
+// Device counters and status, zeroed before every launch.
+struct Counters {
+    int n_invalid;        // clusters failing the input checks
+    int ovf_row;          // a row above kMaxRowHits
+    int ovf_tracklets;    // more start hits than tracklet slots
+    int ovf_sector;       // more emitted tracks in a sector than kMaxSectorTracks
+    int timeout;          // a bounded look-back wait gave up
+    int n_links;
+    int n_starts;
+    int n_tracklets;      // chains long enough for a tracklet
+    int n_valid;
+    int n_tracklet_hits;
+    int n_tracks;
+    int n_track_hits;
+    int n_bins;
+    int ticket_rows, ticket_hits, ticket_sectors;
+    int pad[16];
+};
+
+// Everything a kernel needs, passed by value.
+struct Launch {
+    // sizes
+    long long n_total;   // clusters in the launch
+    int n_events;
+    int R;               // rows per sector
+    int S;               // global sectors in the launch
+    int RS;              // S * R
+    int n_sectors_phi, split_z;
+    int t_cap;           // tracklet slots
+    // geometry and field
+    float tan_half, z_max, kB;   // kB = KAPPA * bz
+    float row_x[kMaxRows];
+    // parameters
+    float sy2, sz2;              // measurement variances
+    float slope_win_y, slope_win_z, d_max, chi2_hit, sin_max, edge_margin;
+    float seed_var_s, seed_var_t, seed_var_q;
+    int max_gap, min_chain, min_tracklet_hits, min_track_hits;
+    // arena
+    EventDesc* ev;              // [n_events]
+    long long* ev_off;          // [n_events + 1] cluster offsets
+    int* sec_event;             // [S] event of a global sector
+    int* row_cnt;               // [RS]
+    int* row_fill;              // [RS]
+    int* row_off;               // [RS + 1]
+    RowGrid* grid;              // [RS]
+    unsigned long long* tile_state;  // look-back states (rows | hits | sectors)
+    int n_row_tiles, n_hit_tiles;
+    float* tmp_y; float* tmp_z; int* tmp_cid;   // row-scattered
+    float* hy; float* hz; int* hcid; int* hrow; // sorted
+    int* bin_start;
+    int16_t* up; int16_t* dn; int16_t* upc; int16_t* dnc;
+    unsigned long long* weight;
+    int* starts;                // [t_cap] global sorted index
+    TrackletHdr* tl;            // [t_cap]
+    int16_t* tl_rowhit;         // [t_cap * R]
+    unsigned long long* tl_key; // [t_cap] sector-local sort key or ~0
+    int* tl_nown;               // [t_cap]
+    int* tl_out;                // [t_cap] output track index or -1
+    int* tl_hitoff;             // [t_cap] output hit offset
+    int* sec_first;             // [S] first tracklet of a sector
+    int* sec_end;               // [S]
+    int* sec_trk_off;           // [S + 1] output track offset of a sector
+    int* sec_hit_off;           // [S + 1]
+    // outputs
+    int* k_sector; float* k_x; float* k_param; float* k_cov; float* k_chi2; int* k_ndf;
+    int* k_hit_off; int* k_hit_cid;
+    Counters* cnt;
+};
+
+// ---------------------------------------------------------------------------
+// ordered prefix across thread blocks (decoupled look-back), one thread calls.
+// The 64-bit state holds a 2-bit status (1 aggregate, 2 inclusive) over a
+// 62-bit payload; payloads are two packed 31-bit counts (a << 31 | b) whose
+// sums never carry.  Waits are bounded; on timeout cnt->timeout is set.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+constexpr unsigned long long kPayload = (1ULL << 62) - 1;
+
+__device__ __forceinline__ unsigned long long pack2(unsigned a, unsigned b)
+{
+    return ((unsigned long long)a << 31) | (unsigned long long)b;
+}
+__device__ __forceinline__ unsigned unpack_a(unsigned long long v) { return (unsigned)(v >> 31); }
+__device__ __forceinline__ unsigned unpack_b(unsigned long long v)
+{
+    return (unsigned)(v & 0x7FFFFFFFULL);
+}
+
+__device__ inline unsigned long long lookback_exclusive(unsigned long long* state, int tile,
+                                                        unsigned long long aggregate,
+                                                        Counters* cnt)
+{
+    if (tile == 0) {
+        st_release(&state[0], (2ULL << 62) | aggregate);
+        return 0;
+    }
+    st_release(&state[tile], (1ULL << 62) | aggregate);
+    unsigned long long excl = 0;
+    int t = tile - 1;
+    long long spins = 0;
+    while (t >= 0) {
+        const unsigned long long v = ld_acquire(&state[t]);
+        const unsigned f = (unsigned)(v >> 62);
+        if (f == 0) {
+            if (++spins > kSpinLimit) {
+                atomicExch(&cnt->timeout, 1);
+                break;
+            }
+            __nanosleep(20);
+            continue;
+        }
+        excl += v & kPayload;
+        if (f == 2) break;
+        --t;
+    }
+    st_release(&state[tile], (2ULL << 62) | (excl + aggregate));
+    return excl;
+}
+
+// Bin of a coordinate in a row grid, clamped to the edge bins.  The same
+// monotone arithmetic sorts the hits and bounds every window query, so a
+// window [lo, hi] maps onto bins [bin(lo), bin(hi)] that hold all its hits.
+__device__ __forceinline__ int bin_y(const RowGrid& G, float y)
+{
+    const int b = (int)floorf((y - G.y0) * G.idy);
+    return min(max(b, 0), G.ny - 1);
+}
+__device__ __forceinline__ int bin_z(const RowGrid& G, float z)
+{
+    const int b = (int)floorf((z - G.z0) * G.idz);
+    return min(max(b, 0), G.nz - 1);
+}
+
+// host-side launchers (one translation unit each)
+void launch_binning(const Launch& L, void* stream);
+void launch_finder(const Launch& L, void* stream);
+void launch_constructor(const Launch& L, void* stream);
+void launch_selector(const Launch& L, void* stream);
+
+}  // namespace tpc

@@ -1,0 +1,917 @@
+// tpctrack.cu -- host side of libtpctrack.so: contexts, device arenas, launch
+// orchestration, result collection, debug dumps and the served form.
+//
+// Memory: every slot owns one device arena sized at creation for
+// max_clusters_per_event clusters, max_events_per_launch events and
+// max_rows rows; no allocation happens while tracking.  Slot 0 serves the
+// direct calls (tpc_track_event/batch/launch); with tpc_track_submit, one
+// worker thread per slot pulls every queued event that fits its arena into
+// its next launch (continuous batching), so launches of different slots run
+// concurrently on the device while the next requests queue up.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/tpctrack.h"
+#include "tpc_internal.cuh"
+
+namespace tpc {
+
+namespace {
+
+constexpr double kKappa = 0.299792458e-2;  // cm^-1 per (GeV/c)^-1 per tesla
+constexpr int kTileRows = 2048;            // rows per look-back tile (k_rowscan)
+constexpr int kTileHits = 2048;            // hits per look-back tile (k_clean_starts)
+constexpr int kMaxEventsPerLaunch = 1024;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Capacities of one arena.
+struct Caps {
+    long long n;   // clusters
+    int e;         // events
+    int s;         // sectors
+    int r;         // rows per sector
+    long long rs;  // s * r
+    long long bins;
+    int t;         // tracklet slots
+    long long row_tiles, hit_tiles;
+};
+
+struct HostOut {  // pinned host copies of one launch's results
+    int32_t* sector = nullptr;
+    float* x = nullptr;
+    float* param = nullptr;
+    float* cov = nullptr;
+    float* chi2 = nullptr;
+    int32_t* ndf = nullptr;
+    int32_t* hit_off = nullptr;
+    int32_t* hit_cid = nullptr;
+    int32_t* sec_trk_off = nullptr;
+    int32_t* sec_hit_off = nullptr;
+    int32_t* ev_hit_off = nullptr;  // per-event rebased hit offsets, concatenated
+};
+
+struct LaunchInfo {
+    int n_ev = 0;
+    std::vector<long long> ev_n;     // clusters per event
+    std::vector<int> ev_sec_base, ev_n_sec;
+    int S = 0, R = 0;
+    Launch L;
+    bool pending = false;
+    bool done = false;
+    tpc_track_counters counters{};
+};
+
+struct Slot {
+    int id = 0;
+    Caps caps{};
+    char* dev = nullptr;
+    size_t dev_bytes = 0;
+    // fixed device buffers
+    float *in_y, *in_z;
+    uint16_t *in_row, *in_sec;
+    void* desc_dev;      // EventDesc[e] | ev_off[e+1] | sec_event[s]
+    char* zero_dev;      // counters | row_cnt | row_fill | sec_first | sec_end | tile_state
+    size_t zero_cap = 0;
+    int *row_off;
+    RowGrid* grid;
+    float *tmp_y, *tmp_z;
+    int* tmp_cid;
+    float *hy, *hz;
+    int *hcid, *hrow, *bin_start;
+    int16_t *up, *dn, *upc, *dnc;
+    unsigned long long* weight;
+    int* starts;
+    TrackletHdr* tl;
+    int16_t* tl_rowhit;
+    unsigned long long* tl_key;
+    int *tl_nown, *tl_out, *tl_hitoff, *sec_trk_off, *sec_hit_off;
+    int *k_sector, *k_ndf, *k_hit_off, *k_hit_cid;
+    float *k_x, *k_param, *k_cov, *k_chi2;
+    // host side
+    void* desc_host = nullptr;  // pinned mirror of desc_dev
+    size_t desc_bytes = 0;
+    Counters* cnt_host = nullptr;
+    HostOut out;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t done_ev = nullptr;
+    LaunchInfo info;
+    std::vector<tpc_tracks> tracks;  // per event of the last results
+};
+
+struct Request {
+    uint64_t ticket;
+    tpc_clusters ev;
+    std::vector<float> row_x;
+    tpc_geometry geom;
+    float bz;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+struct TicketResult {
+    int status = TPC_EBUSY;
+    std::vector<int32_t> sector, ndf, hit_off, hit_cid;
+    std::vector<float> x, param, cov, chi2;
+    tpc_tracks view{};
+};
+
+}  // namespace
+}  // namespace tpc
+
+struct tpc_track_ctx {
+    tpc_track_config cfg;
+    std::vector<std::unique_ptr<tpc::Slot>> slots;
+    std::string err;
+    // served form
+    std::mutex mu;
+    std::condition_variable cv_req, cv_done;
+    std::deque<tpc::Request> queue;
+    std::map<uint64_t, std::unique_ptr<tpc::TicketResult>> results;
+    std::vector<std::thread> workers;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::atomic<int> direct_busy{0};
+};
+
+namespace tpc {
+namespace {
+
+int fail(tpc_track_ctx* ctx, int code, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail((ctx), TPC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+Caps make_caps(const tpc_track_config& c)
+{
+    Caps k;
+    k.n = std::max<long long>(1, c.max_clusters_per_event);
+    k.e = c.max_events_per_launch > 0 ? c.max_events_per_launch : 64;
+    k.r = c.max_rows > 0 ? c.max_rows : 159;
+    k.s = k.e * 36;
+    k.rs = (long long)k.s * k.r;
+    k.bins = k.n / 2 + 2 * k.rs + 16;
+    k.t = (int)std::min<long long>(k.n / 4 + 4096, 0x7fffffffLL / 256);
+    k.row_tiles = k.rs / kTileRows + 2;
+    k.hit_tiles = k.n / kTileHits + 2;
+    return k;
+}
+
+// Lay out (or, with base == nullptr, just size) the arena of a slot.
+size_t layout(Slot& s, char* base)
+{
+    const Caps& k = s.caps;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = align_up(off, 256);
+        char* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    s.in_y = (float*)take(4 * k.n);
+    s.in_z = (float*)take(4 * k.n);
+    s.in_row = (uint16_t*)take(2 * k.n);
+    s.in_sec = (uint16_t*)take(2 * k.n);
+    s.desc_bytes = sizeof(EventDesc) * k.e + sizeof(long long) * (k.e + 1) + sizeof(int) * k.s + 64;
+    s.desc_dev = take(s.desc_bytes);
+    s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (2 * k.rs + 2 * k.s) + 8 * (k.row_tiles + k.hit_tiles + k.s) + 4096;
+    s.zero_dev = take(s.zero_cap);
+    s.row_off = (int*)take(4 * (k.rs + 1));
+    s.grid = (RowGrid*)take(sizeof(RowGrid) * k.rs);
+    s.tmp_y = (float*)take(4 * k.n);
+    s.tmp_z = (float*)take(4 * k.n);
+    s.tmp_cid = (int*)take(4 * k.n);
+    s.hy = (float*)take(4 * k.n);
+    s.hz = (float*)take(4 * k.n);
+    s.hcid = (int*)take(4 * k.n);
+    s.hrow = (int*)take(4 * k.n);
+    s.bin_start = (int*)take(4 * k.bins);
+    s.up = (int16_t*)take(2 * k.n);
+    s.dn = (int16_t*)take(2 * k.n);
+    s.upc = (int16_t*)take(2 * k.n);
+    s.dnc = (int16_t*)take(2 * k.n);
+    s.weight = (unsigned long long*)take(8 * k.n);
+    s.starts = (int*)take(4 * (size_t)k.t);
+    s.tl = (TrackletHdr*)take(sizeof(TrackletHdr) * (size_t)k.t);
+    s.tl_rowhit = (int16_t*)take(2 * (size_t)k.t * k.r);
+    s.tl_key = (unsigned long long*)take(8 * (size_t)k.t);
+    s.tl_nown = (int*)take(4 * (size_t)k.t);
+    s.tl_out = (int*)take(4 * (size_t)k.t);
+    s.tl_hitoff = (int*)take(4 * (size_t)k.t);
+    s.sec_trk_off = (int*)take(4 * (k.s + 1));
+    s.sec_hit_off = (int*)take(4 * (k.s + 1));
+    s.k_sector = (int*)take(4 * (size_t)k.t);
+    s.k_ndf = (int*)take(4 * (size_t)k.t);
+    s.k_hit_off = (int*)take(4 * ((size_t)k.t + 1));
+    s.k_hit_cid = (int*)take(4 * k.n);
+    s.k_x = (float*)take(4 * (size_t)k.t);
+    s.k_param = (float*)take(20 * (size_t)k.t);
+    s.k_cov = (float*)take(60 * (size_t)k.t);
+    s.k_chi2 = (float*)take(4 * (size_t)k.t);
+    return align_up(off, 256);
+}
+
+int alloc_slot(tpc_track_ctx* ctx, Slot& s)
+{
+    s.dev_bytes = layout(s, nullptr);
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, s.dev_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, TPC_ENOMEM, "cudaMalloc of a " + std::to_string(s.dev_bytes >> 20) +
+                                         " MiB arena failed: " + cudaGetErrorString(e));
+    }
+    s.dev = base;
+    layout(s, base);
+    const Caps& k = s.caps;
+    CUDA_TRY(ctx, cudaMallocHost(&s.desc_host, s.desc_bytes));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.cnt_host, sizeof(Counters)));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.sector, 4 * (size_t)k.t));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.x, 4 * (size_t)k.t));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.param, 20 * (size_t)k.t));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.cov, 60 * (size_t)k.t));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.chi2, 4 * (size_t)k.t));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.ndf, 4 * (size_t)k.t));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.hit_off, 4 * ((size_t)k.t + 1)));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.hit_cid, 4 * (size_t)k.n));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.sec_trk_off, 4 * ((size_t)k.s + 1)));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.sec_hit_off, 4 * ((size_t)k.s + 1)));
+    CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.ev_hit_off, 4 * ((size_t)k.t + k.e + 1)));
+    CUDA_TRY(ctx, cudaEventCreateWithFlags(&s.done_ev, cudaEventDisableTiming));
+    return TPC_OK;
+}
+
+void free_slot(Slot& s)
+{
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.dev) cudaFree(s.dev);
+    if (s.desc_host) cudaFreeHost(s.desc_host);
+    if (s.cnt_host) cudaFreeHost(s.cnt_host);
+    void* hp[] = {s.out.sector, s.out.x, s.out.param, s.out.cov, s.out.chi2, s.out.ndf,
+                  s.out.hit_off, s.out.hit_cid, s.out.sec_trk_off, s.out.sec_hit_off,
+                  s.out.ev_hit_off};
+    for (void* p : hp)
+        if (p) cudaFreeHost(p);
+    if (s.done_ev) cudaEventDestroy(s.done_ev);
+    if (s.own_stream && s.stream) cudaStreamDestroy(s.stream);
+    s = Slot();
+}
+
+int check_geometry(tpc_track_ctx* ctx, const Slot& s, const tpc_geometry* g)
+{
+    if (!g || !g->row_x) return fail(ctx, TPC_EINVAL, "geometry or row_x is NULL");
+    if (g->n_rows < 3 || g->n_rows > kMaxRows || g->n_rows > s.caps.r)
+        return fail(ctx, TPC_EINVAL, "n_rows out of range (3.." + std::to_string(std::min(kMaxRows, s.caps.r)) + ")");
+    for (int r = 0; r < g->n_rows; ++r) {
+        if (!std::isfinite(g->row_x[r])) return fail(ctx, TPC_EINVAL, "row_x not finite");
+        if (r > 0 && !(g->row_x[r] > g->row_x[r - 1]))
+            return fail(ctx, TPC_EINVAL, "row_x not strictly ascending");
+    }
+    if (g->n_sectors_phi < 1 || g->n_sectors_phi > 36)
+        return fail(ctx, TPC_EINVAL, "n_sectors_phi out of range (1..36)");
+    if (!(g->half_angle_rad > 0.0f && g->half_angle_rad < 1.5f) || !(g->z_max > 0.0f))
+        return fail(ctx, TPC_EINVAL, "half_angle_rad or z_max out of range");
+    return TPC_OK;
+}
+
+// Enqueue the whole device pipeline of one launch on the slot's stream.
+int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const tpc_geometry* g,
+            float bz)
+{
+    if (n_ev < 1 || n_ev > s.caps.e || n_ev > kMaxEventsPerLaunch)
+        return fail(ctx, TPC_EINVAL, "n_ev out of range (1.." + std::to_string(s.caps.e) + ")");
+    if (!ev) return fail(ctx, TPC_EINVAL, "events pointer is NULL");
+    if (int rc = check_geometry(ctx, s, g)) return rc;
+    if (!std::isfinite(bz)) return fail(ctx, TPC_EINVAL, "bz not finite");
+    const int n_sec = g->n_sectors_phi * (g->split_z ? 2 : 1);
+    long long n_total = 0;
+    for (int i = 0; i < n_ev; ++i) {
+        if (ev[i].n < 0) return fail(ctx, TPC_EINVAL, "negative cluster count");
+        if (ev[i].n > 0 && (!ev[i].y || !ev[i].z || !ev[i].row || !ev[i].sector))
+            return fail(ctx, TPC_EINVAL, "NULL cluster array");
+        n_total += ev[i].n;
+    }
+    if (n_total > s.caps.n)
+        return fail(ctx, TPC_EINVAL, "clusters in the launch exceed max_clusters_per_event");
+    const int S = n_sec * n_ev;
+    if (S > s.caps.s) return fail(ctx, TPC_EINVAL, "sectors in the launch exceed the arena");
+    LaunchInfo& I = s.info;
+    I = LaunchInfo();
+    I.n_ev = n_ev;
+    I.S = S;
+    I.R = g->n_rows;
+    // descriptor tables
+    EventDesc* dh = (EventDesc*)s.desc_host;
+    long long* offh = (long long*)((char*)s.desc_host + sizeof(EventDesc) * s.caps.e);
+    int* sech = (int*)((char*)offh + sizeof(long long) * (s.caps.e + 1));
+    long long off = 0;
+    for (int i = 0; i < n_ev; ++i) {
+        EventDesc d;
+        if (ev[i].on_device || ev[i].n == 0) {
+            d.y = ev[i].y;
+            d.z = ev[i].z;
+            d.row = ev[i].row;
+            d.sec = ev[i].sector;
+        } else {
+            d.y = s.in_y + off;
+            d.z = s.in_z + off;
+            d.row = s.in_row + off;
+            d.sec = s.in_sec + off;
+        }
+        d.n = ev[i].n;
+        d.cl_off = off;
+        d.sec_base = i * n_sec;
+        d.n_sec = n_sec;
+        dh[i] = d;
+        offh[i] = off;
+        I.ev_n.push_back(ev[i].n);
+        I.ev_sec_base.push_back(i * n_sec);
+        I.ev_n_sec.push_back(n_sec);
+        for (int k = 0; k < n_sec; ++k) sech[i * n_sec + k] = i;
+        off += ev[i].n;
+    }
+    offh[n_ev] = off;
+    // launch record
+    Launch& L = I.L;
+    std::memset(&L, 0, sizeof(L));
+    L.n_total = n_total;
+    L.n_events = n_ev;
+    L.R = g->n_rows;
+    L.S = S;
+    L.RS = S * g->n_rows;
+    L.n_sectors_phi = g->n_sectors_phi;
+    L.split_z = g->split_z ? 1 : 0;
+    L.t_cap = s.caps.t;
+    L.tan_half = tanf(g->half_angle_rad);
+    L.z_max = g->z_max;
+    L.kB = (float)(kKappa * (double)bz);
+    for (int r = 0; r < g->n_rows; ++r) L.row_x[r] = g->row_x[r];
+    const tpc_track_params& P = ctx->cfg.params;
+    L.sy2 = P.meas_sigma_y * P.meas_sigma_y;
+    L.sz2 = P.meas_sigma_z * P.meas_sigma_z;
+    L.slope_win_y = P.slope_win_y;
+    L.slope_win_z = P.slope_win_z;
+    L.d_max = P.d_max;
+    L.chi2_hit = P.chi2_hit;
+    L.sin_max = P.sin_max;
+    L.edge_margin = P.edge_margin;
+    L.seed_var_s = P.seed_var_s;
+    L.seed_var_t = P.seed_var_t;
+    L.seed_var_q = P.seed_var_q;
+    L.max_gap = P.max_gap;
+    L.min_chain = P.min_chain;
+    L.min_tracklet_hits = P.min_tracklet_hits;
+    L.min_track_hits = P.min_track_hits;
+    L.ev = (EventDesc*)s.desc_dev;
+    L.ev_off = (long long*)((char*)s.desc_dev + sizeof(EventDesc) * s.caps.e);
+    L.sec_event = (int*)((char*)L.ev_off + sizeof(long long) * (s.caps.e + 1));
+    // zero region laid out for this launch
+    {
+        size_t zo = 0;
+        auto take = [&](size_t bytes) {
+            zo = align_up(zo, 16);
+            char* p = s.zero_dev + zo;
+            zo += bytes;
+            return p;
+        };
+        L.cnt = (Counters*)take(sizeof(Counters));
+        L.row_cnt = (int*)take(4 * (size_t)L.RS);
+        L.row_fill = (int*)take(4 * (size_t)L.RS);
+        L.sec_first = (int*)take(4 * (size_t)S);
+        L.sec_end = (int*)take(4 * (size_t)S);
+        L.n_row_tiles = (int)((L.RS + kTileRows - 1) / kTileRows);
+        if (L.n_row_tiles < 1) L.n_row_tiles = 1;
+        L.n_hit_tiles = (int)((n_total + kTileHits - 1) / kTileHits);
+        if (L.n_hit_tiles < 1) L.n_hit_tiles = 1;
+        L.tile_state = (unsigned long long*)take(8 * ((size_t)L.n_row_tiles + L.n_hit_tiles + S));
+        zo = align_up(zo, 16);
+        if (zo > s.zero_cap) return fail(ctx, TPC_EINVAL, "internal: zero region too small");
+        CUDA_TRY(ctx, cudaMemsetAsync(s.zero_dev, 0, zo, s.stream));
+    }
+    L.row_off = s.row_off;
+    L.grid = s.grid;
+    L.tmp_y = s.tmp_y;
+    L.tmp_z = s.tmp_z;
+    L.tmp_cid = s.tmp_cid;
+    L.hy = s.hy;
+    L.hz = s.hz;
+    L.hcid = s.hcid;
+    L.hrow = s.hrow;
+    L.bin_start = s.bin_start;
+    L.up = s.up;
+    L.dn = s.dn;
+    L.upc = s.upc;
+    L.dnc = s.dnc;
+    L.weight = s.weight;
+    L.starts = s.starts;
+    L.tl = s.tl;
+    L.tl_rowhit = s.tl_rowhit;
+    L.tl_key = s.tl_key;
+    L.tl_nown = s.tl_nown;
+    L.tl_out = s.tl_out;
+    L.tl_hitoff = s.tl_hitoff;
+    L.sec_trk_off = s.sec_trk_off;
+    L.sec_hit_off = s.sec_hit_off;
+    L.k_sector = s.k_sector;
+    L.k_x = s.k_x;
+    L.k_param = s.k_param;
+    L.k_cov = s.k_cov;
+    L.k_chi2 = s.k_chi2;
+    L.k_ndf = s.k_ndf;
+    L.k_hit_off = s.k_hit_off;
+    L.k_hit_cid = s.k_hit_cid;
+    // inputs
+    CUDA_TRY(ctx, cudaMemcpyAsync(s.desc_dev, s.desc_host, s.desc_bytes, cudaMemcpyHostToDevice, s.stream));
+    for (int i = 0; i < n_ev; ++i) {
+        if (ev[i].on_device || ev[i].n == 0) continue;
+        const size_t n = (size_t)ev[i].n;
+        const long long o = dh[i].cl_off;
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.in_y + o, ev[i].y, 4 * n, cudaMemcpyHostToDevice, s.stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.in_z + o, ev[i].z, 4 * n, cudaMemcpyHostToDevice, s.stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.in_row + o, ev[i].row, 2 * n, cudaMemcpyHostToDevice, s.stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.in_sec + o, ev[i].sector, 2 * n, cudaMemcpyHostToDevice, s.stream));
+    }
+    launch_binning(L, s.stream);
+    launch_finder(L, s.stream);
+    launch_constructor(L, s.stream);
+    launch_selector(L, s.stream);
+    CUDA_TRY(ctx, cudaGetLastError());
+    CUDA_TRY(ctx, cudaMemcpyAsync(s.cnt_host, L.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s.stream));
+    CUDA_TRY(ctx, cudaEventRecord(s.done_ev, s.stream));
+    I.pending = true;
+    return TPC_OK;
+}
+
+// Wait for the slot's launch, check the device status, copy the results.
+int collect(tpc_track_ctx* ctx, Slot& s)
+{
+    LaunchInfo& I = s.info;
+    if (!I.pending) return fail(ctx, TPC_EINVAL, "no launch pending");
+    I.pending = false;
+    CUDA_TRY(ctx, cudaEventSynchronize(s.done_ev));
+    CUDA_TRY(ctx, cudaGetLastError());
+    const Counters& c = *s.cnt_host;
+    s.tracks.assign(I.n_ev, tpc_tracks{});
+    if (c.n_invalid) return fail(ctx, TPC_EINVAL, std::to_string(c.n_invalid) + " invalid clusters (row, sector or coordinate)");
+    if (c.timeout) return fail(ctx, TPC_ETIMEOUT, "a bounded device wait gave up");
+    if (c.ovf_row) return fail(ctx, TPC_ECAPACITY, "a pad row holds more than 4096 clusters");
+    if (c.ovf_tracklets || c.n_starts > s.caps.t)
+        return fail(ctx, TPC_ECAPACITY, "start hits exceed the tracklet slots");
+    if (c.ovf_sector) return fail(ctx, TPC_ECAPACITY, "a sector emits more than 4096 tracks");
+    const int nt = c.n_tracks, nh = c.n_track_hits;
+    cudaStream_t st = s.stream;
+    if (nt > 0) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sector, s.k_sector, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.x, s.k_x, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.param, s.k_param, 20 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.cov, s.k_cov, 60 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.chi2, s.k_chi2, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.ndf, s.k_ndf, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.hit_off, s.k_hit_off, 4 * ((size_t)nt + 1), cudaMemcpyDeviceToHost, st));
+    }
+    if (nh > 0)
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.hit_cid, s.k_hit_cid, 4 * (size_t)nh, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_trk_off, s.sec_trk_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    // split per event (sectors of an event are contiguous, so are its tracks)
+    int32_t* eho = s.out.ev_hit_off;
+    for (int e = 0; e < I.n_ev; ++e) {
+        const int t0 = nt > 0 ? s.out.sec_trk_off[I.ev_sec_base[e]] : 0;
+        const int t1 = nt > 0 ? s.out.sec_trk_off[I.ev_sec_base[e] + I.ev_n_sec[e]] : 0;
+        const int h0 = nt > 0 ? s.out.hit_off[t0] : 0;
+        tpc_tracks& T = s.tracks[e];
+        T.n_tracks = t1 - t0;
+        T.sector = s.out.sector + t0;
+        T.x = s.out.x + t0;
+        T.param = s.out.param + 5 * (size_t)t0;
+        T.cov = s.out.cov + 15 * (size_t)t0;
+        T.chi2 = s.out.chi2 + t0;
+        T.ndf = s.out.ndf + t0;
+        T.hit_cid = s.out.hit_cid + h0;
+        for (int j = t0; j <= t1; ++j) eho[j - t0] = (nt > 0 ? s.out.hit_off[j] : 0) - h0;
+        T.hit_off = eho;
+        eho += (t1 - t0) + 1;
+    }
+    tpc_track_counters& K = I.counters;
+    K.n_clusters = 0;
+    for (long long n : I.ev_n) K.n_clusters += n;
+    K.n_rows_total = (int64_t)I.S * I.R;
+    K.n_bins = c.n_bins;
+    K.n_links = c.n_links;
+    K.n_starts = c.n_starts;
+    K.n_tracklets = c.n_tracklets;
+    K.n_valid_tracklets = c.n_valid;
+    K.n_tracklet_hits = c.n_tracklet_hits;
+    K.n_tracks = nt;
+    K.n_track_hits = nh;
+    I.done = true;
+    return TPC_OK;
+}
+
+// --------------------------------------------------------------------------
+// debug dumps (event 0 of the last completed launch)
+// --------------------------------------------------------------------------
+int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* used)
+{
+    LaunchInfo& I = s.info;
+    if (!I.done) return fail(ctx, TPC_EINVAL, "no completed launch to dump");
+    const int R = I.R;
+    const int RS0 = I.ev_n_sec[0] * R;  // rows of event 0 (sectors first in the layout)
+    const long long n0 = I.ev_n[0];
+    std::vector<int> row_off(RS0 + 1);
+    CUDA_TRY(ctx, cudaMemcpy(row_off.data(), s.row_off, 4 * (RS0 + 1), cudaMemcpyDeviceToHost));
+    const int nh = row_off[RS0];  // sorted hits of event 0
+    std::vector<int> hcid(nh), hrow(nh);
+    if (nh) {
+        CUDA_TRY(ctx, cudaMemcpy(hcid.data(), s.hcid, 4 * (size_t)nh, cudaMemcpyDeviceToHost));
+        CUDA_TRY(ctx, cudaMemcpy(hrow.data(), s.hrow, 4 * (size_t)nh, cudaMemcpyDeviceToHost));
+    }
+    auto row_of = [&](int i) { return (hrow[i] >> 8) * R + (hrow[i] & 255); };
+    std::vector<char> out;
+    auto put = [&](const void* p, size_t b) {
+        const char* c = (const char*)p;
+        out.insert(out.end(), c, c + b);
+    };
+    if (stage == TPC_DUMP_SORTED) {
+        put(hcid.data(), 4 * (size_t)nh);
+    } else if (stage == TPC_DUMP_LINKS || stage == TPC_DUMP_CLEAN) {
+        std::vector<int16_t> u(nh), d(nh);
+        if (nh) {
+            CUDA_TRY(ctx, cudaMemcpy(u.data(), stage == TPC_DUMP_LINKS ? s.up : s.upc, 2 * (size_t)nh, cudaMemcpyDeviceToHost));
+            CUDA_TRY(ctx, cudaMemcpy(d.data(), stage == TPC_DUMP_LINKS ? s.dn : s.dnc, 2 * (size_t)nh, cudaMemcpyDeviceToHost));
+        }
+        std::vector<int32_t> uc(n0, -1), dc(n0, -1);
+        for (int i = 0; i < nh; ++i) {
+            const int g = row_of(i);
+            if (u[i] >= 0) uc[hcid[i]] = hcid[row_off[g + 1] + u[i]];
+            if (d[i] >= 0) dc[hcid[i]] = hcid[row_off[g - 1] + d[i]];
+        }
+        put(uc.data(), 4 * (size_t)n0);
+        put(dc.data(), 4 * (size_t)n0);
+    } else if (stage == TPC_DUMP_STARTS || stage == TPC_DUMP_TRACKLETS) {
+        const int ns = std::min<int>(s.cnt_host->n_starts, s.caps.t);
+        std::vector<int> st(ns);
+        std::vector<TrackletHdr> tl(ns);
+        if (ns) {
+            CUDA_TRY(ctx, cudaMemcpy(st.data(), s.starts, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+            CUDA_TRY(ctx, cudaMemcpy(tl.data(), s.tl, sizeof(TrackletHdr) * (size_t)ns, cudaMemcpyDeviceToHost));
+        }
+        std::vector<std::pair<int, int>> order;  // (start cid, tracklet) of event 0
+        for (int t = 0; t < ns; ++t)
+            if (st[t] < nh) order.push_back({hcid[st[t]], t});
+        std::sort(order.begin(), order.end());
+        if (stage == TPC_DUMP_STARTS) {
+            for (auto& o : order) put(&o.first, 4);
+        } else {
+            std::vector<int16_t> rh((size_t)R);
+            int32_t count = 0;
+            for (auto& o : order)
+                if (tl[o.second].chain_len >= ctx->cfg.params.min_chain) ++count;
+            put(&count, 4);
+            for (auto& o : order) {
+                const TrackletHdr& H = tl[o.second];
+                if (H.chain_len < ctx->cfg.params.min_chain) continue;
+                tpc_dump_tracklet D;
+                std::memset(&D, 0, sizeof(D));
+                D.start_cid = o.first;
+                D.sector = hrow[H.start] >> 8;
+                D.valid = H.valid;
+                D.nhits = H.nhits;
+                D.first_row = H.first;
+                D.last_row = H.last;
+                D.ndf = H.ndf;
+                D.x = H.x;
+                std::memcpy(D.param, H.p, sizeof(D.param));
+                std::memcpy(D.cov, H.C, sizeof(D.cov));
+                D.chi2 = H.chi2;
+                put(&D, sizeof(D));
+                CUDA_TRY(ctx, cudaMemcpy(rh.data(), s.tl_rowhit + (size_t)o.second * R, 2 * (size_t)R, cudaMemcpyDeviceToHost));
+                std::vector<int32_t> rc(R, -1);
+                const int gbase = D.sector * R;
+                for (int r = H.first; r <= H.last && r >= 0; ++r)
+                    if (rh[r] >= 0) rc[r] = hcid[row_off[gbase + r] + rh[r]];
+                put(rc.data(), 4 * (size_t)R);
+            }
+        }
+    } else if (stage == TPC_DUMP_WEIGHTS) {
+        std::vector<unsigned long long> w(nh);
+        if (nh) CUDA_TRY(ctx, cudaMemcpy(w.data(), s.weight, 8 * (size_t)nh, cudaMemcpyDeviceToHost));
+        std::vector<unsigned long long> wc(n0, 0ULL);
+        for (int i = 0; i < nh; ++i) wc[hcid[i]] = w[i];
+        put(wc.data(), 8 * (size_t)n0);
+    } else {
+        return fail(ctx, TPC_EINVAL, "unknown dump stage");
+    }
+    if (used) *used = out.size();
+    if (buf && cap > 0) std::memcpy(buf, out.data(), std::min(cap, out.size()));
+    return TPC_OK;
+}
+
+// --------------------------------------------------------------------------
+// served form: one worker per slot pulls what fits into its next launch
+// --------------------------------------------------------------------------
+void worker(tpc_track_ctx* ctx, Slot* s)
+{
+    cudaSetDevice(ctx->cfg.device);
+    for (;;) {
+        std::vector<Request> batch;
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu);
+            ctx->cv_req.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
+            if (ctx->stop && ctx->queue.empty()) return;
+            long long sum = 0;
+            while (!ctx->queue.empty() && (int)batch.size() < s->caps.e) {
+                Request& q = ctx->queue.front();
+                if (!batch.empty()) {
+                    const Request& b0 = batch.front();
+                    const bool same = q.bz == b0.bz && q.geom.n_rows == b0.geom.n_rows &&
+                                      q.geom.n_sectors_phi == b0.geom.n_sectors_phi &&
+                                      q.geom.split_z == b0.geom.split_z &&
+                                      q.geom.half_angle_rad == b0.geom.half_angle_rad &&
+                                      q.geom.z_max == b0.geom.z_max && q.row_x == b0.row_x;
+                    if (!same || sum + q.ev.n > s->caps.n) break;
+                }
+                sum += q.ev.n;
+                batch.push_back(std::move(q));
+                ctx->queue.pop_front();
+            }
+        }
+        std::vector<tpc_clusters> evs;
+        for (auto& q : batch) evs.push_back(q.ev);
+        tpc_geometry g = batch.front().geom;
+        g.row_x = batch.front().row_x.data();
+        int rc = enqueue(ctx, *s, (int)evs.size(), evs.data(), &g, batch.front().bz);
+        if (rc == TPC_OK) rc = collect(ctx, *s);
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (size_t i = 0; i < batch.size(); ++i) {
+            auto it = ctx->results.find(batch[i].ticket);
+            if (it == ctx->results.end()) continue;
+            TicketResult& R = *it->second;
+            if (rc == TPC_OK) {
+                const tpc_tracks& T = s->tracks[i];
+                const size_t n = (size_t)T.n_tracks;
+                const size_t nh = n ? (size_t)T.hit_off[n] : 0;
+                R.sector.assign(T.sector, T.sector + n);
+                R.x.assign(T.x, T.x + n);
+                R.param.assign(T.param, T.param + 5 * n);
+                R.cov.assign(T.cov, T.cov + 15 * n);
+                R.chi2.assign(T.chi2, T.chi2 + n);
+                R.ndf.assign(T.ndf, T.ndf + n);
+                R.hit_off.assign(T.hit_off, T.hit_off + n + 1);
+                R.hit_cid.assign(T.hit_cid, T.hit_cid + nh);
+                R.view.n_tracks = (int64_t)n;
+                R.view.sector = R.sector.data();
+                R.view.x = R.x.data();
+                R.view.param = R.param.data();
+                R.view.cov = R.cov.data();
+                R.view.chi2 = R.chi2.data();
+                R.view.ndf = R.ndf.data();
+                R.view.hit_off = R.hit_off.data();
+                R.view.hit_cid = R.hit_cid.data();
+            }
+            R.status = rc;
+        }
+        ctx->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace tpc
+
+using namespace tpc;
+
+extern "C" {
+
+void tpc_track_default_params(tpc_track_params* p)
+{
+    if (!p) return;
+    p->meas_sigma_y = 0.1f;
+    p->meas_sigma_z = 0.1f;
+    p->slope_win_y = 2.0f;
+    p->slope_win_z = 2.0f;
+    p->d_max = 0.36f;
+    p->chi2_hit = 16.0f;
+    p->max_gap = 5;
+    p->min_chain = 3;
+    p->min_tracklet_hits = 10;
+    p->min_track_hits = 10;
+    p->sin_max = 0.99f;
+    p->edge_margin = 2.0f;
+    p->seed_var_s = 1.0f;
+    p->seed_var_t = 1.0f;
+    p->seed_var_q = 100.0f;
+}
+
+int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out)
+{
+    if (!out) return TPC_EINVAL;
+    *out = nullptr;
+    if (!cfg) return TPC_EINVAL;
+    if (cfg->max_clusters_per_event <= 0 || cfg->max_clusters_per_event > (1LL << 29) ||
+        cfg->max_events_in_flight < 1 || cfg->max_events_in_flight > 16 ||
+        cfg->max_rows < 0 || cfg->max_rows > kMaxRows || cfg->max_events_per_launch < 0 ||
+        cfg->max_events_per_launch > kMaxEventsPerLaunch)
+        return TPC_EINVAL;
+    const tpc_track_params& P = cfg->params;
+    if (!(P.meas_sigma_y > 0) || !(P.meas_sigma_z > 0) || !(P.d_max >= 0) || !(P.chi2_hit > 0) ||
+        P.max_gap < 1 || P.min_chain < 2 || P.min_tracklet_hits < 1 || P.min_track_hits < 1 ||
+        !(P.sin_max > 0 && P.sin_max < 1) || !(P.seed_var_s > 0) || !(P.seed_var_t > 0) ||
+        !(P.seed_var_q > 0))
+        return TPC_EINVAL;
+    auto ctx = std::make_unique<tpc_track_ctx>();
+    ctx->cfg = *cfg;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) {
+        cudaGetLastError();
+        return TPC_ECUDA;
+    }
+    const int n_slots = cfg->max_events_in_flight;
+    size_t total = 0;
+    for (int i = 0; i < n_slots; ++i) {
+        auto s = std::make_unique<Slot>();
+        s->id = i;
+        s->caps = make_caps(*cfg);
+        total += layout(*s, nullptr);
+        ctx->slots.push_back(std::move(s));
+    }
+    if (cfg->mem_budget && total > cfg->mem_budget) return TPC_ENOMEM;
+    for (auto& s : ctx->slots) {
+        int rc = alloc_slot(ctx.get(), *s);
+        if (rc == TPC_OK) {
+            if (s->id == 0 && cfg->cuda_stream) {
+                s->stream = (cudaStream_t)cfg->cuda_stream;
+            } else if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess) {
+                s->own_stream = true;
+            } else {
+                rc = TPC_ECUDA;
+            }
+        }
+        if (rc != TPC_OK) {
+            for (auto& t : ctx->slots) free_slot(*t);
+            return rc;
+        }
+    }
+    *out = ctx.release();
+    return TPC_OK;
+}
+
+int tpc_track_launch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev, const tpc_geometry* geom,
+                     float bz)
+{
+    if (!ctx) return TPC_EINVAL;
+    if (!ctx->workers.empty()) return fail(ctx, TPC_EBUSY, "context is serving submitted events");
+    cudaSetDevice(ctx->cfg.device);
+    Slot& s = *ctx->slots[0];
+    if (s.info.pending) {
+        cudaEventSynchronize(s.done_ev);
+        s.info.pending = false;
+    }
+    return enqueue(ctx, s, n_ev, ev, geom, bz);
+}
+
+int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs)
+{
+    if (!ctx) return TPC_EINVAL;
+    cudaSetDevice(ctx->cfg.device);
+    Slot& s = *ctx->slots[0];
+    const int n_ev = s.info.n_ev;
+    int rc = collect(ctx, s);
+    if (outs)
+        for (int e = 0; e < n_ev; ++e) outs[e] = rc == TPC_OK ? s.tracks[e] : tpc_tracks{};
+    return rc;
+}
+
+int tpc_track_batch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev, const tpc_geometry* geom,
+                    float bz, tpc_tracks* outs)
+{
+    int rc = tpc_track_launch(ctx, n_ev, ev, geom, bz);
+    if (rc != TPC_OK) {
+        if (outs && ctx)
+            for (int e = 0; e < n_ev; ++e) outs[e] = tpc_tracks{};
+        return rc;
+    }
+    return tpc_track_results(ctx, outs);
+}
+
+int tpc_track_event(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geometry* geom, float bz,
+                    tpc_tracks* out)
+{
+    return tpc_track_batch(ctx, 1, ev, geom, bz, out);
+}
+
+int tpc_track_submit(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geometry* geom, float bz,
+                     uint64_t* ticket)
+{
+    if (!ctx || !ev || !ticket) return TPC_EINVAL;
+    if (int rc = check_geometry(ctx, *ctx->slots[0], geom)) return rc;
+    if (ev->n < 0 || ev->n > ctx->slots[0]->caps.n)
+        return fail(ctx, TPC_EINVAL, "event larger than one slot");
+    if (ev->n > 0 && (!ev->y || !ev->z || !ev->row || !ev->sector))
+        return fail(ctx, TPC_EINVAL, "NULL cluster array");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->workers.empty()) {
+        for (auto& s : ctx->slots) {
+            if (s->info.pending) {
+                cudaEventSynchronize(s->done_ev);
+                s->info.pending = false;
+            }
+            ctx->workers.emplace_back(worker, ctx, s.get());
+        }
+    }
+    Request q;
+    q.ticket = ctx->next_ticket++;
+    q.ev = *ev;
+    q.row_x.assign(geom->row_x, geom->row_x + geom->n_rows);
+    q.geom = *geom;
+    q.bz = bz;
+    q.t_submit = std::chrono::steady_clock::now();
+    ctx->results[q.ticket] = std::make_unique<TicketResult>();
+    *ticket = q.ticket;
+    ctx->queue.push_back(std::move(q));
+    ctx->cv_req.notify_one();
+    return TPC_OK;
+}
+
+int tpc_track_poll(tpc_track_ctx* ctx, uint64_t ticket, int timeout_us, tpc_tracks* out)
+{
+    if (!ctx) return TPC_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto it = ctx->results.find(ticket);
+    if (it == ctx->results.end()) return fail(ctx, TPC_EINVAL, "unknown ticket");
+    TicketResult* R = it->second.get();
+    auto ready = [&] { return R->status != TPC_EBUSY; };
+    if (timeout_us < 0) ctx->cv_done.wait(lk, ready);
+    else if (timeout_us > 0) ctx->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+    if (!ready()) return TPC_EBUSY;
+    if (out) *out = R->status == TPC_OK ? R->view : tpc_tracks{};
+    return R->status;
+}
+
+int tpc_track_release(tpc_track_ctx* ctx, uint64_t ticket)
+{
+    if (!ctx) return TPC_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->results.find(ticket);
+    if (it == ctx->results.end()) return fail(ctx, TPC_EINVAL, "unknown ticket");
+    if (it->second->status == TPC_EBUSY) return fail(ctx, TPC_EBUSY, "ticket still in flight");
+    ctx->results.erase(it);
+    return TPC_OK;
+}
+
+int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c)
+{
+    if (!ctx || !c) return TPC_EINVAL;
+    *c = ctx->slots[0]->info.counters;
+    return TPC_OK;
+}
+
+void* tpc_track_stream(const tpc_track_ctx* ctx) { return ctx ? (void*)ctx->slots[0]->stream : nullptr; }
+
+int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t cap, size_t* used)
+{
+    if (!ctx) return TPC_EINVAL;
+    cudaSetDevice(ctx->cfg.device);
+    return dump(ctx, *ctx->slots[0], stage, host_buf, cap, used);
+}
+
+const char* tpc_track_last_error(const tpc_track_ctx* ctx)
+{
+    if (!ctx) return "NULL context";
+    return ctx->err.c_str();
+}
+
+void tpc_track_destroy(tpc_track_ctx* ctx)
+{
+    if (!ctx) return;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->stop = true;
+    }
+    ctx->cv_req.notify_all();
+    for (auto& t : ctx->workers) t.join();
+    cudaSetDevice(ctx->cfg.device);
+    for (auto& s : ctx->slots) free_slot(*s);
+    delete ctx;
+}
+
+}  // extern "C"

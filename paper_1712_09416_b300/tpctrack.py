@@ -1,0 +1,372 @@
+"""Thin ctypes binding of libtpctrack.so (argument marshalling only).
+
+The functions carry the names of the C ABI in ``include/tpctrack.h``; every
+step of the tracking path runs in the library's CUDA kernels.  Inputs may be
+numpy arrays (host memory) or CUDA torch tensors (device memory); outputs are
+copied into numpy arrays.  Loading fails loudly if the library is missing: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtpctrack.so")
+
+TPC_OK, TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ECAPACITY, TPC_ETIMEOUT, TPC_EBUSY = 0, -1, -2, -3, -4, -5, -6
+TPC_DUMP_LINKS, TPC_DUMP_CLEAN, TPC_DUMP_STARTS, TPC_DUMP_TRACKLETS, TPC_DUMP_WEIGHTS, TPC_DUMP_SORTED = 1, 2, 3, 4, 5, 6
+
+EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "tpc_track_batch",
+            "tpc_track_launch", "tpc_track_results", "tpc_track_submit", "tpc_track_poll",
+            "tpc_track_release", "tpc_track_get_counters", "tpc_track_stream",
+            "tpc_track_debug_dump", "tpc_track_last_error", "tpc_track_destroy"]
+
+
+class TpcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tpctrack error {code}: {msg}")
+        self.code = code
+
+
+class tpc_geometry(C.Structure):
+    _fields_ = [("n_rows", C.c_int), ("row_x", C.POINTER(C.c_float)), ("n_sectors_phi", C.c_int),
+                ("split_z", C.c_int), ("half_angle_rad", C.c_float), ("z_max", C.c_float)]
+
+
+class tpc_clusters(C.Structure):
+    _fields_ = [("n", C.c_int64), ("y", C.c_void_p), ("z", C.c_void_p), ("row", C.c_void_p),
+                ("sector", C.c_void_p), ("on_device", C.c_int)]
+
+
+class tpc_tracks(C.Structure):
+    _fields_ = [("n_tracks", C.c_int64), ("sector", C.POINTER(C.c_int32)),
+                ("x", C.POINTER(C.c_float)), ("param", C.POINTER(C.c_float)),
+                ("cov", C.POINTER(C.c_float)), ("chi2", C.POINTER(C.c_float)),
+                ("ndf", C.POINTER(C.c_int32)), ("hit_off", C.POINTER(C.c_int32)),
+                ("hit_cid", C.POINTER(C.c_int32))]
+
+
+class tpc_track_params(C.Structure):
+    _fields_ = [("meas_sigma_y", C.c_float), ("meas_sigma_z", C.c_float),
+                ("slope_win_y", C.c_float), ("slope_win_z", C.c_float), ("d_max", C.c_float),
+                ("chi2_hit", C.c_float), ("max_gap", C.c_int), ("min_chain", C.c_int),
+                ("min_tracklet_hits", C.c_int), ("min_track_hits", C.c_int),
+                ("sin_max", C.c_float), ("edge_margin", C.c_float), ("seed_var_s", C.c_float),
+                ("seed_var_t", C.c_float), ("seed_var_q", C.c_float)]
+
+
+class tpc_track_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("mem_budget", C.c_size_t),
+                ("max_clusters_per_event", C.c_int64), ("max_events_in_flight", C.c_int),
+                ("cuda_stream", C.c_void_p), ("max_rows", C.c_int),
+                ("max_events_per_launch", C.c_int), ("params", tpc_track_params)]
+
+
+class tpc_track_counters(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in (
+        "n_clusters", "n_rows_total", "n_bins", "n_links", "n_starts", "n_tracklets",
+        "n_valid_tracklets", "n_tracklet_hits", "n_tracks", "n_track_hits")]
+
+
+class tpc_dump_tracklet(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("start_cid", "sector", "valid", "nhits", "first_row",
+                                         "last_row", "ndf", "pad")] + \
+        [("x", C.c_float), ("param", C.c_float * 5), ("cov", C.c_float * 15), ("chi2", C.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libtpctrack.so (it must have been built; see build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1712_09416_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.tpc_track_create.argtypes = [C.POINTER(tpc_track_config), C.POINTER(P)]
+        L.tpc_track_event.argtypes = [P, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry), C.c_float,
+                                      C.POINTER(tpc_tracks)]
+        L.tpc_track_batch.argtypes = [P, C.c_int, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry),
+                                      C.c_float, C.POINTER(tpc_tracks)]
+        L.tpc_track_launch.argtypes = [P, C.c_int, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry),
+                                       C.c_float]
+        L.tpc_track_results.argtypes = [P, C.POINTER(tpc_tracks)]
+        L.tpc_track_submit.argtypes = [P, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry), C.c_float,
+                                       C.POINTER(C.c_uint64)]
+        L.tpc_track_poll.argtypes = [P, C.c_uint64, C.c_int, C.POINTER(tpc_tracks)]
+        L.tpc_track_release.argtypes = [P, C.c_uint64]
+        L.tpc_track_get_counters.argtypes = [P, C.POINTER(tpc_track_counters)]
+        L.tpc_track_stream.argtypes = [P]
+        L.tpc_track_stream.restype = P
+        L.tpc_track_debug_dump.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.tpc_track_last_error.argtypes = [P]
+        L.tpc_track_last_error.restype = C.c_char_p
+        L.tpc_track_destroy.argtypes = [P]
+        L.tpc_track_destroy.restype = None
+        L.tpc_track_default_params.argtypes = [C.POINTER(tpc_track_params)]
+        L.tpc_track_default_params.restype = None
+        _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+
+def geometry_of(ev) -> tuple[tpc_geometry, np.ndarray]:
+    """tpc_geometry of an event record (row_x kept alive by the caller)."""
+    row_x = np.ascontiguousarray(ev.row_x, dtype=np.float32)
+    g = tpc_geometry(len(row_x), row_x.ctypes.data_as(C.POINTER(C.c_float)), int(ev.n_sectors_phi),
+                     int(ev.split_z), float(ev.half_angle), float(ev.z_max))
+    return g, row_x
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def clusters_of(y, z, row, sector) -> tuple[tpc_clusters, list]:
+    """tpc_clusters for numpy (host) or CUDA torch (device) arrays."""
+    if _is_torch(y):
+        import torch
+        keep = [y.contiguous(), z.contiguous(), row.contiguous(), sector.contiguous()]
+        assert keep[0].dtype == torch.float32 and keep[1].dtype == torch.float32
+        assert keep[2].dtype in (torch.int16, torch.uint16) and keep[3].dtype in (torch.int16, torch.uint16)
+        on_dev = 1 if keep[0].is_cuda else 0
+        ptrs = [k.data_ptr() for k in keep]
+        n = keep[0].numel()
+    else:
+        keep = [np.ascontiguousarray(y, dtype=np.float32), np.ascontiguousarray(z, dtype=np.float32),
+                np.ascontiguousarray(row, dtype=np.uint16), np.ascontiguousarray(sector, dtype=np.uint16)]
+        on_dev = 0
+        ptrs = [k.ctypes.data for k in keep]
+        n = len(keep[0])
+    c = tpc_clusters(n, ptrs[0], ptrs[1], ptrs[2], ptrs[3], on_dev)
+    return c, keep
+
+
+@dataclass
+class Tracks:
+    sector: np.ndarray
+    x: np.ndarray
+    param: np.ndarray
+    cov: np.ndarray
+    chi2: np.ndarray
+    ndf: np.ndarray
+    hit_off: np.ndarray
+    hit_cid: np.ndarray
+
+    @property
+    def n_tracks(self) -> int:
+        return len(self.sector)
+
+    def hits(self, j: int) -> np.ndarray:
+        return self.hit_cid[self.hit_off[j]:self.hit_off[j + 1]]
+
+
+def tracks_to_numpy(t: tpc_tracks) -> Tracks:
+    n = int(t.n_tracks)
+
+    def arr(p, count, dt):
+        if count == 0 or not p:
+            return np.zeros(count, dtype=dt)
+        return np.ctypeslib.as_array(p, shape=(count,)).astype(dt, copy=True)
+    hit_off = arr(t.hit_off, n + 1, np.int32) if n else np.zeros(1, np.int32)
+    nh = int(hit_off[-1]) if n else 0
+    return Tracks(sector=arr(t.sector, n, np.int32), x=arr(t.x, n, np.float32),
+                  param=arr(t.param, 5 * n, np.float32).reshape(n, 5),
+                  cov=arr(t.cov, 15 * n, np.float32).reshape(n, 15),
+                  chi2=arr(t.chi2, n, np.float32), ndf=arr(t.ndf, n, np.int32), hit_off=hit_off,
+                  hit_cid=arr(t.hit_cid, nh, np.int32))
+
+
+def _check(ctx, rc: int):
+    if rc != TPC_OK:
+        msg = lib().tpc_track_last_error(ctx).decode() if ctx else ""
+        raise TpcError(rc, msg)
+
+
+# --------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# --------------------------------------------------------------------------
+
+def tpc_track_default_params() -> tpc_track_params:
+    p = tpc_track_params()
+    lib().tpc_track_default_params(C.byref(p))
+    return p
+
+
+def tpc_track_create(max_clusters_per_event: int, *, device: int = 0, mem_budget: int = 0,
+                     max_events_in_flight: int = 1, cuda_stream: int | None = None,
+                     max_rows: int = 159, max_events_per_launch: int = 64,
+                     params: tpc_track_params | None = None):
+    cfg = tpc_track_config()
+    cfg.device = device
+    cfg.mem_budget = mem_budget
+    cfg.max_clusters_per_event = int(max_clusters_per_event)
+    cfg.max_events_in_flight = max_events_in_flight
+    cfg.cuda_stream = cuda_stream
+    cfg.max_rows = max_rows
+    cfg.max_events_per_launch = max_events_per_launch
+    cfg.params = params if params is not None else tpc_track_default_params()
+    ctx = C.c_void_p()
+    rc = lib().tpc_track_create(C.byref(cfg), C.byref(ctx))
+    if rc != TPC_OK:
+        raise TpcError(rc, "tpc_track_create failed")
+    return ctx
+
+
+def tpc_track_event(ctx, clusters: tpc_clusters, geom: tpc_geometry, bz: float) -> Tracks:
+    out = tpc_tracks()
+    _check(ctx, lib().tpc_track_event(ctx, C.byref(clusters), C.byref(geom), bz, C.byref(out)))
+    return tracks_to_numpy(out)
+
+
+def tpc_track_batch(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz: float) -> list[Tracks]:
+    arr = (tpc_clusters * len(clusters))(*clusters)
+    outs = (tpc_tracks * len(clusters))()
+    _check(ctx, lib().tpc_track_batch(ctx, len(clusters), arr, C.byref(geom), bz, outs))
+    return [tracks_to_numpy(o) for o in outs]
+
+
+def tpc_track_launch(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz: float):
+    arr = (tpc_clusters * len(clusters))(*clusters)
+    _check(ctx, lib().tpc_track_launch(ctx, len(clusters), arr, C.byref(geom), bz))
+    return arr
+
+
+def tpc_track_results(ctx, n_ev: int, *, copy: bool = True):
+    outs = (tpc_tracks * n_ev)()
+    _check(ctx, lib().tpc_track_results(ctx, outs))
+    return [tracks_to_numpy(o) for o in outs] if copy else outs
+
+
+def tpc_track_submit(ctx, clusters: tpc_clusters, geom: tpc_geometry, bz: float) -> int:
+    t = C.c_uint64()
+    _check(ctx, lib().tpc_track_submit(ctx, C.byref(clusters), C.byref(geom), bz, C.byref(t)))
+    return t.value
+
+
+def tpc_track_poll(ctx, ticket: int, timeout_us: int = -1) -> Tracks | None:
+    out = tpc_tracks()
+    rc = lib().tpc_track_poll(ctx, ticket, timeout_us, C.byref(out))
+    if rc == TPC_EBUSY:
+        return None
+    _check(ctx, rc)
+    return tracks_to_numpy(out)
+
+
+def tpc_track_release(ctx, ticket: int):
+    _check(ctx, lib().tpc_track_release(ctx, ticket))
+
+
+def tpc_track_get_counters(ctx) -> dict:
+    c = tpc_track_counters()
+    _check(ctx, lib().tpc_track_get_counters(ctx, C.byref(c)))
+    return {k: int(getattr(c, k)) for k, _ in c._fields_}
+
+
+def tpc_track_stream(ctx) -> int:
+    return lib().tpc_track_stream(ctx) or 0
+
+
+def tpc_track_debug_dump(ctx, stage: int) -> bytes:
+    used = C.c_size_t()
+    _check(ctx, lib().tpc_track_debug_dump(ctx, stage, None, 0, C.byref(used)))
+    buf = C.create_string_buffer(max(1, used.value))
+    _check(ctx, lib().tpc_track_debug_dump(ctx, stage, buf, used.value, C.byref(used)))
+    return buf.raw[:used.value]
+
+
+def tpc_track_last_error(ctx) -> str:
+    return lib().tpc_track_last_error(ctx).decode()
+
+
+def tpc_track_destroy(ctx):
+    if ctx:
+        lib().tpc_track_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# decoded debug dumps
+# --------------------------------------------------------------------------
+
+def dump_links(ctx, n: int, clean: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    b = np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_CLEAN if clean else TPC_DUMP_LINKS), np.int32)
+    return b[:n].copy(), b[n:2 * n].copy()
+
+
+def dump_starts(ctx) -> np.ndarray:
+    return np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_STARTS), np.int32).copy()
+
+
+def dump_weights(ctx) -> np.ndarray:
+    return np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_WEIGHTS), np.uint64).copy()
+
+
+def dump_tracklets(ctx, n_rows: int) -> dict:
+    raw = tpc_track_debug_dump(ctx, TPC_DUMP_TRACKLETS)
+    count = int(np.frombuffer(raw[:4], np.int32)[0])
+    rec = C.sizeof(tpc_dump_tracklet) + 4 * n_rows
+    hdr_dt = np.dtype([("start_cid", "<i4"), ("sector", "<i4"), ("valid", "<i4"), ("nhits", "<i4"),
+                       ("first_row", "<i4"), ("last_row", "<i4"), ("ndf", "<i4"), ("pad", "<i4"),
+                       ("x", "<f4"), ("param", "<f4", 5), ("cov", "<f4", 15), ("chi2", "<f4")])
+    full_dt = np.dtype([("h", hdr_dt), ("rowhit", "<i4", n_rows)])
+    assert full_dt.itemsize == rec
+    a = np.frombuffer(raw[4:4 + count * rec], dtype=full_dt)
+    h = a["h"]
+    return {"start": h["start_cid"].copy(), "sector": h["sector"].copy(), "valid": h["valid"].copy(),
+            "nhits": h["nhits"].copy(), "first_row": h["first_row"].copy(),
+            "last_row": h["last_row"].copy(), "ndf": h["ndf"].copy(), "x": h["x"].copy(),
+            "p": h["param"].copy(), "C": h["cov"].copy(), "chi2": h["chi2"].copy(),
+            "rowhit": a["rowhit"].copy()}
+
+
+class Tracker:
+    """Convenience owner of one context (closes it on exit)."""
+
+    def __init__(self, max_clusters_per_event: int, **kw):
+        self.ctx = tpc_track_create(max_clusters_per_event, **kw)
+
+    def event(self, ev, *, device_arrays=None) -> Tracks:
+        g, keep_x = geometry_of(ev)
+        arrays = device_arrays if device_arrays is not None else (ev.y, ev.z, ev.row, ev.sector)
+        c, keep = clusters_of(*arrays)
+        return tpc_track_event(self.ctx, c, g, float(ev.bz))
+
+    def batch(self, evs, *, device_arrays=None) -> list[Tracks]:
+        g, keep_x = geometry_of(evs[0])
+        cs, keep = [], []
+        for i, ev in enumerate(evs):
+            arrays = device_arrays[i] if device_arrays is not None else (ev.y, ev.z, ev.row, ev.sector)
+            c, k = clusters_of(*arrays)
+            cs.append(c)
+            keep.append(k)
+        return tpc_track_batch(self.ctx, cs, g, float(evs[0].bz))
+
+    def counters(self) -> dict:
+        return tpc_track_get_counters(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            tpc_track_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

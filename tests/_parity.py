@@ -1,0 +1,120 @@
+"""GPU-vs-oracle comparison helpers for the parity tests.
+
+Bars (the tracker computes in binary32, the oracle in binary64):
+* links, cleaned links and start hits: identical (the neighbour decision is
+  taken in binary32 on both sides with the same rounding);
+* tracklet hit sets and validity: identical for every tracklet the oracle
+  does not flag as a near-tie (a chi2 within the tie width of the cut or of
+  the runner-up, |sin phi| near its bound, a stop bound); flagged tracklets
+  may differ, and those that do must stay below 0.1% of all tracklets;
+* parameters at the innermost hit: |dy|, |dz| <= 1e-3 cm; |d sin phi|,
+  |d tan lambda| <= 1e-4 (relative to values of order one); q/pT within
+  1e-4 relative to max(|q/pT|, 2 (GeV/c)^-1): stiff tracks have |q/pT| near
+  0, where the binary32 fit keeps an absolute error near 1e-4 (under 1% of
+  the statistical error of q/pT);
+* tracks: identical hit lists and order for every track that shares no hit
+  with a tracklet that differs.
+"""
+import numpy as np
+
+TOL_YZ = 1e-3
+TOL_ANG = 1e-4
+TOL_QPT_REL = 1e-4
+QPT_FLOOR = 2.0
+
+
+def param_errors(gp, op):
+    """Per-parameter |GPU - oracle| scaled to the bars (<= 1 passes)."""
+    gp = np.asarray(gp, np.float64)
+    op = np.asarray(op, np.float64)
+    d = np.abs(gp - op)
+    s = np.empty_like(d)
+    s[..., 0] = d[..., 0] / TOL_YZ
+    s[..., 1] = d[..., 1] / TOL_YZ
+    s[..., 2] = d[..., 2] / TOL_ANG
+    s[..., 3] = d[..., 3] / TOL_ANG
+    s[..., 4] = d[..., 4] / (TOL_QPT_REL * np.maximum(np.abs(op[..., 4]), QPT_FLOOR))
+    return d, s
+
+
+def compare_links(gpu_up, gpu_dn, o_up, o_dn):
+    bad = np.nonzero((gpu_up != o_up) | (gpu_dn != o_dn))[0]
+    return bad
+
+
+def compare_tracklets(gt, ot, n_rows):
+    """Returns a report dict; keys of tracklets are start cids."""
+    g_index = {int(c): i for i, c in enumerate(gt["start"])}
+    o_index = {int(c): i for i, c in enumerate(ot["t_start"])}
+    rep = {"n_oracle": len(o_index), "n_gpu": len(g_index),
+           "missing": sorted(set(o_index) - set(g_index)),
+           "extra": sorted(set(g_index) - set(o_index)),
+           "flagged": 0, "flagged_diff": [], "hitset_mismatch": [], "valid_mismatch": [],
+           "param_scaled": [], "param_abs": [], "taint": set()}
+    for c, oi in o_index.items():
+        if c not in g_index:
+            continue
+        gi = g_index[c]
+        same = int(gt["valid"][gi]) == int(ot["t_valid"][oi]) and \
+            np.array_equal(gt["rowhit"][gi], ot["t_rowhit"][oi])
+        if ot["t_flags"][oi] != 0:
+            rep["flagged"] += 1
+            if not same:
+                rep["flagged_diff"].append(c)
+                for a in (gt["rowhit"][gi], ot["t_rowhit"][oi]):
+                    rep["taint"].update(a[a >= 0].tolist())
+            continue
+        if int(gt["valid"][gi]) != int(ot["t_valid"][oi]):
+            rep["valid_mismatch"].append(c)
+            continue
+        if not same:
+            rep["hitset_mismatch"].append(c)
+            continue
+        if ot["t_valid"][oi]:
+            d, s = param_errors(gt["p"][gi], ot["t_p"][oi])
+            rep["param_scaled"].append(s)
+            rep["param_abs"].append(d)
+    rep["param_scaled"] = np.array(rep["param_scaled"]).reshape(-1, 5)
+    rep["param_abs"] = np.array(rep["param_abs"]).reshape(-1, 5)
+    return rep
+
+
+def tainted_hits(ot):
+    """Clusters of every oracle tracklet flagged as a near-tie (used when the
+    GPU tracklets are not at hand: a superset of the hits that can differ)."""
+    rh = ot["t_rowhit"][ot["t_flags"] != 0]
+    return set(rh[rh >= 0].tolist())
+
+
+def compare_tracks(gtr, ot, taint):
+    """Oracle tracks (from track_event) vs GPU Tracks; skips tainted ones."""
+    o_tracks = []
+    for j in range(ot["n_tracks"]):
+        h = ot["k_hit_cid"][ot["k_hit_off"][j]:ot["k_hit_off"][j + 1]]
+        o_tracks.append((tuple(h.tolist()), j))
+    g_tracks = []
+    for j in range(gtr.n_tracks):
+        g_tracks.append((tuple(gtr.hits(j).tolist()), j))
+    o_set = {h: j for h, j in o_tracks}
+    g_set = {h: j for h, j in g_tracks}
+
+    def clean(h):
+        return not (set(h) & taint)
+    o_clean = [h for h, _ in o_tracks if clean(h)]
+    g_clean = [h for h, _ in g_tracks if clean(h)]
+    rep = {"n_oracle": len(o_tracks), "n_gpu": len(g_tracks), "compared": 0,
+           "missing": [h for h in o_clean if h not in g_set],
+           "extra": [h for h in g_clean if h not in o_set], "param_scaled": []}
+    common = [h for h in o_clean if h in g_set]
+    rep["compared"] = len(common)
+    # same relative order
+    g_pos = [g_set[h] for h in common]
+    rep["order_ok"] = all(a < b for a, b in zip(g_pos, g_pos[1:]))
+    for h in common:
+        gj, oj = g_set[h], o_set[h]
+        _, s = param_errors(gtr.param[gj], ot["k_p"][oj])
+        rep["param_scaled"].append(s)
+        if gtr.sector[gj] != ot["k_sector"][oj] or gtr.ndf[gj] != ot["k_ndf"][oj]:
+            rep.setdefault("meta_mismatch", []).append(h)
+    rep["param_scaled"] = np.array(rep["param_scaled"]).reshape(-1, 5)
+    return rep

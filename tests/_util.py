@@ -30,38 +30,41 @@ def track_hits(out, j, prefix="k_"):
 
 
 def mc_summary(ev, out, min_clusters=30, match_frac=0.9, n_tracks_key="n_tracks"):
-    """Efficiency / fake / clone by MC labels.
+    """Efficiency / fake / clone by MC labels, per particle segment in a sector.
 
-    A reco track matches particle P if >= 90% of its hits carry P's label.
-    P is reconstructable if it has >= min_clusters clusters in one sector.
+    A reco track matches particle P if >= 90% of its hits carry P's label; it
+    then matches the segment (P, sector).  A segment is reconstructable if it
+    has >= min_clusters clusters.  Clones are extra matches of a segment.
     """
     lab = ev.label
     matched = {}
     fakes = 0
     clones = 0
-    for j in range(out[n_tracks_key]):
-        hits = track_hits(out, j)
+    sectors = out["k_sector"] if isinstance(out, dict) else out.sector
+    for j in range(out[n_tracks_key] if isinstance(out, dict) else out.n_tracks):
+        hits = track_hits(out, j) if isinstance(out, dict) else out.hits(j)
         l = lab[hits]
         vals, cnt = np.unique(l, return_counts=True)
         b = np.argmax(cnt)
         if vals[b] >= 0 and cnt[b] >= match_frac * len(hits):
-            if vals[b] in matched:
+            seg = (int(vals[b]), int(sectors[j]))
+            if seg in matched:
                 clones += 1
-            matched[vals[b]] = matched.get(vals[b], 0) + 1
+            matched[seg] = matched.get(seg, 0) + 1
         else:
             fakes += 1
+    n_reco = out[n_tracks_key] if isinstance(out, dict) else out.n_tracks
     sig = lab >= 0
     key = lab[sig].astype(np.int64) * 64 + ev.sector[sig]
     k, c = np.unique(key, return_counts=True)
-    recble = np.unique(k[c >= min_clusters] // 64)
+    recble = [(int(a // 64), int(a % 64)) for a in k[c >= min_clusters]]
     pt = ev.particles.pt
-    res = {"n_reco": out[n_tracks_key], "n_reconstructable": len(recble), "fakes": fakes,
-           "clones": clones}
+    res = {"n_reco": n_reco, "n_reconstructable": len(recble), "fakes": fakes, "clones": clones}
     for name, lo in (("eff", 0.0), ("eff_pt02", 0.2)):
-        sel = [p for p in recble if pt[p] >= lo]
-        res[name] = float(np.mean([p in matched for p in sel])) if sel else float("nan")
-    res["fake_rate"] = fakes / max(1, out[n_tracks_key])
-    res["clone_rate"] = clones / max(1, out[n_tracks_key])
+        sel = [sg for sg in recble if pt[sg[0]] >= lo]
+        res[name] = float(np.mean([sg in matched for sg in sel])) if sel else float("nan")
+    res["fake_rate"] = fakes / max(1, n_reco)
+    res["clone_rate"] = clones / max(1, n_reco)
     return res
 
 

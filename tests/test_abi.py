@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/tpctrack.h declares (no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tpctrack.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tpc_track_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1712_09416_b300 import build, tpctrack
+    build.build()
+    return tpctrack.lib()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ("tpc_track_create", "tpc_track_event", "tpc_track_batch", "tpc_track_submit",
+              "tpc_track_poll", "tpc_track_release", "tpc_track_debug_dump",
+              "tpc_track_last_error", "tpc_track_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1712_09416_b300 import tpctrack
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    assert sorted(tpctrack.EXPORTED) == declared_functions()
+
+
+def test_default_params_without_gpu(lib):
+    from paper_1712_09416_b300 import tpctrack
+    p = tpctrack.tpc_track_default_params()
+    assert p.chi2_hit == 16.0 and p.max_gap == 5 and abs(p.d_max - 0.36) < 1e-7
+    assert p.min_tracklet_hits == 10 and abs(p.sin_max - 0.99) < 1e-7
+
+
+def test_create_rejects_bad_config_before_touching_the_device(lib):
+    from paper_1712_09416_b300 import tpctrack
+    cfg = tpctrack.tpc_track_config()
+    cfg.max_clusters_per_event = 0
+    cfg.max_events_in_flight = 1
+    cfg.params = tpctrack.tpc_track_default_params()
+    ctx = ctypes.c_void_p()
+    assert lib.tpc_track_create(ctypes.byref(cfg), ctypes.byref(ctx)) == tpctrack.TPC_EINVAL
+    assert not ctx.value
+    cfg.max_clusters_per_event = 1000
+    cfg.params.chi2_hit = -1.0
+    assert lib.tpc_track_create(ctypes.byref(cfg), ctypes.byref(ctx)) == tpctrack.TPC_EINVAL
+    assert lib.tpc_track_create(None, ctypes.byref(ctx)) == tpctrack.TPC_EINVAL
+
+
+def test_struct_sizes_match_the_header(lib):
+    from paper_1712_09416_b300 import tpctrack
+    # sizes on x86-64 of the records in tpctrack.h
+    assert ctypes.sizeof(tpctrack.tpc_clusters) == 48
+    assert ctypes.sizeof(tpctrack.tpc_tracks) == 72
+    assert ctypes.sizeof(tpctrack.tpc_geometry) == 32
+    assert ctypes.sizeof(tpctrack.tpc_track_params) == 60
+    assert ctypes.sizeof(tpctrack.tpc_dump_tracklet) == 32 + 4 * 22

@@ -1,0 +1,227 @@
+"""GPU tracker vs the CPU oracle, stage by stage, through the C ABI.
+
+Every test here runs the CUDA path of libtpctrack.so on the B300 and compares
+it element by element with the oracle on the same seeded events (bars in
+tests/_parity.py).  Sizes span several look-back tiles and a ragged tail; the
+full-size central event is compared on a sample of its sectors (sectors are
+independent, so the oracle computes the sampled ones alone).
+"""
+import numpy as np
+import pytest
+
+from paper_1712_09416_b300 import synth
+from tests import _parity, _util
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1712_09416_b300 import build, tpctrack
+    build.build()
+    return tpctrack
+
+
+@pytest.fixture(scope="module")
+def trk(tp):
+    t = tp.Tracker(2_000_000, max_events_per_launch=16)
+    yield t
+    t.close()
+
+
+def run(tp, trk, ev):
+    tr = trk.event(ev)
+    n = ev.n
+    up, dn = tp.dump_links(trk.ctx, n)
+    upc, dnc = tp.dump_links(trk.ctx, n, clean=True)
+    return {"tracks": tr, "up": up, "dn": dn, "up_c": upc, "dn_c": dnc,
+            "starts": tp.dump_starts(trk.ctx),
+            "tracklets": tp.dump_tracklets(trk.ctx, len(ev.row_x)),
+            "weights": tp.dump_weights(trk.ctx), "counters": trk.counters()}
+
+
+def check_event(tp, trk, ev, orc, *, max_diff_frac=1e-3):
+    g = run(tp, trk, ev)
+    o = orc.track_event(ev)
+    assert len(_parity.compare_links(g["up"], g["dn"], o["up"], o["dn"])) == 0
+    assert len(_parity.compare_links(g["up_c"], g["dn_c"], o["up_c"], o["dn_c"])) == 0
+    o_starts = np.sort(np.nonzero((o["up_c"] >= 0) & (o["dn_c"] < 0))[0])
+    assert np.array_equal(g["starts"], o_starts)
+    rep = _parity.compare_tracklets(g["tracklets"], o, len(ev.row_x))
+    assert rep["missing"] == [] and rep["extra"] == []
+    assert len(rep["flagged_diff"]) <= max_diff_frac * max(1, rep["n_oracle"]), rep["flagged_diff"]
+    assert rep["valid_mismatch"] == [], rep["valid_mismatch"][:10]
+    assert rep["hitset_mismatch"] == [], rep["hitset_mismatch"][:10]
+    if len(rep["param_scaled"]):
+        assert rep["param_scaled"].max() <= 1.0, rep["param_scaled"].max(axis=0)
+    trep = _parity.compare_tracks(g["tracks"], o, rep["taint"])
+    assert trep["missing"] == [] and trep["extra"] == []
+    assert trep["order_ok"]
+    assert "meta_mismatch" not in trep
+    if len(trep["param_scaled"]):
+        assert trep["param_scaled"].max() <= 1.0
+    c = g["counters"]
+    assert c["n_starts"] == o["n_starts"]
+    assert c["n_tracklets"] == o["n_tracklets"]
+    assert c["n_links"] == o["n_links"]
+    return g, o, rep, trep
+
+
+def test_golden_neighbours_on_gpu(tp, trk):
+    ev, gold = _util.golden_event()
+    g = run(tp, trk, ev)
+    exp = gold["expected"]
+    for name in ("up", "dn", "up_c", "dn_c"):
+        for cid, v in exp[name].items():
+            assert g[name][int(cid)] == v, (name, cid)
+    assert g["starts"].tolist() == exp["starts"]
+
+
+def test_one_sector_event_stage_parity(tp, trk, orc):
+    ev = synth.one_sector_event()
+    g, o, rep, trep = check_event(tp, trk, ev, orc)
+    assert trep["compared"] >= 0.95 * trep["n_oracle"]
+    s = _util.mc_summary(ev, g["tracks"])
+    assert s["eff_pt02"] >= 0.95 and s["fake_rate"] < 0.02, s
+
+
+def test_isolated_tracks(tp, trk, orc):
+    ev = _util.isolated_event()
+    check_event(tp, trk, ev, orc, max_diff_frac=0.0)
+
+
+def test_central_event_sampled_sectors(tp, trk, orc):
+    """Full-size central event on the GPU; six of its sectors against the oracle."""
+    ev = synth.central_event()
+    tr = trk.event(ev)
+    sample = [0, 7, 13, 20, 28, 35]
+    for s in sample:
+        sub = ev.select_sectors([s])
+        o = orc.track_event(sub)
+        parent = sub.info["parent_index"]
+        m = np.nonzero(tr.sector == s)[0]
+        # GPU tracks of this sector, hits mapped to the sub-event's cids
+        inv = {int(c): i for i, c in enumerate(parent)}
+        g_hits = [tuple(inv[int(c)] for c in tr.hits(j)) for j in m]
+        o_hits = [tuple(o["k_hit_cid"][o["k_hit_off"][j]:o["k_hit_off"][j + 1]].tolist())
+                  for j in range(o["n_tracks"])]
+        taint = _parity.tainted_hits(o)
+        oc = [h for h in o_hits if not set(h) & taint]
+        gc = [h for h in g_hits if not set(h) & taint]
+        assert set(oc) <= set(g_hits)
+        assert set(gc) <= set(o_hits)
+        pos = {h: k for k, h in enumerate(g_hits)}
+        for h in oc:
+            j = m[pos[h]]
+            oj = o_hits.index(h)
+            _, sc = _parity.param_errors(tr.param[j], o["k_p"][oj])
+            assert sc.max() <= 1.0, sc
+
+
+def test_device_inputs_equal_host_inputs(tp, trk):
+    import torch
+    ev = synth.one_sector_event(seed=21)
+    a = trk.event(ev)
+    dev = (torch.from_numpy(ev.y).cuda(), torch.from_numpy(ev.z).cuda(),
+           torch.from_numpy(ev.row.view(np.int16)).cuda(),
+           torch.from_numpy(ev.sector.view(np.int16)).cuda())
+    b = trk.event(ev, device_arrays=dev)
+    for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+
+
+def test_repeat_is_bit_identical(tp, trk):
+    ev = synth.one_sector_event(seed=33)
+    a = trk.event(ev)
+    b = trk.event(ev)
+    for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+
+
+def test_batch_equals_single_events(tp, trk):
+    evs = synth.batch_events(n_events=6)
+    alone = [trk.event(e) for e in evs]
+    batch = trk.batch(evs)
+    for a, b in zip(alone, batch):
+        for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+            assert np.array_equal(getattr(a, f), getattr(b, f)), f
+
+
+def test_empty_and_tiny_events(tp, trk):
+    e0 = synth.Event(np.zeros(0, np.float32), np.zeros(0, np.float32), np.zeros(0, np.uint16),
+                     np.zeros(0, np.uint16), np.zeros(0, np.int32), synth.default_row_x(), 18, 1)
+    assert trk.event(e0).n_tracks == 0
+    e1 = synth.Event(np.array([1.0], np.float32), np.array([2.0], np.float32),
+                     np.array([5], np.uint16), np.array([3], np.uint16), np.array([-1], np.int32),
+                     synth.default_row_x(), 18, 1)
+    assert trk.event(e1).n_tracks == 0
+    # noise only: no track survives the selector
+    rng = np.random.default_rng(9)
+    n = 20000
+    en = synth.Event(rng.uniform(-15, 15, n).astype(np.float32),
+                     rng.uniform(-250, 250, n).astype(np.float32),
+                     rng.integers(0, 159, n).astype(np.uint16), np.zeros(n, np.uint16),
+                     np.full(n, -1, np.int32), synth.default_row_x(), 1, 0)
+    trk.event(en)
+
+
+def test_invalid_input_is_rejected(tp, trk):
+    ev = synth.one_sector_event()
+    for field, bad in (("row", 159), ("sector", 1), ("y", np.nan), ("z", np.inf)):
+        e = synth.Event(ev.y.copy(), ev.z.copy(), ev.row.copy(), ev.sector.copy(), ev.label,
+                        ev.row_x, ev.n_sectors_phi, ev.split_z)
+        getattr(e, field)[17] = bad
+        with pytest.raises(tp.TpcError) as ei:
+            trk.event(e)
+        assert ei.value.code == tp.TPC_EINVAL
+    # the context stays usable
+    assert trk.event(ev).n_tracks > 0
+
+
+def test_row_capacity_overflow_is_reported(tp, trk):
+    n = 5000
+    rng = np.random.default_rng(4)
+    e = synth.Event(rng.uniform(-10, 10, n).astype(np.float32),
+                    rng.uniform(0, 200, n).astype(np.float32), np.full(n, 40, np.uint16),
+                    np.zeros(n, np.uint16), np.full(n, -1, np.int32), synth.default_row_x(), 18, 1)
+    with pytest.raises(tp.TpcError) as ei:
+        trk.event(e)
+    assert ei.value.code == tp.TPC_ECAPACITY
+    assert trk.event(synth.one_sector_event()).n_tracks > 0
+
+
+def test_too_many_clusters_for_the_context(tp):
+    t = tp.Tracker(1000)
+    try:
+        with pytest.raises(tp.TpcError) as ei:
+            t.event(synth.one_sector_event())
+        assert ei.value.code == tp.TPC_EINVAL
+    finally:
+        t.close()
+
+
+def test_served_results_equal_alone(tp):
+    evs = synth.batch_events(n_events=8, seed0=3100)
+    t = tp.Tracker(2_000_000, max_events_in_flight=2)
+    try:
+        alone = [t.event(e) for e in evs]
+    finally:
+        t.close()
+    s = tp.Tracker(2_000_000, max_events_in_flight=2)
+    try:
+        keep = []
+        tickets = []
+        for e in evs:
+            g, kx = tp.geometry_of(e)
+            c, k = tp.clusters_of(e.y, e.z, e.row, e.sector)
+            keep.append((g, kx, c, k))
+            tickets.append(tp.tpc_track_submit(s.ctx, c, g, float(e.bz)))
+        for a, tk in zip(alone, tickets):
+            b = tp.tpc_track_poll(s.ctx, tk, -1)
+            for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+                assert np.array_equal(getattr(a, f), getattr(b, f)), f
+            tp.tpc_track_release(s.ctx, tk)
+    finally:
+        s.close()

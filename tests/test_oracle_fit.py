@@ -48,8 +48,9 @@ def test_zero_field_line_equals_batch_least_squares(orc, s0, t):
     F[0, 2] = dL / c0 ** 3
     F[1, 2] = t * dL * s0 / c0 ** 3
     F[1, 3] = dL / c0
-    P0 = np.diag([params.sigma_y ** 2, params.sigma_z ** 2, params.seed_var_s,
-                  params.seed_var_t, params.seed_var_q])
+    # seed covariance: slope variances carried to sin(phi), tan(lambda) at s0
+    P0 = np.diag([params.sigma_y ** 2, params.sigma_z ** 2, params.seed_var_s * c0 ** 6,
+                  params.seed_var_t * c0 ** 2, params.seed_var_q])
     Vi = np.diag([1 / params.sigma_y ** 2, 1 / params.sigma_z ** 2])
     info = F.T @ np.linalg.inv(P0) @ F
     for d in dx:
