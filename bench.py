@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 TPC sector tracker (one JSON line on stdout).
+
+Workload: the central heavy-ion-like event (10,000 primary helices plus 1,000
+secondaries plus 5% noise, 36 sectors x 159 pad rows, 0.5 T, seed 2, about
+1.73M binary32 clusters).  One step = the whole tracking path (binning,
+neighbours, cleaning, start hits, tracklet construction, selection) over one
+such event, inputs resident in HBM.  Eight device copies of the event are used
+in turn so that the inputs of consecutive steps (168 MB) exceed the 126 MB L2.
+
+Also measured: the same metric end to end through the C ABI with pinned host
+buffers (host->device copy of the clusters and device->host copy of the
+tracks inside the timed region), per-kernel device times (CUDA events on the
+launch stream) for the roofline of the dominant kernel, served (continuous
+batching) versus one-event-at-a-time latency under Poisson arrivals, SM
+clocks during the timed region, and the CPU oracle on a bounded sample.
+
+--impl reference times the CPU oracle (the reference of this build) on the
+same workload and metric, each step a bounded sample of sectors.
+Multi-GPU (torchrun): independent replicas, one event stream per GPU, no
+collective on the data path; value = clusters of all ranks / slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "clusters/s & central-event p50/p99 latency, served vs one-event, 1 B300"
+UNIT = "clusters/s"
+WORKLOAD = ("central event: 10,000 primaries + 1,000 secondaries + 5% noise, 36 sectors x "
+            "159 rows (85-247 cm), |z| < 250 cm, 0.5 T, seed 2")
+N_COPIES = 8
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes per kernel launch (one read or write of each array the
+# method needs; reuse of a neighbour's data is not counted)
+# --------------------------------------------------------------------------
+
+def kernel_bytes(c: dict) -> dict:
+    N, RS, B = c["n_clusters"], c["n_rows_total"], c["n_bins"]
+    T, Tl, Th = c["n_starts"], c["n_tracklets"], c["n_tracklet_hits"]
+    K, Kh = c["n_tracks"], c["n_track_hits"]
+    return {
+        "k_count": 12 * N + 4 * RS,
+        "k_rowscan": 4 * RS + 4 * RS + 32 * RS,
+        "k_scatter": 12 * N + 12 * N,
+        "k_rowsort": 12 * N + 16 * N + 8 * N + 4 * (B + RS) + 32 * RS,
+        "k_neighbours": 8 * N + 4 * N + 4 * B,
+        "k_clean_starts": 4 * N + 4 * N + 4 * N + 4 * N + 4 * T,
+        "k_constructor": 34 * Th + 116 * Tl,
+        "k_sel_decide": 10 * Th + 32 * T,
+        "k_sel_sort": 12 * T + 8 * K,
+        "k_sel_write": 212 * K + 18 * Kh,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running (clocks, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(ev_full, n_sectors: int = 4) -> dict:
+    """The oracle as it stands, single-threaded, on a few sectors of the event."""
+    from oracle import oracle
+    sectors = list(range(0, 36, 36 // n_sectors))[:n_sectors]
+    sub = ev_full.select_sectors(sectors)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.track_event(sub)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_sectors} of 36 sectors of the central event ({sub.n} clusters), "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def percentile(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))
+    return v[k]
+
+
+def served_vs_one(tp, torch, host_events, geom, bz, n_per_event, rate_factors=(0.7, 1.5),
+                  n_events=120, seed=4):
+    """Poisson arrivals of central events: one-at-a-time FIFO server vs the
+    served form (continuous batching over 3 slots).  Rates are set relative
+    to the measured one-at-a-time capacity."""
+    import numpy as np
+    ctx1 = tp.tpc_track_create(2_000_000, max_events_per_launch=1)
+    try:
+        # service time of one event through the C ABI with host inputs
+        for e in host_events[:2]:
+            tp.tpc_track_event(ctx1, e, geom, bz)
+        t0 = time.perf_counter()
+        for i in range(6):
+            tp.tpc_track_event(ctx1, host_events[i % len(host_events)], geom, bz)
+        service = (time.perf_counter() - t0) / 6
+    finally:
+        tp.tpc_track_destroy(ctx1)
+    cap = 1.0 / service
+    out = {"service_ms_one_event": service * 1e3, "points": []}
+    rng = np.random.default_rng(seed)
+    for rf in rate_factors:
+        lam = rf * cap
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n_events))
+        # one at a time (FIFO): latency = finish - arrival
+        ctx1 = tp.tpc_track_create(2_000_000, max_events_per_launch=1)
+        lat1 = []
+        try:
+            t_start = time.perf_counter()
+            for i, a in enumerate(arrivals):
+                now = time.perf_counter() - t_start
+                if now < a:
+                    time.sleep(a - now)
+                tp.tpc_track_event(ctx1, host_events[i % len(host_events)], geom, bz)
+                lat1.append(time.perf_counter() - t_start - a)
+            span1 = time.perf_counter() - t_start
+        finally:
+            tp.tpc_track_destroy(ctx1)
+        # served: submit on arrival, a poller collects completions
+        ctxs = tp.tpc_track_create(4 * n_per_event + 1024, max_events_in_flight=3,
+                                   max_events_per_launch=4)
+        lats = [None] * n_events
+        errors = []
+        try:
+            tickets = [None] * n_events
+            t_start = time.perf_counter()
+            done = threading.Event()
+
+            def poller():
+                try:
+                    for i in range(n_events):
+                        deadline = time.perf_counter() + 60.0
+                        while tickets[i] is None:
+                            if errors or time.perf_counter() > deadline:
+                                raise TimeoutError("ticket never submitted")
+                            time.sleep(0.0001)
+                        if tp.tpc_track_poll(ctxs, tickets[i], 60_000_000) is None:
+                            raise TimeoutError("ticket not done after 60 s")
+                        lats[i] = time.perf_counter() - t_start - arrivals[i]
+                        tp.tpc_track_release(ctxs, tickets[i])
+                except Exception as e:  # reported in the JSON line
+                    errors.append(repr(e))
+                finally:
+                    done.set()
+            th = threading.Thread(target=poller, daemon=True)
+            th.start()
+            try:
+                for i, a in enumerate(arrivals):
+                    now = time.perf_counter() - t_start
+                    if now < a:
+                        time.sleep(a - now)
+                    tickets[i] = tp.tpc_track_submit(ctxs, host_events[i % len(host_events)],
+                                                     geom, bz)
+            except Exception as e:
+                errors.append(repr(e))
+            if not done.wait(180.0):
+                errors.append("served run did not finish within 180 s")
+            spans = time.perf_counter() - t_start
+        finally:
+            if not errors:
+                tp.tpc_track_destroy(ctxs)
+        if errors:
+            out["error"] = errors[0]
+            return out
+        out["points"].append({
+            "rate_per_s": lam,
+            "one_event": {"p50_ms": percentile(lat1, 50) * 1e3, "p99_ms": percentile(lat1, 99) * 1e3,
+                          "clusters_per_s": n_events * n_per_event / span1},
+            "served": {"p50_ms": percentile(lats, 50) * 1e3, "p99_ms": percentile(lats, 99) * 1e3,
+                       "clusters_per_s": n_events * n_per_event / spans},
+        })
+    return out
+
+
+def traffic_for(kernel: str, counters: dict):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of that kernel."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1712_09416_b300", "csrc", e["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != e["source_sha"]:
+        return None
+    return e["dram_bytes_per_cluster"] * counters["n_clusters"]
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1712_09416_b300 import build, synth, tpctrack as tp
+    build.build()
+    ev = synth.central_event(seed=2)
+    n = ev.n
+    geom, keep_x = tp.geometry_of(ev)
+    bz = float(ev.bz)
+    dev = []
+    for _ in range(N_COPIES):
+        dev.append((torch.from_numpy(ev.y).cuda(), torch.from_numpy(ev.z).cuda(),
+                    torch.from_numpy(ev.row.view(np.int16)).cuda(),
+                    torch.from_numpy(ev.sector.view(np.int16)).cuda()))
+    cls = [tp.clusters_of(*d) for d in dev]
+    stream = torch.cuda.current_stream()
+    ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, cuda_stream=stream.cuda_stream)
+
+    def step(i):
+        tp.tpc_track_launch(ctx, [cls[i % N_COPIES][0]], geom, bz)
+
+    for i in range(args.warmup):
+        step(i)
+        tp.tpc_track_results(ctx, 1, copy=False)
+    counters = tp.tpc_track_get_counters(ctx)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    tp.tpc_track_set_profiling(ctx, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for i in range(args.steps):
+            step(i)
+        e1.record(stream)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    tp.tpc_track_results(ctx, 1, copy=False)  # status of the last step
+    ktimes = tp.tpc_track_kernel_times(ctx)
+    tp.tpc_track_set_profiling(ctx, False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * n * args.steps / (ms_total * 1e-3)
+    launches = sum(v[1] for v in ktimes.values())
+
+    # roofline of the dominant kernel
+    kb = kernel_bytes(counters)
+    peak, peak_src = peaks()
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms = ktimes[dom][0] / ktimes[dom][1]
+    achieved = kb[dom] / (dom_ms * 1e-3) / 1e9
+    b_alg = sum(kb.values()) / n
+
+    # end to end through the C ABI with pinned host inputs
+    pinned = [torch.from_numpy(ev.y).pin_memory(), torch.from_numpy(ev.z).pin_memory(),
+              torch.from_numpy(ev.row.view(np.int16)).pin_memory(),
+              torch.from_numpy(ev.sector.view(np.int16)).pin_memory()]
+    hc, hkeep = tp.clusters_of(*pinned)
+    ctx_h = tp.tpc_track_create(n + 65536, max_events_per_launch=1)
+    for _ in range(2):
+        tr = tp.tpc_track_event(ctx_h, hc, geom, bz)
+    k_e2e = max(5, min(args.steps, 20))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        tr = tp.tpc_track_event(ctx_h, hc, geom, bz)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    tp.tpc_track_destroy(ctx_h)
+    h2d = 12 * n + 4096
+    d2h = 256 + tr.n_tracks * (4 + 4 + 20 + 60 + 4 + 4 + 4) + 4 * len(tr.hit_cid) + 4 * 37
+    e2e = {"value": world * n * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": k_e2e}
+
+    served = None
+    if not args.no_served and rank == 0:
+        try:
+            served = served_vs_one(tp, torch, [hc], geom, bz, n)
+        except Exception as e:  # reported, the bench line still goes out
+            served = {"error": repr(e)}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(ev)
+
+    tp.tpc_track_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "clusters_per_event": n,
+                       "l2": f"inputs rotate over {N_COPIES} device copies "
+                             f"({N_COPIES * 12 * n / 1e6:.0f} MB) > 126 MB L2; each step also "
+                             "writes ~150 MB of intermediate arrays",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "tracks_per_event": counters["n_tracks"],
+                       "tracklets_per_event": counters["n_tracklets"]},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": traffic_for(dom, counters),
+                         "algorithmic_bytes_per_launch": kb[dom], "launch_ms": dom_ms},
+            "path_roofline": {"bytes_per_cluster": b_alg,
+                              "clusters_per_s_at_peak": peak * 1e9 / b_alg,
+                              "frac": value / world / (peak * 1e9 / b_alg)},
+            "kernels_ms": {k: v[0] / v[1] for k, v in ktimes.items()},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "cpu_baseline": cpu, "served": served,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1712_09416_b300 import synth
+    from oracle import oracle
+    oracle.build()
+    ev = synth.central_event(seed=2)
+    sectors = [0, 9, 18, 27]
+    sub = ev.select_sectors(sectors)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.track_event(sub.select_sectors([0]))
+    t0 = time.perf_counter()
+    n_total = 0
+    for i in range(args.steps):
+        s = sub.select_sectors([sectors[i % len(sectors)]])
+        oracle.track_event(s)
+        n_total += s.n
+    dt = time.perf_counter() - t0
+    v = n_total / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "clusters_per_event": ev.n,
+                       "sample": "each step tracks one of sectors 0, 9, 18, 27 of the event"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single sectors of the central event, "
+                                       "single-threaded"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("warmup raised to 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -96,7 +96,7 @@ typedef struct {
 typedef struct {
     float meas_sigma_y, meas_sigma_z;  /* cluster errors, cm (0.1, 0.1) */
     float slope_win_y, slope_win_z;    /* neighbour windows |dy| <= w |dx| (2.0, 2.0) */
-    float d_max;                       /* neighbour kink cut (0.36) */
+    float d_max;                       /* neighbour kink cut (0.6) */
     float chi2_hit;                    /* searched-hit chi2 cut (16) */
     int max_gap;                       /* consecutive missed rows ending a search (5) */
     int min_chain;                     /* hits of a chain to build a tracklet (3) */
@@ -182,6 +182,20 @@ int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c);
 
 /* Stream the context launches on (a cudaStream_t). */
 void* tpc_track_stream(const tpc_track_ctx* ctx);
+
+/* Kernel timing for benchmarks.  tpc_track_set_profiling(ctx, 1) waits for
+ * the context's stream, clears the record, and makes every later direct
+ * launch record a CUDA event after each of its kernels on the launch stream
+ * (0 turns it off).  tpc_track_kernel_times waits for the stream and writes,
+ * per kernel name in launch order, the summed device time and the number of
+ * launches recorded (up to cap entries; *n receives the count). */
+typedef struct {
+    char name[32];
+    double total_ms;
+    int64_t launches;
+} tpc_kernel_time;
+int tpc_track_set_profiling(tpc_track_ctx* ctx, int on);
+int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, int* n);
 
 /* Debug dump of an intermediate stage of event 0 of the last completed
  * launch, for parity tests.  Writes at most cap bytes to host_buf and the

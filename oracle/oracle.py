@@ -79,7 +79,7 @@ class Params:
     sigma_z: float = 0.1
     slope_win_y: float = 2.0
     slope_win_z: float = 2.0
-    d_max: float = 0.36
+    d_max: float = 0.6
     chi2_hit: float = 16.0
     max_gap: int = 5
     min_chain: int = 3

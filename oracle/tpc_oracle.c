@@ -283,11 +283,12 @@ static int row_list(const hits_t* H, int sec, int r, const int32_t** out)
 /*
  * Hit h on row r (1 <= r <= R-2).  Candidate c on row r+-1 is admissible iff
  * |y_c - y_h| <= SY |x_c - x_h| and |z_c - z_h| <= SZ |x_c - x_h|.  Slopes
- * sy_u = (y_u - y_h)/(x_u - x_h), sy_d = (y_h - y_d)/(x_h - x_d), likewise z;
- * score D = (sy_u - sy_d)^2 + (sz_u - sz_d)^2.  The admissible pair (d, u)
- * with the least D wins, exact ties going to the lower cid(u) and then the
- * lower cid(d); the links are set iff D <= D_MAX.  Binary32, one rounding per
- * operation.
+ * sy_u = (y_u - y_h)/(x_u - x_h), sy_d = (y_h - y_d)/(x_h - x_d), likewise z,
+ * each taken as the coordinate difference times the rounded reciprocal of the
+ * row spacing; score D = (sy_u - sy_d)^2 + (sz_u - sz_d)^2.  The admissible
+ * pair (d, u) with the least D wins, exact ties going to the lower cid(u) and
+ * then the lower cid(d); the links are set iff D <= D_MAX.  Binary32, one
+ * rounding per operation.
  */
 static void best_pair_f32(const hits_t* H, const orc_config* cfg, int sec, int r, int32_t h,
                           int32_t* up, int32_t* dn)
@@ -296,7 +297,7 @@ static void best_pair_f32(const hits_t* H, const orc_config* cfg, int sec, int r
     const int nu = row_list(H, sec, r + 1, &lu);
     const int nd = row_list(H, sec, r - 1, &ld);
     const float xh = H->xrf[r], xu = H->xrf[r + 1], xd = H->xrf[r - 1];
-    const float dxu = xu - xh, dxd = xh - xd;
+    const float iu = 1.0f / (xu - xh), id = 1.0f / (xh - xd);
     const float wyu = cfg->slope_win_y * fabsf(xu - xh), wzu = cfg->slope_win_z * fabsf(xu - xh);
     const float wyd = cfg->slope_win_y * fabsf(xd - xh), wzd = cfg->slope_win_z * fabsf(xd - xh);
     const float yh = H->yf[h], zh = H->zf[h];
@@ -306,12 +307,12 @@ static void best_pair_f32(const hits_t* H, const orc_config* cfg, int sec, int r
         const int32_t u = lu[a];
         const float ddyu = H->yf[u] - yh, ddzu = H->zf[u] - zh;
         if (!(fabsf(ddyu) <= wyu) || !(fabsf(ddzu) <= wzu)) continue;
-        const float syu = ddyu / dxu, szu = ddzu / dxu;
+        const float syu = ddyu * iu, szu = ddzu * iu;
         for (int b = 0; b < nd; ++b) {
             const int32_t d = ld[b];
             const float ddyd = yh - H->yf[d], ddzd = zh - H->zf[d];
             if (!(fabsf(ddyd) <= wyd) || !(fabsf(ddzd) <= wzd)) continue;
-            const float syd = ddyd / dxd, szd = ddzd / dxd;
+            const float syd = ddyd * id, szd = ddzd * id;
             const float ey = syu - syd, ez = szu - szd;
             const float ey2 = ey * ey, ez2 = ez * ez;
             const float D = ey2 + ez2;

@@ -79,7 +79,7 @@ __device__ __forceinline__ RowGrid make_grid(const Launch& L, int g, int cnt)
     const int r = g - gs * L.R;
     const int e = L.sec_event[gs];
     const int s = gs - L.ev[e].sec_base;
-    const float x = L.row_x[r];
+    const float x = __ldg(&L.xr[r]);
     const float yh = x * L.tan_half + 2.0f;
     float zlo = -L.z_max, zhi = L.z_max;
     if (L.split_z) {
@@ -299,17 +299,21 @@ size_t rowsort_smem_bytes()
            3 * sizeof(int16_t) * kMaxRowHits;
 }
 
-void launch_binning(const Launch& L, void* stream_)
+void launch_binning(const Launch& L, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
     const int blocks = 148 * 4;
     k_count<<<blocks, 256, 0, stream>>>(L);
+    hook_after(hook, "k_count");
     k_rowscan<<<L.n_row_tiles, kScanThreads, 0, stream>>>(L);
+    hook_after(hook, "k_rowscan");
     k_scatter<<<blocks, 256, 0, stream>>>(L);
+    hook_after(hook, "k_scatter");
     const size_t sm = rowsort_smem_bytes();
     cudaFuncSetAttribute(k_rowsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int rows_blocks = L.RS < 148 * 16 ? L.RS : 148 * 16;
     k_rowsort<<<rows_blocks > 0 ? rows_blocks : 1, kSortThreads, sm, stream>>>(L);
+    hook_after(hook, "k_rowsort");
 }
 
 }  // namespace tpc

@@ -1,8 +1,7 @@
 // k_finder.cu -- the cellular-automaton part of the sector tracker (paper,
 // Abstract): neighbour finding, mutual-link cleaning and start hits.
 //
-//   k_neighbours   one block per (sector, row r), one thread per hit h of the
-//                  row.  Candidates on rows r +- 1 inside the slope windows
+//   k_neighbours   one thread per hit h on row r.  Candidates on rows r +- 1 inside the slope windows
 //                  |dy| <= SY |dx|, |dz| <= SZ |dx| are taken from the y-z bins
 //                  that cover the window; every (down, up) pair is scored by
 //                  the straight-line kink D = (sy_u - sy_d)^2 + (sz_u - sz_d)^2;
@@ -24,78 +23,173 @@ namespace tpc {
 
 namespace {
 
-constexpr int kNbThreads = 128;
+constexpr int kNbThreads = 256;
 
+struct RowView {      // one adjacent row
+    const float* y;
+    const float* z;
+    const int* cid;
+    const int* bins;
+    RowGrid G;
+};
+
+// Admissible candidates of one side, kept in registers (at most kList); the
+// insert is a chain of predicated moves so that the list never spills.
+constexpr int kList = 4;
+struct CandList {
+    float sy[kList], sz[kList];
+    int cid[kList], k[kList];
+    int n;
+};
+
+__device__ __forceinline__ void push(CandList& c, float sy, float sz, int cid, int k)
+{
+#pragma unroll
+    for (int j = 0; j < kList; ++j) {
+        if (c.n == j) {
+            c.sy[j] = sy;
+            c.sz[j] = sz;
+            c.cid[j] = cid;
+            c.k[j] = k;
+        }
+    }
+    ++c.n;
+}
+
+// Scan one side's window: admissible candidates and their slopes.  up = true
+// gives slopes (c - h) * inv, up = false gives (h - c) * inv.
+__device__ __forceinline__ void collect(const RowView& V, float yh, float zh, float inv, float wy,
+                                       float wz, bool up, CandList& c)
+{
+    const float my = 1e-3f * (1.0f + fabsf(yh)), mz = 1e-3f * (1.0f + fabsf(zh));
+    const int y0 = bin_y(V.G, yh - wy - my), y1 = bin_y(V.G, yh + wy + my);
+    const int z0 = bin_z(V.G, zh - wz - mz), z1 = bin_z(V.G, zh + wz + mz);
+    c.n = 0;
+    for (int bz = z0; bz <= z1; ++bz) {
+        const int a = V.bins[bz * V.G.ny + y0], b = V.bins[bz * V.G.ny + y1 + 1];
+        for (int k = a; k < b; ++k) {
+            const float ddy = up ? __fsub_rn(V.y[k], yh) : __fsub_rn(yh, V.y[k]);
+            const float ddz = up ? __fsub_rn(V.z[k], zh) : __fsub_rn(zh, V.z[k]);
+            if (!(fabsf(ddy) <= wy) || !(fabsf(ddz) <= wz)) continue;
+            push(c, __fmul_rn(ddy, inv), __fmul_rn(ddz, inv), V.cid[k], k);
+        }
+    }
+}
+
+__device__ __forceinline__ void consider(float syu, float szu, int cu, int ku, float syd, float szd,
+                                         int cd, int kd, float& bestD, int& bcu, int& bcd,
+                                         int& biu, int& bid)
+{
+    const float ey = __fsub_rn(syu, syd), ez = __fsub_rn(szu, szd);
+    const float Dv = __fadd_rn(__fmul_rn(ey, ey), __fmul_rn(ez, ez));
+    const bool better = bcu < 0 || Dv < bestD || (Dv == bestD && (cu < bcu || (cu == bcu && cd < bcd)));
+    if (better) {
+        bestD = Dv;
+        bcu = cu;
+        bcd = cd;
+        biu = ku;
+        bid = kd;
+    }
+}
+
+// Best (down, up) pair of hit (yh, zh): least D over all admissible pairs.
+__device__ __forceinline__ void best_pair(const RowView& U, const RowView& D, float yh, float zh,
+                                          float iu, float id, float wyu, float wzu, float wyd,
+                                          float wzd, float& bestD, int& bcu, int& bcd, int& biu,
+                                          int& bid)
+{
+    CandList cu, cd;
+    collect(U, yh, zh, iu, wyu, wzu, true, cu);
+    collect(D, yh, zh, id, wyd, wzd, false, cd);
+    if (cu.n <= kList && cd.n <= kList) {
+#pragma unroll
+        for (int a = 0; a < kList; ++a) {
+            if (a >= cu.n) break;
+#pragma unroll
+            for (int b = 0; b < kList; ++b) {
+                if (b >= cd.n) break;
+                consider(cu.sy[a], cu.sz[a], cu.cid[a], cu.k[a], cd.sy[b], cd.sz[b], cd.cid[b],
+                         cd.k[b], bestD, bcu, bcd, biu, bid);
+            }
+        }
+        return;
+    }
+    // more candidates than the lists hold: evaluate every pair from the rows
+    const float my = 1e-3f * (1.0f + fabsf(yh)), mz = 1e-3f * (1.0f + fabsf(zh));
+    const int uy0 = bin_y(U.G, yh - wyu - my), uy1 = bin_y(U.G, yh + wyu + my);
+    const int uz0 = bin_z(U.G, zh - wzu - mz), uz1 = bin_z(U.G, zh + wzu + mz);
+    for (int bzu = uz0; bzu <= uz1; ++bzu) {
+        const int ua = U.bins[bzu * U.G.ny + uy0], ub = U.bins[bzu * U.G.ny + uy1 + 1];
+        for (int ku = ua; ku < ub; ++ku) {
+            const float ddyu = __fsub_rn(U.y[ku], yh);
+            const float ddzu = __fsub_rn(U.z[ku], zh);
+            if (!(fabsf(ddyu) <= wyu) || !(fabsf(ddzu) <= wzu)) continue;
+            const float syu = __fmul_rn(ddyu, iu), szu = __fmul_rn(ddzu, iu);
+            const int ccu = U.cid[ku];
+            CandList all = cd;  // re-scan the down side when its list overflowed
+            if (cd.n > kList) {
+                const int dy0 = bin_y(D.G, yh - wyd - my), dy1 = bin_y(D.G, yh + wyd + my);
+                const int dz0 = bin_z(D.G, zh - wzd - mz), dz1 = bin_z(D.G, zh + wzd + mz);
+                for (int bzd = dz0; bzd <= dz1; ++bzd) {
+                    const int da = D.bins[bzd * D.G.ny + dy0], db = D.bins[bzd * D.G.ny + dy1 + 1];
+                    for (int kd = da; kd < db; ++kd) {
+                        const float ddyd = __fsub_rn(yh, D.y[kd]);
+                        const float ddzd = __fsub_rn(zh, D.z[kd]);
+                        if (!(fabsf(ddyd) <= wyd) || !(fabsf(ddzd) <= wzd)) continue;
+                        consider(syu, szu, ccu, ku, __fmul_rn(ddyd, id), __fmul_rn(ddzd, id),
+                                 D.cid[kd], kd, bestD, bcu, bcd, biu, bid);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < kList; ++b)
+                    if (b < all.n)
+                        consider(syu, szu, ccu, ku, all.sy[b], all.sz[b], all.cid[b], all.k[b],
+                                 bestD, bcu, bcd, biu, bid);
+            }
+        }
+    }
+}
+
+// One thread per sorted hit; the adjacent rows' hits, bins and grids are read
+// through the L1 cache (the hits of a block share one or two rows).
 __global__ void __launch_bounds__(kNbThreads) k_neighbours(Launch L)
 {
-    for (int g = blockIdx.x; g < L.RS; g += gridDim.x) {
-        const int gs = g / L.R;
-        const int r = g - gs * L.R;
-        const int base = L.row_off[g];
-        const int n = L.row_off[g + 1] - base;
+    const int n_hits = L.row_off[L.RS];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_hits; i += gridDim.x * blockDim.x) {
+        const int hr = __ldg(&L.hrow[i]);
+        const int gs = hr >> 8, r = hr & 255;
         if (r == 0 || r == L.R - 1) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                L.up[base + i] = -1;
-                L.dn[base + i] = -1;
-            }
+            L.up[i] = -1;
+            L.dn[i] = -1;
             continue;
         }
-        const float xh = L.row_x[r], xu = L.row_x[r + 1], xd = L.row_x[r - 1];
-        const float dxu = __fsub_rn(xu, xh), dxd = __fsub_rn(xh, xd);
+        const int g = gs * L.R + r;
+        const float xh = __ldg(&L.xr[r]), xu = __ldg(&L.xr[r + 1]), xd = __ldg(&L.xr[r - 1]);
+        const float iu = __frcp_rn(__fsub_rn(xu, xh)), id = __frcp_rn(__fsub_rn(xh, xd));
         const float wyu = __fmul_rn(L.slope_win_y, fabsf(__fsub_rn(xu, xh)));
         const float wzu = __fmul_rn(L.slope_win_z, fabsf(__fsub_rn(xu, xh)));
         const float wyd = __fmul_rn(L.slope_win_y, fabsf(__fsub_rn(xd, xh)));
         const float wzd = __fmul_rn(L.slope_win_z, fabsf(__fsub_rn(xd, xh)));
-        const RowGrid Gu = L.grid[g + 1], Gd = L.grid[g - 1];
-        const int bu = L.row_off[g + 1], bd = L.row_off[g - 1];
-        const int* binu = L.bin_start + Gu.bin_off;
-        const int* bind = L.bin_start + Gd.bin_off;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const float yh = L.hy[base + i], zh = L.hz[base + i];
-            // bins covering the windows, widened by a margin so that rounding
-            // of the bounds can never drop an admissible candidate
-            const float my = 1e-3f * (1.0f + fabsf(yh)), mz = 1e-3f * (1.0f + fabsf(zh));
-            const int uy0 = bin_y(Gu, yh - wyu - my), uy1 = bin_y(Gu, yh + wyu + my);
-            const int uz0 = bin_z(Gu, zh - wzu - mz), uz1 = bin_z(Gu, zh + wzu + mz);
-            const int dy0 = bin_y(Gd, yh - wyd - my), dy1 = bin_y(Gd, yh + wyd + my);
-            const int dz0 = bin_z(Gd, zh - wzd - mz), dz1 = bin_z(Gd, zh + wzd + mz);
-            float bestD = 0.0f;
-            int bcu = -1, bcd = -1, biu = -1, bid = -1;
-            for (int bzu = uz0; bzu <= uz1; ++bzu) {
-                const int ua = binu[bzu * Gu.ny + uy0], ub = binu[bzu * Gu.ny + uy1 + 1];
-                for (int ku = ua; ku < ub; ++ku) {
-                    const float ddyu = __fsub_rn(L.hy[bu + ku], yh);
-                    const float ddzu = __fsub_rn(L.hz[bu + ku], zh);
-                    if (!(fabsf(ddyu) <= wyu) || !(fabsf(ddzu) <= wzu)) continue;
-                    const float syu = __fdiv_rn(ddyu, dxu), szu = __fdiv_rn(ddzu, dxu);
-                    const int cu = L.hcid[bu + ku];
-                    for (int bzd = dz0; bzd <= dz1; ++bzd) {
-                        const int da = bind[bzd * Gd.ny + dy0], db = bind[bzd * Gd.ny + dy1 + 1];
-                        for (int kd = da; kd < db; ++kd) {
-                            const float ddyd = __fsub_rn(yh, L.hy[bd + kd]);
-                            const float ddzd = __fsub_rn(zh, L.hz[bd + kd]);
-                            if (!(fabsf(ddyd) <= wyd) || !(fabsf(ddzd) <= wzd)) continue;
-                            const float syd = __fdiv_rn(ddyd, dxd), szd = __fdiv_rn(ddzd, dxd);
-                            const float ey = __fsub_rn(syu, syd), ez = __fsub_rn(szu, szd);
-                            const float D = __fadd_rn(__fmul_rn(ey, ey), __fmul_rn(ez, ez));
-                            const int cd = L.hcid[bd + kd];
-                            const bool better = bcu < 0 || D < bestD ||
-                                                (D == bestD && (cu < bcu || (cu == bcu && cd < bcd)));
-                            if (better) {
-                                bestD = D;
-                                bcu = cu;
-                                bcd = cd;
-                                biu = ku;
-                                bid = kd;
-                            }
-                        }
-                    }
-                }
-            }
-            const bool link = bcu >= 0 && bestD <= L.d_max;
-            L.up[base + i] = link ? (int16_t)biu : (int16_t)-1;
-            L.dn[base + i] = link ? (int16_t)bid : (int16_t)-1;
-        }
+        RowView U, D;
+        U.G = L.grid[g + 1];
+        D.G = L.grid[g - 1];
+        const int bu = __ldg(&L.row_off[g + 1]), bd = __ldg(&L.row_off[g - 1]);
+        U.y = L.hy + bu;
+        U.z = L.hz + bu;
+        U.cid = L.hcid + bu;
+        U.bins = L.bin_start + U.G.bin_off;
+        D.y = L.hy + bd;
+        D.z = L.hz + bd;
+        D.cid = L.hcid + bd;
+        D.bins = L.bin_start + D.G.bin_off;
+        const float yh = L.hy[i], zh = L.hz[i];
+        float bestD = 0.0f;
+        int bcu = -1, bcd = -1, biu = -1, bid = -1;
+        best_pair(U, D, yh, zh, iu, id, wyu, wzu, wyd, wzd, bestD, bcu, bcd, biu, bid);
+        const bool link = bcu >= 0 && bestD <= L.d_max;
+        L.up[i] = link ? (int16_t)biu : (int16_t)-1;
+        L.dn[i] = link ? (int16_t)bid : (int16_t)-1;
     }
 }
 
@@ -127,13 +221,19 @@ __global__ void __launch_bounds__(kCsThreads) k_clean_starts(Launch L)
             const int li = i - L.row_off[g];
             const int u = L.up[i], d = L.dn[i];
             int16_t uc = -1, dc = -1;
+            int ug = -1;
             if (u >= 0) {
                 n_link++;
-                if (L.dn[L.row_off[g + 1] + u] == li) uc = (int16_t)u;
+                const int gu = L.row_off[g + 1] + u;
+                if (L.dn[gu] == li) {
+                    uc = (int16_t)u;
+                    ug = gu;
+                }
             }
             if (d >= 0 && L.up[L.row_off[g - 1] + d] == li) dc = (int16_t)d;
             L.upc[i] = uc;
             L.dnc[i] = dc;
+            L.upg[i] = ug;
             is_start[k] = uc >= 0 && dc < 0;
         }
     }
@@ -190,12 +290,16 @@ __global__ void __launch_bounds__(kCsThreads) k_clean_starts(Launch L)
 
 }  // namespace
 
-void launch_finder(const Launch& L, void* stream_)
+void launch_finder(const Launch& L, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
-    const int blocks = L.RS < 148 * 16 ? L.RS : 148 * 16;
-    k_neighbours<<<blocks > 0 ? blocks : 1, kNbThreads, 0, stream>>>(L);
+    long long nb = (L.n_total + kNbThreads - 1) / kNbThreads;
+    if (nb > 148 * 64) nb = 148 * 64;
+    if (nb < 1) nb = 1;
+    k_neighbours<<<(int)nb, kNbThreads, 0, stream>>>(L);
+    hook_after(hook, "k_neighbours");
     k_clean_starts<<<L.n_hit_tiles, kCsThreads, 0, stream>>>(L);
+    hook_after(hook, "k_clean_starts");
 }
 
 }  // namespace tpc

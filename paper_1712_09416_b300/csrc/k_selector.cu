@@ -39,12 +39,11 @@ __global__ void k_sel_decide(Launch L)
         if (H.chain_len >= L.min_chain && H.valid) {
             const unsigned long long key = ((unsigned long long)H.nhits << 32) |
                                            (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
-            const int16_t* rowhit = L.tl_rowhit + (size_t)t * L.R;
-            const int gbase = gs * L.R;
+            const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
             int first_own = -1;
             for (int r = H.first; r <= H.last; ++r) {
-                const int k = rowhit[r];
-                if (k >= 0 && L.weight[L.row_off[gbase + r] + k] == key) {
+                const int h = rowhit[r];
+                if (h >= 0 && L.weight[h] == key) {
                     if (first_own < 0) first_own = r;
                     ++nown;
                 }
@@ -183,30 +182,30 @@ __global__ void k_sel_write(Launch L)
         L.k_hit_off[j] = off;
         const unsigned long long key = ((unsigned long long)H.nhits << 32) |
                                        (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
-        const int16_t* rowhit = L.tl_rowhit + (size_t)t * L.R;
-        const int gbase = gs * L.R;
+        const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
         for (int r = H.first; r <= H.last; ++r) {
-            const int k = rowhit[r];
-            if (k < 0) continue;
-            const int h = L.row_off[gbase + r] + k;
-            if (L.weight[h] == key) L.k_hit_cid[off++] = L.hcid[h];
+            const int h = rowhit[r];
+            if (h >= 0 && L.weight[h] == key) L.k_hit_cid[off++] = L.hcid[h];
         }
     }
 }
 
 }  // namespace
 
-void launch_selector(const Launch& L, void* stream_)
+void launch_selector(const Launch& L, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
     int blocks = (L.t_cap + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
     if (blocks < 1) blocks = 1;
     k_sel_decide<<<blocks, 256, 0, stream>>>(L);
+    hook_after(hook, "k_sel_decide");
     const size_t sm = kMaxSectorTracks * (sizeof(unsigned long long) + sizeof(int));
     cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_sel_sort<<<L.S, kSortThreads, sm, stream>>>(L);
+    hook_after(hook, "k_sel_sort");
     k_sel_write<<<blocks, 256, 0, stream>>>(L);
+    hook_after(hook, "k_sel_write");
 }
 
 }  // namespace tpc

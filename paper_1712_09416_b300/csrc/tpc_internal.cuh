@@ -8,11 +8,13 @@
 //               sees one flat list of sectors
 //   hits        sorted by (sector, row, bin, cid): hy, hz (f32), hcid (event
 //               cid), hrow (sector << 8 | row); bins hold row-local offsets
-//   links       up/dn/upc/dnc as int16 row-local indices into the adjacent row
-//   tracklets   one per start hit: header + rowhit[R] (int16 row-local index)
+//   links       up/dn/upc/dnc as int16 row-local indices into the adjacent row,
+//               upg the cleaned up link as a global hit index
+//   tracklets   one per start hit: header + rowhit[R] (global hit index)
 //   outputs     tracks in canonical order, hit cids
 #pragma once
 #include <cstdint>
+#include <vector_types.h>
 
 namespace tpc {
 
@@ -60,7 +62,8 @@ struct Counters {
     int n_track_hits;
     int n_bins;
     int ticket_rows, ticket_hits, ticket_sectors;
-    int pad[16];
+    int tl_next;          // work counter of the persistent constructor
+    int pad[15];
 };
 
 // Everything a kernel needs, passed by value.
@@ -75,7 +78,9 @@ struct Launch {
     int t_cap;           // tracklet slots
     // geometry and field
     float tan_half, z_max, kB;   // kB = KAPPA * bz
-    float row_x[kMaxRows];
+    // pad-row radii live in device memory (indexing a kernel-parameter array
+    // with a lane-dependent row serialises on the constant cache)
+    const float* xr;            // [R]
     // parameters
     float sy2, sz2;              // measurement variances
     float slope_win_y, slope_win_z, d_max, chi2_hit, sin_max, edge_margin;
@@ -95,10 +100,12 @@ struct Launch {
     float* hy; float* hz; int* hcid; int* hrow; // sorted
     int* bin_start;
     int16_t* up; int16_t* dn; int16_t* upc; int16_t* dnc;
+    int* upg;                   // [N] cleaned up link, global index or -1
     unsigned long long* weight;
     int* starts;                // [t_cap] global sorted index
     TrackletHdr* tl;            // [t_cap]
-    int16_t* tl_rowhit;         // [t_cap * R]
+    int* tl_rowhit;             // [t_cap * R] global hit index or -1
+    float2* tl_yz;              // [t_cap * R] coordinates of the rowhit hits
     unsigned long long* tl_key; // [t_cap] sector-local sort key or ~0
     int* tl_nown;               // [t_cap]
     int* tl_out;                // [t_cap] output track index or -1
@@ -188,10 +195,20 @@ __device__ __forceinline__ int bin_z(const RowGrid& G, float z)
     return min(max(b, 0), G.nz - 1);
 }
 
+// Profiling hook: called on the host right after each kernel is enqueued.
+struct KernelHook {
+    void (*after)(void* user, const char* name);
+    void* user;
+};
+inline void hook_after(const KernelHook* h, const char* name)
+{
+    if (h && h->after) h->after(h->user, name);
+}
+
 // host-side launchers (one translation unit each)
-void launch_binning(const Launch& L, void* stream);
-void launch_finder(const Launch& L, void* stream);
-void launch_constructor(const Launch& L, void* stream);
-void launch_selector(const Launch& L, void* stream);
+void launch_binning(const Launch& L, void* stream, const KernelHook* hook);
+void launch_finder(const Launch& L, void* stream, const KernelHook* hook);
+void launch_constructor(const Launch& L, void* stream, const KernelHook* hook);
+void launch_selector(const Launch& L, void* stream, const KernelHook* hook);
 
 }  // namespace tpc

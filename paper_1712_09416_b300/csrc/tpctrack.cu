@@ -15,6 +15,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -96,14 +97,26 @@ struct Slot {
     unsigned long long* weight;
     int* starts;
     TrackletHdr* tl;
-    int16_t* tl_rowhit;
+    int* tl_rowhit;
+    float2* tl_yz;
+    int* upg;
     unsigned long long* tl_key;
     int *tl_nown, *tl_out, *tl_hitoff, *sec_trk_off, *sec_hit_off;
     int *k_sector, *k_ndf, *k_hit_off, *k_hit_cid;
     float *k_x, *k_param, *k_cov, *k_chi2;
     // host side
-    void* desc_host = nullptr;  // pinned mirror of desc_dev
+    void* desc_ring[2] = {nullptr, nullptr};  // pinned mirrors of desc_dev, used in turn
+    cudaEvent_t desc_done[2] = {nullptr, nullptr};
+    bool desc_used[2] = {false, false};
+    int desc_turn = 0;
+    void* desc_host = nullptr;  // the mirror of the current launch
     size_t desc_bytes = 0;
+    // profiling: one event after every kernel of every launch while enabled
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_used = 0;
+    std::vector<std::pair<std::string, std::pair<size_t, size_t>>> prof_marks;  // name, (ev0, ev1)
+    size_t prof_last = 0;
     Counters* cnt_host = nullptr;
     HostOut out;
     cudaStream_t stream = nullptr;
@@ -145,6 +158,7 @@ struct tpc_track_ctx {
     bool stop = false;
     uint64_t next_ticket = 1;
     std::atomic<int> direct_busy{0};
+    bool trace = false;  // TPC_TRACE=1: one stderr line per served launch
 };
 
 namespace tpc {
@@ -172,7 +186,7 @@ Caps make_caps(const tpc_track_config& c)
     k.s = k.e * 36;
     k.rs = (long long)k.s * k.r;
     k.bins = k.n / 2 + 2 * k.rs + 16;
-    k.t = (int)std::min<long long>(k.n / 4 + 4096, 0x7fffffffLL / 256);
+    k.t = (int)std::min<long long>(k.n / 8 + 4096, 0x7fffffffLL / 256);
     k.row_tiles = k.rs / kTileRows + 2;
     k.hit_tiles = k.n / kTileHits + 2;
     return k;
@@ -193,7 +207,8 @@ size_t layout(Slot& s, char* base)
     s.in_z = (float*)take(4 * k.n);
     s.in_row = (uint16_t*)take(2 * k.n);
     s.in_sec = (uint16_t*)take(2 * k.n);
-    s.desc_bytes = sizeof(EventDesc) * k.e + sizeof(long long) * (k.e + 1) + sizeof(int) * k.s + 64;
+    s.desc_bytes = sizeof(EventDesc) * k.e + sizeof(long long) * (k.e + 1) + sizeof(int) * k.s +
+                   sizeof(float) * kMaxRows + 64;
     s.desc_dev = take(s.desc_bytes);
     s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (2 * k.rs + 2 * k.s) + 8 * (k.row_tiles + k.hit_tiles + k.s) + 4096;
     s.zero_dev = take(s.zero_cap);
@@ -214,7 +229,9 @@ size_t layout(Slot& s, char* base)
     s.weight = (unsigned long long*)take(8 * k.n);
     s.starts = (int*)take(4 * (size_t)k.t);
     s.tl = (TrackletHdr*)take(sizeof(TrackletHdr) * (size_t)k.t);
-    s.tl_rowhit = (int16_t*)take(2 * (size_t)k.t * k.r);
+    s.tl_rowhit = (int*)take(4 * (size_t)k.t * k.r);
+    s.tl_yz = (float2*)take(8 * (size_t)k.t * k.r);
+    s.upg = (int*)take(4 * k.n);
     s.tl_key = (unsigned long long*)take(8 * (size_t)k.t);
     s.tl_nown = (int*)take(4 * (size_t)k.t);
     s.tl_out = (int*)take(4 * (size_t)k.t);
@@ -245,7 +262,11 @@ int alloc_slot(tpc_track_ctx* ctx, Slot& s)
     s.dev = base;
     layout(s, base);
     const Caps& k = s.caps;
-    CUDA_TRY(ctx, cudaMallocHost(&s.desc_host, s.desc_bytes));
+    for (int i = 0; i < 2; ++i) {
+        CUDA_TRY(ctx, cudaMallocHost(&s.desc_ring[i], s.desc_bytes));
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&s.desc_done[i], cudaEventDisableTiming));
+    }
+    s.desc_host = s.desc_ring[0];
     CUDA_TRY(ctx, cudaMallocHost((void**)&s.cnt_host, sizeof(Counters)));
     CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.sector, 4 * (size_t)k.t));
     CUDA_TRY(ctx, cudaMallocHost((void**)&s.out.x, 4 * (size_t)k.t));
@@ -266,7 +287,11 @@ void free_slot(Slot& s)
 {
     if (s.stream) cudaStreamSynchronize(s.stream);
     if (s.dev) cudaFree(s.dev);
-    if (s.desc_host) cudaFreeHost(s.desc_host);
+    for (int i = 0; i < 2; ++i) {
+        if (s.desc_ring[i]) cudaFreeHost(s.desc_ring[i]);
+        if (s.desc_done[i]) cudaEventDestroy(s.desc_done[i]);
+    }
+    for (cudaEvent_t e : s.prof_pool) cudaEventDestroy(e);
     if (s.cnt_host) cudaFreeHost(s.cnt_host);
     void* hp[] = {s.out.sector, s.out.x, s.out.param, s.out.cov, s.out.chi2, s.out.ndf,
                   s.out.hit_off, s.out.hit_cid, s.out.sec_trk_off, s.out.sec_hit_off,
@@ -295,6 +320,18 @@ int check_geometry(tpc_track_ctx* ctx, const Slot& s, const tpc_geometry* g)
     return TPC_OK;
 }
 
+// Record the next profiling event on the slot's stream; returns its index.
+size_t prof_event(Slot& s)
+{
+    if (s.prof_used == s.prof_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        s.prof_pool.push_back(e);
+    }
+    cudaEventRecord(s.prof_pool[s.prof_used], s.stream);
+    return s.prof_used++;
+}
+
 // Enqueue the whole device pipeline of one launch on the slot's stream.
 int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const tpc_geometry* g,
             float bz)
@@ -316,6 +353,10 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
         return fail(ctx, TPC_EINVAL, "clusters in the launch exceed max_clusters_per_event");
     const int S = n_sec * n_ev;
     if (S > s.caps.s) return fail(ctx, TPC_EINVAL, "sectors in the launch exceed the arena");
+    // descriptor mirror of this launch: wait until its previous copy is done
+    s.desc_turn ^= 1;
+    if (s.desc_used[s.desc_turn]) CUDA_TRY(ctx, cudaEventSynchronize(s.desc_done[s.desc_turn]));
+    s.desc_host = s.desc_ring[s.desc_turn];
     LaunchInfo& I = s.info;
     I = LaunchInfo();
     I.n_ev = n_ev;
@@ -325,6 +366,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     EventDesc* dh = (EventDesc*)s.desc_host;
     long long* offh = (long long*)((char*)s.desc_host + sizeof(EventDesc) * s.caps.e);
     int* sech = (int*)((char*)offh + sizeof(long long) * (s.caps.e + 1));
+    float* xrh = (float*)(sech + s.caps.s);
+    for (int r = 0; r < g->n_rows; ++r) xrh[r] = g->row_x[r];
     long long off = 0;
     for (int i = 0; i < n_ev; ++i) {
         EventDesc d;
@@ -366,7 +409,6 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.tan_half = tanf(g->half_angle_rad);
     L.z_max = g->z_max;
     L.kB = (float)(kKappa * (double)bz);
-    for (int r = 0; r < g->n_rows; ++r) L.row_x[r] = g->row_x[r];
     const tpc_track_params& P = ctx->cfg.params;
     L.sy2 = P.meas_sigma_y * P.meas_sigma_y;
     L.sz2 = P.meas_sigma_z * P.meas_sigma_z;
@@ -386,6 +428,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.ev = (EventDesc*)s.desc_dev;
     L.ev_off = (long long*)((char*)s.desc_dev + sizeof(EventDesc) * s.caps.e);
     L.sec_event = (int*)((char*)L.ev_off + sizeof(long long) * (s.caps.e + 1));
+    L.xr = (const float*)(L.sec_event + s.caps.s);
     // zero region laid out for this launch
     {
         size_t zo = 0;
@@ -427,6 +470,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.starts = s.starts;
     L.tl = s.tl;
     L.tl_rowhit = s.tl_rowhit;
+    L.tl_yz = s.tl_yz;
+    L.upg = s.upg;
     L.tl_key = s.tl_key;
     L.tl_nown = s.tl_nown;
     L.tl_out = s.tl_out;
@@ -443,6 +488,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.k_hit_cid = s.k_hit_cid;
     // inputs
     CUDA_TRY(ctx, cudaMemcpyAsync(s.desc_dev, s.desc_host, s.desc_bytes, cudaMemcpyHostToDevice, s.stream));
+    CUDA_TRY(ctx, cudaEventRecord(s.desc_done[s.desc_turn], s.stream));
+    s.desc_used[s.desc_turn] = true;
     for (int i = 0; i < n_ev; ++i) {
         if (ev[i].on_device || ev[i].n == 0) continue;
         const size_t n = (size_t)ev[i].n;
@@ -452,10 +499,23 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
         CUDA_TRY(ctx, cudaMemcpyAsync(s.in_row + o, ev[i].row, 2 * n, cudaMemcpyHostToDevice, s.stream));
         CUDA_TRY(ctx, cudaMemcpyAsync(s.in_sec + o, ev[i].sector, 2 * n, cudaMemcpyHostToDevice, s.stream));
     }
-    launch_binning(L, s.stream);
-    launch_finder(L, s.stream);
-    launch_constructor(L, s.stream);
-    launch_selector(L, s.stream);
+    KernelHook hook{nullptr, nullptr};
+    if (s.prof) {
+        hook.after = [](void* user, const char* name) {
+            Slot& sl = *(Slot*)user;
+            const size_t i0 = sl.prof_last;
+            const size_t i1 = prof_event(sl);
+            sl.prof_marks.push_back({name, {i0, i1}});
+            sl.prof_last = i1;
+        };
+        hook.user = &s;
+        s.prof_last = prof_event(s);
+    }
+    const KernelHook* hk = s.prof ? &hook : nullptr;
+    launch_binning(L, s.stream, hk);
+    launch_finder(L, s.stream, hk);
+    launch_constructor(L, s.stream, hk);
+    launch_selector(L, s.stream, hk);
     CUDA_TRY(ctx, cudaGetLastError());
     CUDA_TRY(ctx, cudaMemcpyAsync(s.cnt_host, L.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s.stream));
     CUDA_TRY(ctx, cudaEventRecord(s.done_ev, s.stream));
@@ -584,7 +644,7 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* 
         if (stage == TPC_DUMP_STARTS) {
             for (auto& o : order) put(&o.first, 4);
         } else {
-            std::vector<int16_t> rh((size_t)R);
+            std::vector<int32_t> rh((size_t)R);
             int32_t count = 0;
             for (auto& o : order)
                 if (tl[o.second].chain_len >= ctx->cfg.params.min_chain) ++count;
@@ -606,11 +666,10 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* 
                 std::memcpy(D.cov, H.C, sizeof(D.cov));
                 D.chi2 = H.chi2;
                 put(&D, sizeof(D));
-                CUDA_TRY(ctx, cudaMemcpy(rh.data(), s.tl_rowhit + (size_t)o.second * R, 2 * (size_t)R, cudaMemcpyDeviceToHost));
+                CUDA_TRY(ctx, cudaMemcpy(rh.data(), s.tl_rowhit + (size_t)o.second * R, 4 * (size_t)R, cudaMemcpyDeviceToHost));
                 std::vector<int32_t> rc(R, -1);
-                const int gbase = D.sector * R;
                 for (int r = H.first; r <= H.last && r >= 0; ++r)
-                    if (rh[r] >= 0) rc[r] = hcid[row_off[gbase + r] + rh[r]];
+                    if (rh[r] >= 0 && rh[r] < nh) rc[r] = hcid[rh[r]];
                 put(rc.data(), 4 * (size_t)R);
             }
         }
@@ -661,38 +720,57 @@ void worker(tpc_track_ctx* ctx, Slot* s)
         for (auto& q : batch) evs.push_back(q.ev);
         tpc_geometry g = batch.front().geom;
         g.row_x = batch.front().row_x.data();
+        const auto t0 = std::chrono::steady_clock::now();
         int rc = enqueue(ctx, *s, (int)evs.size(), evs.data(), &g, batch.front().bz);
+        const auto t1 = std::chrono::steady_clock::now();
         if (rc == TPC_OK) rc = collect(ctx, *s);
-        std::lock_guard<std::mutex> lk(ctx->mu);
+        const auto t2 = std::chrono::steady_clock::now();
+        // copy each event's tracks into its own buffers outside the lock
+        std::vector<std::unique_ptr<TicketResult>> done(batch.size());
         for (size_t i = 0; i < batch.size(); ++i) {
-            auto it = ctx->results.find(batch[i].ticket);
-            if (it == ctx->results.end()) continue;
-            TicketResult& R = *it->second;
+            auto R = std::make_unique<TicketResult>();
             if (rc == TPC_OK) {
                 const tpc_tracks& T = s->tracks[i];
                 const size_t n = (size_t)T.n_tracks;
                 const size_t nh = n ? (size_t)T.hit_off[n] : 0;
-                R.sector.assign(T.sector, T.sector + n);
-                R.x.assign(T.x, T.x + n);
-                R.param.assign(T.param, T.param + 5 * n);
-                R.cov.assign(T.cov, T.cov + 15 * n);
-                R.chi2.assign(T.chi2, T.chi2 + n);
-                R.ndf.assign(T.ndf, T.ndf + n);
-                R.hit_off.assign(T.hit_off, T.hit_off + n + 1);
-                R.hit_cid.assign(T.hit_cid, T.hit_cid + nh);
-                R.view.n_tracks = (int64_t)n;
-                R.view.sector = R.sector.data();
-                R.view.x = R.x.data();
-                R.view.param = R.param.data();
-                R.view.cov = R.cov.data();
-                R.view.chi2 = R.chi2.data();
-                R.view.ndf = R.ndf.data();
-                R.view.hit_off = R.hit_off.data();
-                R.view.hit_cid = R.hit_cid.data();
+                R->sector.assign(T.sector, T.sector + n);
+                R->x.assign(T.x, T.x + n);
+                R->param.assign(T.param, T.param + 5 * n);
+                R->cov.assign(T.cov, T.cov + 15 * n);
+                R->chi2.assign(T.chi2, T.chi2 + n);
+                R->ndf.assign(T.ndf, T.ndf + n);
+                R->hit_off.assign(T.hit_off, T.hit_off + n + 1);
+                R->hit_cid.assign(T.hit_cid, T.hit_cid + nh);
+                R->view.n_tracks = (int64_t)n;
+                R->view.sector = R->sector.data();
+                R->view.x = R->x.data();
+                R->view.param = R->param.data();
+                R->view.cov = R->cov.data();
+                R->view.chi2 = R->chi2.data();
+                R->view.ndf = R->ndf.data();
+                R->view.hit_off = R->hit_off.data();
+                R->view.hit_cid = R->hit_cid.data();
             }
-            R.status = rc;
+            R->status = rc;
+            done[i] = std::move(R);
+        }
+        // fill the tickets' own result objects in place (pollers hold pointers
+        // to them); the swapped-out placeholders are freed outside the lock
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        for (size_t i = 0; i < batch.size(); ++i) {
+            auto it = ctx->results.find(batch[i].ticket);
+            if (it == ctx->results.end()) continue;
+            std::swap(*it->second, *done[i]);
+        }
+        if (ctx->trace) {
+            const auto t3 = std::chrono::steady_clock::now();
+            auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+            std::fprintf(stderr, "[tpctrack slot %d] events %zu enqueue %.3f ms, device+collect %.3f ms, publish %.3f ms, queue %zu\n",
+                         s->id, batch.size(), ms(t0, t1), ms(t1, t2), ms(t2, t3), ctx->queue.size());
         }
         ctx->cv_done.notify_all();
+        lk.unlock();
+        done.clear();
     }
 }
 
@@ -710,7 +788,7 @@ void tpc_track_default_params(tpc_track_params* p)
     p->meas_sigma_z = 0.1f;
     p->slope_win_y = 2.0f;
     p->slope_win_z = 2.0f;
-    p->d_max = 0.36f;
+    p->d_max = 0.6f;
     p->chi2_hit = 16.0f;
     p->max_gap = 5;
     p->min_chain = 3;
@@ -741,6 +819,8 @@ int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out)
         return TPC_EINVAL;
     auto ctx = std::make_unique<tpc_track_ctx>();
     ctx->cfg = *cfg;
+    const char* tr = std::getenv("TPC_TRACE");
+    ctx->trace = tr && tr[0] == '1';
     if (cudaSetDevice(cfg->device) != cudaSuccess) {
         cudaGetLastError();
         return TPC_ECUDA;
@@ -782,10 +862,8 @@ int tpc_track_launch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev, const
     if (!ctx->workers.empty()) return fail(ctx, TPC_EBUSY, "context is serving submitted events");
     cudaSetDevice(ctx->cfg.device);
     Slot& s = *ctx->slots[0];
-    if (s.info.pending) {
-        cudaEventSynchronize(s.done_ev);
-        s.info.pending = false;
-    }
+    s.info.pending = false;  // results of an uncollected launch are dropped
+    if (s.prof && s.prof_used > 60000) return fail(ctx, TPC_EINVAL, "profiling buffer full");
     return enqueue(ctx, s, n_ev, ev, geom, bz);
 }
 
@@ -870,11 +948,52 @@ int tpc_track_poll(tpc_track_ctx* ctx, uint64_t ticket, int timeout_us, tpc_trac
 int tpc_track_release(tpc_track_ctx* ctx, uint64_t ticket)
 {
     if (!ctx) return TPC_EINVAL;
+    std::unique_ptr<TicketResult> gone;  // freed after the lock is released
     std::lock_guard<std::mutex> lk(ctx->mu);
     auto it = ctx->results.find(ticket);
     if (it == ctx->results.end()) return fail(ctx, TPC_EINVAL, "unknown ticket");
     if (it->second->status == TPC_EBUSY) return fail(ctx, TPC_EBUSY, "ticket still in flight");
+    gone = std::move(it->second);
     ctx->results.erase(it);
+    return TPC_OK;
+}
+
+int tpc_track_set_profiling(tpc_track_ctx* ctx, int on)
+{
+    if (!ctx) return TPC_EINVAL;
+    Slot& s = *ctx->slots[0];
+    if (s.stream) CUDA_TRY(ctx, cudaStreamSynchronize(s.stream));
+    s.prof = on != 0;
+    s.prof_used = 0;
+    s.prof_marks.clear();
+    return TPC_OK;
+}
+
+int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, int* n)
+{
+    if (!ctx || !n) return TPC_EINVAL;
+    Slot& s = *ctx->slots[0];
+    cudaSetDevice(ctx->cfg.device);
+    CUDA_TRY(ctx, cudaStreamSynchronize(s.stream));
+    std::vector<tpc_kernel_time> acc;
+    for (auto& m : s.prof_marks) {
+        float ms = 0.0f;
+        CUDA_TRY(ctx, cudaEventElapsedTime(&ms, s.prof_pool[m.second.first], s.prof_pool[m.second.second]));
+        tpc_kernel_time* t = nullptr;
+        for (auto& a : acc)
+            if (m.first == a.name) t = &a;
+        if (!t) {
+            tpc_kernel_time z;
+            std::memset(&z, 0, sizeof(z));
+            std::snprintf(z.name, sizeof(z.name), "%s", m.first.c_str());
+            acc.push_back(z);
+            t = &acc.back();
+        }
+        t->total_ms += ms;
+        t->launches += 1;
+    }
+    *n = (int)acc.size();
+    for (int i = 0; i < (int)acc.size() && i < cap; ++i) out[i] = acc[i];
     return TPC_OK;
 }
 

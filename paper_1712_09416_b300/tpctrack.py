@@ -23,6 +23,7 @@ TPC_DUMP_LINKS, TPC_DUMP_CLEAN, TPC_DUMP_STARTS, TPC_DUMP_TRACKLETS, TPC_DUMP_WE
 EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "tpc_track_batch",
             "tpc_track_launch", "tpc_track_results", "tpc_track_submit", "tpc_track_poll",
             "tpc_track_release", "tpc_track_get_counters", "tpc_track_stream",
+            "tpc_track_set_profiling", "tpc_track_kernel_times",
             "tpc_track_debug_dump", "tpc_track_last_error", "tpc_track_destroy"]
 
 
@@ -72,6 +73,10 @@ class tpc_track_counters(C.Structure):
         "n_valid_tracklets", "n_tracklet_hits", "n_tracks", "n_track_hits")]
 
 
+class tpc_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("total_ms", C.c_double), ("launches", C.c_int64)]
+
+
 class tpc_dump_tracklet(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("start_cid", "sector", "valid", "nhits", "first_row",
                                          "last_row", "ndf", "pad")] + \
@@ -105,6 +110,9 @@ def lib():
         L.tpc_track_get_counters.argtypes = [P, C.POINTER(tpc_track_counters)]
         L.tpc_track_stream.argtypes = [P]
         L.tpc_track_stream.restype = P
+        L.tpc_track_set_profiling.argtypes = [P, C.c_int]
+        L.tpc_track_kernel_times.argtypes = [P, C.POINTER(tpc_kernel_time), C.c_int,
+                                             C.POINTER(C.c_int)]
         L.tpc_track_debug_dump.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_size_t)]
         L.tpc_track_last_error.argtypes = [P]
         L.tpc_track_last_error.restype = C.c_char_p
@@ -275,6 +283,18 @@ def tpc_track_get_counters(ctx) -> dict:
 
 def tpc_track_stream(ctx) -> int:
     return lib().tpc_track_stream(ctx) or 0
+
+
+def tpc_track_set_profiling(ctx, on: bool):
+    _check(ctx, lib().tpc_track_set_profiling(ctx, 1 if on else 0))
+
+
+def tpc_track_kernel_times(ctx) -> dict:
+    """{kernel name: (total ms, launches)} recorded since profiling was enabled."""
+    arr = (tpc_kernel_time * 64)()
+    n = C.c_int()
+    _check(ctx, lib().tpc_track_kernel_times(ctx, arr, 64, C.byref(n)))
+    return {arr[i].name.decode(): (arr[i].total_ms, int(arr[i].launches)) for i in range(n.value)}
 
 
 def tpc_track_debug_dump(ctx, stage: int) -> bytes:

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_params_without_gpu(lib):
     from paper_1712_09416_b300 import tpctrack
     p = tpctrack.tpc_track_default_params()
-    assert p.chi2_hit == 16.0 and p.max_gap == 5 and abs(p.d_max - 0.36) < 1e-7
+    assert p.chi2_hit == 16.0 and p.max_gap == 5 and abs(p.d_max - 0.6) < 1e-7
     assert p.min_tracklet_hits == 10 and abs(p.sin_max - 0.99) < 1e-7
 
 

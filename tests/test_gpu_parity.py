@@ -219,7 +219,8 @@ def test_served_results_equal_alone(tp):
             keep.append((g, kx, c, k))
             tickets.append(tp.tpc_track_submit(s.ctx, c, g, float(e.bz)))
         for a, tk in zip(alone, tickets):
-            b = tp.tpc_track_poll(s.ctx, tk, -1)
+            b = tp.tpc_track_poll(s.ctx, tk, 60_000_000)
+            assert b is not None, "served ticket not done within 60 s"
             for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
                 assert np.array_equal(getattr(a, f), getattr(b, f)), f
             tp.tpc_track_release(s.ctx, tk)
