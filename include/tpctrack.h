@@ -218,6 +218,35 @@ typedef struct {
 int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t cap,
                          size_t* used);
 
+/* Neighbour links of one event without any allocation (this entry point has
+ * no counterpart in the paper; it serves callers that cannot allocate device
+ * memory: code running inside a framework that owns the device allocator,
+ * code under a hard memory budget where a cudaMalloc may fail at any moment,
+ * and callers that must avoid the device-wide synchronisation cudaMalloc and
+ * cudaFree can imply).  It runs the tracker's binning and neighbour-finding
+ * kernels on ev's clusters and writes, for every cluster id c, the cid of its
+ * up and down neighbour (or -1) to up_cid[c] and dn_cid[c]: the same links as
+ * TPC_DUMP_LINKS after tpc_track_event.
+ *   ev        device clusters (on_device must be 1), at most 131072 of them;
+ *             more gives TPC_EINVAL before any device work
+ *   geom      as for tpc_track_event, at most 36 sectors in total
+ *   params    slope windows and d_max are used
+ *   up_cid, dn_cid  device arrays of ev->n int32 each, written by the call
+ *   cuda_stream     stream for the work (NULL = legacy default stream)
+ * Scratch memory is a static device array of this library, about 8.3 MB,
+ * held on every device that loads the library until the process exits.  No
+ * context, cudaMalloc or cudaFree is involved.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  Every
+ * call on a device shares the array and clears what must start at zero, so
+ * calls whose work overlaps on the GPU (other threads, other streams) race:
+ * serialise them.  Returns after the work has completed: TPC_OK, TPC_EINVAL
+ * (bad argument or invalid cluster), TPC_ECAPACITY (a row above 4096
+ * clusters), TPC_ETIMEOUT or TPC_ECUDA. */
+int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometry* geom,
+                            const tpc_track_params* params, int32_t* up_cid, int32_t* dn_cid,
+                            void* cuda_stream);
+
 /* One-line description of the last error on the context (never NULL). */
 const char* tpc_track_last_error(const tpc_track_ctx* ctx);
 

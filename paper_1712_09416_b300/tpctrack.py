@@ -24,7 +24,8 @@ EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "
             "tpc_track_launch", "tpc_track_results", "tpc_track_submit", "tpc_track_poll",
             "tpc_track_release", "tpc_track_get_counters", "tpc_track_stream",
             "tpc_track_set_profiling", "tpc_track_kernel_times",
-            "tpc_track_debug_dump", "tpc_track_last_error", "tpc_track_destroy"]
+            "tpc_track_debug_dump", "tpc_track_last_error", "tpc_track_destroy",
+            "tpc_track_links_noalloc"]
 
 
 class TpcError(RuntimeError):
@@ -118,6 +119,8 @@ def lib():
         L.tpc_track_last_error.restype = C.c_char_p
         L.tpc_track_destroy.argtypes = [P]
         L.tpc_track_destroy.restype = None
+        L.tpc_track_links_noalloc.argtypes = [C.POINTER(tpc_clusters), C.POINTER(tpc_geometry),
+                                              C.POINTER(tpc_track_params), P, P, P]
         L.tpc_track_default_params.argtypes = [C.POINTER(tpc_track_params)]
         L.tpc_track_default_params.restype = None
         _lib = L
@@ -303,6 +306,15 @@ def tpc_track_debug_dump(ctx, stage: int) -> bytes:
     buf = C.create_string_buffer(max(1, used.value))
     _check(ctx, lib().tpc_track_debug_dump(ctx, stage, buf, used.value, C.byref(used)))
     return buf.raw[:used.value]
+
+
+def tpc_track_links_noalloc(clusters: tpc_clusters, geom: tpc_geometry,
+                            params: tpc_track_params, up_cid_ptr: int, dn_cid_ptr: int,
+                            stream: int = 0) -> int:
+    """Neighbour links by cid into two device int32 arrays, without allocating.
+    Returns the status code (the caller checks it)."""
+    return lib().tpc_track_links_noalloc(C.byref(clusters), C.byref(geom), C.byref(params),
+                                         up_cid_ptr, dn_cid_ptr, stream)
 
 
 def tpc_track_last_error(ctx) -> str:
