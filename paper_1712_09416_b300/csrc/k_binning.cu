@@ -4,12 +4,13 @@
 // neighbours in the adjacent pad rows and the fit picks up hits row by row,
 // so every hit is kept sorted by (sector, row, y-z bin, cid) with per-bin
 // offsets: a window query on a row touches a few contiguous ranges.
-//   k_count    checks every cluster (row, sector in range, y and z finite)
-//              and counts the clusters of each (sector, row)
+//   k_count    checks every cluster (row, sector in range, y and z finite),
+//              counts the clusters of each (sector, row) and keeps each
+//              cluster's arrival rank in its row
 //   k_rowscan  exclusive scan of the row counts and of the per-row bin
 //              counts (single pass, decoupled look-back), and the y-z grid
 //              of each row sized for about two hits per bin
-//   k_scatter  moves every cluster into its row's range
+//   k_scatter  moves every cluster to row offset + rank
 //   k_rowsort  one block per row: counting sort by bin in shared memory,
 //              cid order inside a bin, writes the sorted hits and the bin
 //              offsets (and clears the hit weights for the fit)
@@ -66,7 +67,7 @@ __global__ void k_count(Launch L)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n_total; i += stride) {
         float y, z;
         int g, cid;
-        if (cluster_of(L, off_s, i, y, z, g, cid)) atomicAdd(&L.row_cnt[g], 1);
+        if (cluster_of(L, off_s, i, y, z, g, cid)) L.rank[i] = atomicAdd(&L.row_cnt[g], 1);
         else atomicAdd(&L.cnt->n_invalid, 1);
     }
 }
@@ -197,7 +198,7 @@ __global__ void k_scatter(Launch L)
         float y, z;
         int g, cid;
         if (!cluster_of(L, off_s, i, y, z, g, cid)) continue;
-        const int pos = L.row_off[g] + atomicAdd(&L.row_fill[g], 1);
+        const int pos = L.row_off[g] + L.rank[i];
         L.tmp_y[pos] = y;
         L.tmp_z[pos] = z;
         L.tmp_cid[pos] = cid;

@@ -57,7 +57,9 @@ __device__ __forceinline__ void push(CandList& c, float sy, float sz, int cid, i
 }
 
 // Scan one side's window: admissible candidates and their slopes.  up = true
-// gives slopes (c - h) * inv, up = false gives (h - c) * inv.
+// gives slopes (c - h) * inv, up = false gives (h - c) * inv.  The hit ranges
+// of the window's z-bins (up to four) are walked as one flat index space so
+// that lanes with different bin counts stay together.
 __device__ __forceinline__ void collect(const RowView& V, float yh, float zh, float inv, float wy,
                                        float wz, bool up, CandList& c)
 {
@@ -65,13 +67,34 @@ __device__ __forceinline__ void collect(const RowView& V, float yh, float zh, fl
     const int y0 = bin_y(V.G, yh - wy - my), y1 = bin_y(V.G, yh + wy + my);
     const int z0 = bin_z(V.G, zh - wz - mz), z1 = bin_z(V.G, zh + wz + mz);
     c.n = 0;
-    for (int bz = z0; bz <= z1; ++bz) {
-        const int a = V.bins[bz * V.G.ny + y0], b = V.bins[bz * V.G.ny + y1 + 1];
-        for (int k = a; k < b; ++k) {
-            const float ddy = up ? __fsub_rn(V.y[k], yh) : __fsub_rn(yh, V.y[k]);
-            const float ddz = up ? __fsub_rn(V.z[k], zh) : __fsub_rn(zh, V.z[k]);
-            if (!(fabsf(ddy) <= wy) || !(fabsf(ddz) <= wz)) continue;
+    auto test = [&](int k) {
+        const float ddy = up ? __fsub_rn(V.y[k], yh) : __fsub_rn(yh, V.y[k]);
+        const float ddz = up ? __fsub_rn(V.z[k], zh) : __fsub_rn(zh, V.z[k]);
+        if (fabsf(ddy) <= wy && fabsf(ddz) <= wz)
             push(c, __fmul_rn(ddy, inv), __fmul_rn(ddz, inv), V.cid[k], k);
+    };
+    if (z1 - z0 < 4) {
+        int a[4], n[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int bz = z0 + j;
+            a[j] = 0;
+            n[j] = 0;
+            if (bz <= z1) {
+                a[j] = V.bins[bz * V.G.ny + y0];
+                n[j] = V.bins[bz * V.G.ny + y1 + 1] - a[j];
+            }
+        }
+        const int c1 = n[0], c2 = c1 + n[1], c3 = c2 + n[2], tot = c3 + n[3];
+        for (int q = 0; q < tot; ++q) {
+            const int k = q < c1 ? a[0] + q : q < c2 ? a[1] + (q - c1) : q < c3 ? a[2] + (q - c2)
+                                                                               : a[3] + (q - c3);
+            test(k);
+        }
+    } else {
+        for (int bz = z0; bz <= z1; ++bz) {
+            const int ka = V.bins[bz * V.G.ny + y0], kb = V.bins[bz * V.G.ny + y1 + 1];
+            for (int k = ka; k < kb; ++k) test(k);
         }
     }
 }

@@ -6,14 +6,14 @@
 // min_track_hits hits and at least half of its hits; the track keeps the
 // owned hits and the tracklet's parameters.  Tracks are emitted in the order
 // (sector, row of the first owned hit, cid of h0).
-//   k_sel_decide  one thread per tracklet: owned hits, decision, sort key;
+//   k_sel_decide  one warp per tracklet: owned hits, decision, sort key;
 //                 also marks the tracklet range of every sector (tracklets
 //                 are ordered by sector because start hits are)
 //   k_sel_sort    one block per sector, in sector order: compacts the
 //                 emitted tracklets with a warp ballot, sorts their keys in
 //                 shared memory (bitonic), scans their hit counts and takes
 //                 the sector's output offsets from a decoupled look-back
-//   k_sel_write   one thread per emitted tracklet: header and owned hit cids
+//   k_sel_write   one warp per emitted tracklet: header and owned hit cids
 // Bytes per cluster: rowhit 2 + weight 8 per assigned hit (decide), about
 // 100 B per track header and 4 B per output hit (write).
 #include <cuda_runtime.h>
@@ -26,14 +26,19 @@ namespace {
 
 constexpr unsigned long long kNone = ~0ULL;
 
+// one warp per tracklet, lanes over its rows
 __global__ void k_sel_decide(Launch L)
 {
     const int n_st = min(L.cnt->n_starts, L.t_cap);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_st; t += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_st; t += warps) {
         const TrackletHdr& H = L.tl[t];
         const int gs = L.hrow[H.start] >> 8;
-        if (t == 0 || (L.hrow[L.tl[t - 1].start] >> 8) != gs) L.sec_first[gs] = t;
-        if (t == n_st - 1 || (L.hrow[L.tl[t + 1].start] >> 8) != gs) L.sec_end[gs] = t + 1;
+        if (lane == 0) {
+            if (t == 0 || (L.hrow[L.tl[t - 1].start] >> 8) != gs) L.sec_first[gs] = t;
+            if (t == n_st - 1 || (L.hrow[L.tl[t + 1].start] >> 8) != gs) L.sec_end[gs] = t + 1;
+        }
         unsigned long long out = kNone;
         int nown = 0;
         if (H.chain_len >= L.min_chain && H.valid) {
@@ -41,19 +46,25 @@ __global__ void k_sel_decide(Launch L)
                                            (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
             const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
             int first_own = -1;
-            for (int r = H.first; r <= H.last; ++r) {
-                const int h = rowhit[r];
-                if (h >= 0 && L.weight[h] == key) {
-                    if (first_own < 0) first_own = r;
-                    ++nown;
+            for (int r0 = H.first; r0 <= H.last; r0 += 32) {
+                const int r = r0 + lane;
+                bool own = false;
+                if (r <= H.last) {
+                    const int h = rowhit[r];
+                    own = h >= 0 && L.weight[h] == key;
                 }
+                const unsigned b = __ballot_sync(0xffffffffu, own);
+                if (b && first_own < 0) first_own = r0 + __ffs(b) - 1;
+                nown += __popc(b);
             }
             if (nown >= L.min_track_hits && 2 * nown >= H.nhits)
                 out = ((unsigned long long)first_own << 32) | (unsigned long long)(unsigned)L.hcid[H.start];
         }
-        L.tl_key[t] = out;
-        L.tl_nown[t] = nown;
-        L.tl_out[t] = -1;
+        if (lane == 0) {
+            L.tl_key[t] = out;
+            L.tl_nown[t] = nown;
+            L.tl_out[t] = -1;
+        }
     }
 }
 
@@ -161,31 +172,43 @@ __global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
     }
 }
 
+// one warp per tracklet: header by lane 0, owned hits by all lanes in row order
 __global__ void k_sel_write(Launch L)
 {
     const int n_st = min(L.cnt->n_starts, L.t_cap);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_st; t += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_st; t += warps) {
         const int j = L.tl_out[t];
         if (j < 0) continue;
         const TrackletHdr& H = L.tl[t];
-        const int gs = L.hrow[H.start] >> 8;
-        const int e = L.sec_event[gs];
-        L.k_sector[j] = gs - L.ev[e].sec_base;
-        L.k_x[j] = H.x;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) L.k_param[(size_t)j * 5 + i] = H.p[i];
-#pragma unroll
-        for (int i = 0; i < 15; ++i) L.k_cov[(size_t)j * 15 + i] = H.C[i];
-        L.k_chi2[j] = H.chi2;
-        L.k_ndf[j] = H.ndf;
-        int off = L.tl_hitoff[t];
-        L.k_hit_off[j] = off;
+        const int off0 = L.tl_hitoff[t];
+        if (lane < 5) L.k_param[(size_t)j * 5 + lane] = H.p[lane];
+        if (lane < 15) L.k_cov[(size_t)j * 15 + lane] = H.C[lane];
+        if (lane == 0) {
+            const int gs = L.hrow[H.start] >> 8;
+            const int e = L.sec_event[gs];
+            L.k_sector[j] = gs - L.ev[e].sec_base;
+            L.k_x[j] = H.x;
+            L.k_chi2[j] = H.chi2;
+            L.k_ndf[j] = H.ndf;
+            L.k_hit_off[j] = off0;
+        }
         const unsigned long long key = ((unsigned long long)H.nhits << 32) |
                                        (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
         const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
-        for (int r = H.first; r <= H.last; ++r) {
-            const int h = rowhit[r];
-            if (h >= 0 && L.weight[h] == key) L.k_hit_cid[off++] = L.hcid[h];
+        int off = off0;
+        for (int r0 = H.first; r0 <= H.last; r0 += 32) {
+            const int r = r0 + lane;
+            int h = -1;
+            bool own = false;
+            if (r <= H.last) {
+                h = rowhit[r];
+                own = h >= 0 && L.weight[h] == key;
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, own);
+            if (own) L.k_hit_cid[off + __popc(b & ((1u << lane) - 1))] = L.hcid[h];
+            off += __popc(b);
         }
     }
 }
@@ -195,8 +218,8 @@ __global__ void k_sel_write(Launch L)
 void launch_selector(const Launch& L, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
-    int blocks = (L.t_cap + 255) / 256;
-    if (blocks > 148 * 8) blocks = 148 * 8;
+    int blocks = (L.t_cap + 7) / 8;  // one warp per tracklet, 8 warps per block
+    if (blocks > 148 * 16) blocks = 148 * 16;
     if (blocks < 1) blocks = 1;
     k_sel_decide<<<blocks, 256, 0, stream>>>(L);
     hook_after(hook, "k_sel_decide");

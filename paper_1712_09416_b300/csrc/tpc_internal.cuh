@@ -96,6 +96,7 @@ struct Launch {
     RowGrid* grid;              // [RS]
     unsigned long long* tile_state;  // look-back states (rows | hits | sectors)
     int n_row_tiles, n_hit_tiles;
+    int* rank;                  // [n_total] arrival rank of a cluster in its row
     float* tmp_y; float* tmp_z; int* tmp_cid;   // row-scattered
     float* hy; float* hz; int* hcid; int* hrow; // sorted
     int* bin_start;

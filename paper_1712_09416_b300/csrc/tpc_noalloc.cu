@@ -41,7 +41,7 @@ constexpr size_t kNaZero = up256(up256(sizeof(Counters)) + 4 * (2 * kNaRS + 2 * 
                                  8 * (kNaRowTiles + kNaHitTiles + kNaMaxSectors) + 1024);
 constexpr size_t kNaBytes =
     kNaDesc + kNaZero + up256(4 * (kNaRS + 1)) + up256(sizeof(RowGrid) * kNaRS) +
-    up256(4 * kNaBins) + 7 * up256(4 * kNaMaxClusters) /* tmp y z cid, hy hz hcid hrow */ +
+    up256(4 * kNaBins) + 8 * up256(4 * kNaMaxClusters) /* tmp y z cid rank, hy hz hcid hrow */ +
     2 * up256(4 * kNaMaxClusters) /* up dn */ + 2 * up256(4 * kNaMaxClusters) /* upc dnc */ +
     up256(4 * kNaMaxClusters) /* upg */ + up256(8 * kNaMaxClusters) /* weight */ +
     up256(4 * kNaMaxClusters) /* starts */;
@@ -178,6 +178,7 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
     L.tmp_y = (float*)take(4 * kNaMaxClusters);
     L.tmp_z = (float*)take(4 * kNaMaxClusters);
     L.tmp_cid = (int*)take(4 * kNaMaxClusters);
+    L.rank = (int*)take(4 * kNaMaxClusters);
     L.hy = (float*)take(4 * kNaMaxClusters);
     L.hz = (float*)take(4 * kNaMaxClusters);
     L.hcid = (int*)take(4 * kNaMaxClusters);

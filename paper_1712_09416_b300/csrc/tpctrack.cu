@@ -90,7 +90,7 @@ struct Slot {
     int *row_off;
     RowGrid* grid;
     float *tmp_y, *tmp_z;
-    int* tmp_cid;
+    int *tmp_cid, *rank;
     float *hy, *hz;
     int *hcid, *hrow, *bin_start;
     int16_t *up, *dn, *upc, *dnc;
@@ -217,6 +217,7 @@ size_t layout(Slot& s, char* base)
     s.tmp_y = (float*)take(4 * k.n);
     s.tmp_z = (float*)take(4 * k.n);
     s.tmp_cid = (int*)take(4 * k.n);
+    s.rank = (int*)take(4 * k.n);
     s.hy = (float*)take(4 * k.n);
     s.hz = (float*)take(4 * k.n);
     s.hcid = (int*)take(4 * k.n);
@@ -457,6 +458,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.tmp_y = s.tmp_y;
     L.tmp_z = s.tmp_z;
     L.tmp_cid = s.tmp_cid;
+    L.rank = s.rank;
     L.hy = s.hy;
     L.hz = s.hz;
     L.hcid = s.hcid;
