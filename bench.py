@@ -77,7 +77,9 @@ def kernel_bytes(c: dict) -> dict:
         "k_rowsort": 12 * N + 16 * N + 8 * N + 4 * (B + RS) + 32 * RS,
         "k_neighbours": 8 * N + 4 * N + 4 * B,
         "k_clean_starts": 4 * N + 4 * N + 4 * N + 4 * N + 4 * T,
-        "k_constructor": 34 * Th + 116 * Tl,
+        "k_chains": 8 * c["n_chain_hits"] + 32 * T,
+        "k_constructor": 24 * Th + 116 * Tl,
+        "k_weights": 20 * Th + 32 * Tl,
         "k_sel_decide": 10 * Th + 32 * T,
         "k_sel_sort": 12 * T + 8 * K,
         "k_sel_write": 212 * K + 18 * Kh,
@@ -295,7 +297,11 @@ def run_ours(args):
                     torch.from_numpy(ev.row.view(np.int16)).cuda(),
                     torch.from_numpy(ev.sector.view(np.int16)).cuda()))
     cls = [tp.clusters_of(*d) for d in dev]
-    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    # a stream of our own: the tracker launches on it and the timing events
+    # are recorded on it (torch's default stream is the legacy stream 0, for
+    # which the library would create a separate non-blocking stream)
+    stream = torch.cuda.Stream()
     ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, cuda_stream=stream.cuda_stream)
 
     def step(i):

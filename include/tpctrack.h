@@ -173,10 +173,11 @@ int tpc_track_poll(tpc_track_ctx* ctx, uint64_t ticket, int timeout_us, tpc_trac
 int tpc_track_release(tpc_track_ctx* ctx, uint64_t ticket);
 
 /* Per-launch counters of the last tpc_track_results (for the byte model
- * of the benchmark and for tests). */
+ * of the benchmark and for tests).  n_chain_hits is the number of hits on
+ * the chains of all start hits (every start hit included). */
 typedef struct {
     int64_t n_clusters, n_rows_total, n_bins, n_links, n_starts, n_tracklets,
-            n_valid_tracklets, n_tracklet_hits, n_tracks, n_track_hits;
+            n_valid_tracklets, n_tracklet_hits, n_tracks, n_track_hits, n_chain_hits;
 } tpc_track_counters;
 int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c);
 
@@ -233,7 +234,7 @@ int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t c
  *   params    slope windows and d_max are used
  *   up_cid, dn_cid  device arrays of ev->n int32 each, written by the call
  *   cuda_stream     stream for the work (NULL = legacy default stream)
- * Scratch memory is a static device array of this library, about 9.1 MB,
+ * Scratch memory is a static device array of this library, about 9.9 MB,
  * held on every device that loads the library until the process exits.  No
  * context, cudaMalloc or cudaFree is involved.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress, with that

@@ -90,7 +90,7 @@ __device__ __forceinline__ RowGrid make_grid(const Launch& L, int g, int cnt)
     zlo -= 2.0f;
     zhi += 2.0f;
     const float W = 2.0f * yh, H = zhi - zlo;
-    const int nb = max(1, cnt / 2);
+    const int nb = max(1, cnt * kBinsPerHitX2 / 2);
     int ny = (int)(sqrtf((float)nb * W / H) + 0.5f);
     ny = min(max(ny, 1), min(nb, kMaxBinsPerDim));   // ny * nz <= nb always
     int nz = min(max(nb / ny, 1), kMaxBinsPerDim);
@@ -199,8 +199,7 @@ __global__ void k_scatter(Launch L)
         int g, cid;
         if (!cluster_of(L, off_s, i, y, z, g, cid)) continue;
         const int pos = L.row_off[g] + L.rank[i];
-        L.tmp_y[pos] = y;
-        L.tmp_z[pos] = z;
+        L.tmp_yz[pos] = make_float2(y, z);
         L.tmp_cid[pos] = cid;
     }
 }
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
 {
     extern __shared__ unsigned char smem[];
     int* hist = reinterpret_cast<int*>(smem);                                // [nb + 1]
-    int* scid = hist + (kMaxRowHits / 2 + 2);                                // [n]
+    int* scid = hist + (kMaxRowBins + 2);                                // [n]
     int16_t* sbin = reinterpret_cast<int16_t*>(scid + kMaxRowHits);          // [n]
     int16_t* sslot = sbin + kMaxRowHits;                                     // [n]
     int16_t* sorder = sslot + kMaxRowHits;                                   // [n]
@@ -227,8 +226,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
             // (hits copied unsorted, every bin empty); the launch fails.
             if (threadIdx.x == 0) atomicExch(&L.cnt->ovf_row, 1);
             for (int p = threadIdx.x; p < n; p += blockDim.x) {
-                L.hy[base + p] = L.tmp_y[base + p];
-                L.hz[base + p] = L.tmp_z[base + p];
+                L.hyz[base + p] = L.tmp_yz[base + p];
                 L.hcid[base + p] = L.tmp_cid[base + p];
                 L.hrow[base + p] = hrow;
                 L.weight[base + p] = 0ULL;
@@ -239,7 +237,8 @@ __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
         for (int b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int b = bin_z(G, L.tmp_z[base + i]) * G.ny + bin_y(G, L.tmp_y[base + i]);
+            const float2 c = L.tmp_yz[base + i];
+            const int b = bin_z(G, c.y) * G.ny + bin_y(G, c.x);
             sbin[i] = (int16_t)b;
             scid[i] = L.tmp_cid[base + i];
             sslot[i] = (int16_t)atomicAdd(&hist[b], 1);
@@ -281,8 +280,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
         __syncthreads();
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
             const int i = sorder[p];
-            L.hy[base + p] = L.tmp_y[base + i];
-            L.hz[base + p] = L.tmp_z[base + i];
+            L.hyz[base + p] = L.tmp_yz[base + i];
             L.hcid[base + p] = scid[i];
             L.hrow[base + p] = hrow;
             L.weight[base + p] = 0ULL;
@@ -296,7 +294,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
 
 size_t rowsort_smem_bytes()
 {
-    return sizeof(int) * (kMaxRowHits / 2 + 2) + sizeof(int) * kMaxRowHits +
+    return sizeof(int) * (kMaxRowBins + 2) + sizeof(int) * kMaxRowHits +
            3 * sizeof(int16_t) * kMaxRowHits;
 }
 

@@ -26,8 +26,7 @@ namespace {
 constexpr int kNbThreads = 256;
 
 struct RowView {      // one adjacent row
-    const float* y;
-    const float* z;
+    const float2* yz;
     const int* cid;
     const int* bins;
     RowGrid G;
@@ -68,8 +67,9 @@ __device__ __forceinline__ void collect(const RowView& V, float yh, float zh, fl
     const int z0 = bin_z(V.G, zh - wz - mz), z1 = bin_z(V.G, zh + wz + mz);
     c.n = 0;
     auto test = [&](int k) {
-        const float ddy = up ? __fsub_rn(V.y[k], yh) : __fsub_rn(yh, V.y[k]);
-        const float ddz = up ? __fsub_rn(V.z[k], zh) : __fsub_rn(zh, V.z[k]);
+        const float2 v = V.yz[k];
+        const float ddy = up ? __fsub_rn(v.x, yh) : __fsub_rn(yh, v.x);
+        const float ddz = up ? __fsub_rn(v.y, zh) : __fsub_rn(zh, v.y);
         if (fabsf(ddy) <= wy && fabsf(ddz) <= wz)
             push(c, __fmul_rn(ddy, inv), __fmul_rn(ddz, inv), V.cid[k], k);
     };
@@ -144,8 +144,9 @@ __device__ __forceinline__ void best_pair(const RowView& U, const RowView& D, fl
     for (int bzu = uz0; bzu <= uz1; ++bzu) {
         const int ua = U.bins[bzu * U.G.ny + uy0], ub = U.bins[bzu * U.G.ny + uy1 + 1];
         for (int ku = ua; ku < ub; ++ku) {
-            const float ddyu = __fsub_rn(U.y[ku], yh);
-            const float ddzu = __fsub_rn(U.z[ku], zh);
+            const float2 cu2 = U.yz[ku];
+            const float ddyu = __fsub_rn(cu2.x, yh);
+            const float ddzu = __fsub_rn(cu2.y, zh);
             if (!(fabsf(ddyu) <= wyu) || !(fabsf(ddzu) <= wzu)) continue;
             const float syu = __fmul_rn(ddyu, iu), szu = __fmul_rn(ddzu, iu);
             const int ccu = U.cid[ku];
@@ -156,8 +157,9 @@ __device__ __forceinline__ void best_pair(const RowView& U, const RowView& D, fl
                 for (int bzd = dz0; bzd <= dz1; ++bzd) {
                     const int da = D.bins[bzd * D.G.ny + dy0], db = D.bins[bzd * D.G.ny + dy1 + 1];
                     for (int kd = da; kd < db; ++kd) {
-                        const float ddyd = __fsub_rn(yh, D.y[kd]);
-                        const float ddzd = __fsub_rn(zh, D.z[kd]);
+                        const float2 cd2 = D.yz[kd];
+                        const float ddyd = __fsub_rn(yh, cd2.x);
+                        const float ddzd = __fsub_rn(zh, cd2.y);
                         if (!(fabsf(ddyd) <= wyd) || !(fabsf(ddzd) <= wzd)) continue;
                         consider(syu, szu, ccu, ku, __fmul_rn(ddyd, id), __fmul_rn(ddzd, id),
                                  D.cid[kd], kd, bestD, bcu, bcd, biu, bid);
@@ -198,15 +200,14 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbours(Launch L)
         U.G = L.grid[g + 1];
         D.G = L.grid[g - 1];
         const int bu = __ldg(&L.row_off[g + 1]), bd = __ldg(&L.row_off[g - 1]);
-        U.y = L.hy + bu;
-        U.z = L.hz + bu;
+        U.yz = L.hyz + bu;
         U.cid = L.hcid + bu;
         U.bins = L.bin_start + U.G.bin_off;
-        D.y = L.hy + bd;
-        D.z = L.hz + bd;
+        D.yz = L.hyz + bd;
         D.cid = L.hcid + bd;
         D.bins = L.bin_start + D.G.bin_off;
-        const float yh = L.hy[i], zh = L.hz[i];
+        const float2 ch = L.hyz[i];
+        const float yh = ch.x, zh = ch.y;
         float bestD = 0.0f;
         int bcu = -1, bcd = -1, biu = -1, bid = -1;
         best_pair(U, D, yh, zh, iu, id, wyu, wzu, wyd, wzd, bestD, bcu, bcd, biu, bid);

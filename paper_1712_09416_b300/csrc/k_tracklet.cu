@@ -2,16 +2,18 @@
 // sector tracker (paper, Abstract), one thread per chain like the paper's
 // one-thread-per-track fit (Sect. 4.1, Listing 2).
 //
-// For every start hit the thread follows the chain of cleaned up-links, seeds
-// a state (y, z, sin phi, tan lambda, q/pT) from the chord of the chain, fits
+// k_chains follows, for every start hit, the chain of cleaned up-links (one
+// thread per start hit).  k_constructor then, one lane per chain, seeds a
+// state (y, z, sin phi, tan lambda, q/pT) from the chord of the chain, fits
 // the chain forward, extends it outward row by row (transport to the pad-row
 // plane, least-chi2 hit in the box that bounds the chi2 ellipse, update), then
 // refits backward from the last hit with the covariance reset to the seed,
 // picking up hits below the chain the same way.  The result is the state and
 // covariance at the innermost hit.  The 5-vector and the 15 covariance
 // entries live in registers; the forward hit list lives in the tracklet's
-// rowhit slot and the inputs of the next row are loaded one step ahead.  Valid tracklets raise the
-// weight of their hits to the key (nHits << 32 | ~cid(h0)) with atomicMax.
+// rowhit slot and the inputs of the next row are loaded one step ahead.
+// k_weights: valid tracklets raise the weight of their hits to the key
+// (nHits << 32 | ~cid(h0)) with atomicMax.
 //
 // Arithmetic is binary32.  Transport between planes x0 -> x1 (dx = x1 - x0):
 //   s1 = s0 + C_k dx, C_k = -kB q/pT;  y1 = y0 + dx (s0 + s1)/(c0 + c1);
@@ -19,8 +21,10 @@
 // with the exact Jacobian; d(dS)/dC_k is evaluated as
 //   dS^2 [ (s1/c1) sinc^2(dphi/2) / 2 + (sin dphi - dphi)/dphi^2 ],  dphi = C_k dS,
 // a form without cancellation as C_k -> 0.
-// Bytes per assigned hit: chain link 4, y z 8 (forward) + 8 (backward), rowhit
-// 4, weight read-modify-write 16, header about 100 per tracklet.
+// Bytes: k_chains 8 per chain hit (link read, rowhit write) + 32 per start;
+// k_constructor per assigned hit y z 8 (forward) + 8 (backward), rowhit 4
+// (written) + 4 (read back), about 116 per tracklet (chain record, header);
+// k_weights per assigned hit rowhit 4 + weight read-modify-write 16.
 #include <cuda_runtime.h>
 
 #include "tpc_internal.cuh"
@@ -166,39 +170,27 @@ __device__ __forceinline__ bool outside(const Fit& f, const Launch& L)
            fabsf(f.p[1]) > L.z_max + L.edge_margin;
 }
 
-// Bin offsets of the search window of the next row, loaded one step ahead
-// from the position predicted along the current direction (with a margin);
-// used when the exact window falls inside the predicted one.
-struct Spec {
-    int y0, y1, z0, z1;  // predicted bin ranges (z1 <= z0 + 1)
-    int a0, b0, a1, b1;  // row-local hit ranges of z-bins z0 and z0 + 1
-    bool valid;
-};
-
+// Candidates ka..kb-1 (global sorted indices) in batches of four loads.
 __device__ __forceinline__ void scan_range(const Fit& f, int ka, int kb, float S00, float S01,
                                            float S11, float id, const Launch& L, float& best,
                                            int& bk, float& by, float& bzv)
 {
     for (int k = ka; k < kb; k += 4) {
-        float cy[4], cz[4];
+        float2 c[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int kk = k + j < kb ? k + j : ka;
-            cy[j] = L.hy[kk];
-            cz[j] = L.hz[kk];
-        }
+        for (int j = 0; j < 4; ++j) c[j] = L.hyz[k + j < kb ? k + j : ka];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (k + j >= kb) break;
-            const float r0 = cy[j] - f.p[0];
-            const float r1 = cz[j] - f.p[1];
+            const float r0 = c[j].x - f.p[0];
+            const float r1 = c[j].y - f.p[1];
             const float chi2 = (S11 * r0 * r0 - 2.0f * S01 * r0 * r1 + S00 * r1 * r1) * id;
             // exact ties (rare) go to the lower cid; the cid is read only then
             if (chi2 < best || (chi2 == best && L.hcid[k + j] < L.hcid[bk])) {
                 best = chi2;
                 bk = k + j;
-                by = cy[j];
-                bzv = cz[j];
+                by = c[j].x;
+                bzv = c[j].y;
             }
         }
     }
@@ -207,10 +199,11 @@ __device__ __forceinline__ void scan_range(const Fit& f, int ka, int kb, float S
 // Least-chi2 hit of a row (grid G, hits from base) with chi2 <= chi2_hit,
 // exact ties to the lower cid; returns its global index or -1 and its
 // coordinates in (my, mz).  Every hit in the bins covering the box that
-// bounds the chi2 ellipse is tried (a superset when the prefetched bins of
-// the predicted window are used).
-__device__ __forceinline__ int search(const Fit& f, const RowGrid& G, int base, const Spec& sp,
-                                      const Launch& L, float& my, float& mz)
+// bounds the chi2 ellipse is tried.  When the box spans at most two z-bins
+// (nearly always: bins are several cm wide, the box a few mm) the four bin
+// offsets are read at once and the two hit ranges walked as one list.
+__device__ __forceinline__ int search(const Fit& f, const RowGrid& G, int base, const Launch& L,
+                                      float& my, float& mz)
 {
     const float* C = f.C;
     const float S00 = C[0] + L.sy2, S01 = C[1], S11 = C[2] + L.sz2;
@@ -219,14 +212,41 @@ __device__ __forceinline__ int search(const Fit& f, const RowGrid& G, int base, 
     const float wz = 1.01f * sqrtf(L.chi2_hit * S11) + 1e-3f;
     const int y0 = bin_y(G, f.p[0] - wy), y1 = bin_y(G, f.p[0] + wy);
     const int z0 = bin_z(G, f.p[1] - wz), z1 = bin_z(G, f.p[1] + wz);
+    const int* bins = L.bin_start + G.bin_off;
     float best = 3.0e38f, by = 0.0f, bzv = 0.0f;
     int bk = -1;
-    if (sp.valid && y0 >= sp.y0 && y1 <= sp.y1 && z0 >= sp.z0 && z1 <= sp.z1) {
-        scan_range(f, base + sp.a0, base + sp.b0, S00, S01, S11, id, L, best, bk, by, bzv);
-        if (sp.z1 > sp.z0)
-            scan_range(f, base + sp.a1, base + sp.b1, S00, S01, S11, id, L, best, bk, by, bzv);
+    if (z1 - z0 <= 1) {
+        const int a0 = bins[z0 * G.ny + y0], b0 = bins[z0 * G.ny + y1 + 1];
+        int a1 = 0, b1 = 0;
+        if (z1 > z0) {
+            a1 = bins[z1 * G.ny + y0];
+            b1 = bins[z1 * G.ny + y1 + 1];
+        }
+        const int n0 = b0 - a0, tot = n0 + (b1 - a1);
+        for (int q = 0; q < tot; q += 4) {
+            int kk[4];
+            float2 c[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int qj = q + j < tot ? q + j : 0;
+                kk[j] = base + (qj < n0 ? a0 + qj : a1 + (qj - n0));
+                c[j] = L.hyz[kk[j]];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (q + j >= tot) break;
+                const float r0 = c[j].x - f.p[0];
+                const float r1 = c[j].y - f.p[1];
+                const float chi2 = (S11 * r0 * r0 - 2.0f * S01 * r0 * r1 + S00 * r1 * r1) * id;
+                if (chi2 < best || (chi2 == best && L.hcid[kk[j]] < L.hcid[bk])) {
+                    best = chi2;
+                    bk = kk[j];
+                    by = c[j].x;
+                    bzv = c[j].y;
+                }
+            }
+        }
     } else {
-        const int* bins = L.bin_start + G.bin_off;
         for (int bz = z0; bz <= z1; ++bz) {
             const int ka = base + bins[bz * G.ny + y0], kb = base + bins[bz * G.ny + y1 + 1];
             scan_range(f, ka, kb, S00, S01, S11, id, L, best, bk, by, bzv);
@@ -235,34 +255,6 @@ __device__ __forceinline__ int search(const Fit& f, const RowGrid& G, int base, 
     my = by;
     mz = bzv;
     return (bk >= 0 && best <= L.chi2_hit) ? bk : -1;
-}
-
-// Predicted window of the row at xn from the current state, and the loads of
-// its bin offsets.
-__device__ __forceinline__ void speculate(const Fit& f, float xn, const RowGrid& G, const Launch& L,
-                                          Spec& sp)
-{
-    const float s = f.p[2];
-    const float c2 = (1.0f - s) * (1.0f + s);
-    const float ic = rsqrtf(fmaxf(c2, 1e-4f));
-    const float dx = xn - f.x;
-    const float yp = f.p[0] + dx * s * ic, zp = f.p[1] + dx * f.p[3] * ic;
-    const float wy = sqrtf(L.chi2_hit * (f.C[0] + L.sy2)) + 0.5f + 0.1f * fabsf(dx);
-    const float wz = sqrtf(L.chi2_hit * (f.C[2] + L.sz2)) + 0.5f + 0.1f * fabsf(dx);
-    sp.y0 = bin_y(G, yp - wy);
-    sp.y1 = bin_y(G, yp + wy);
-    sp.z0 = bin_z(G, zp - wz);
-    sp.z1 = min(bin_z(G, zp + wz), sp.z0 + 1);
-    const int* bins = L.bin_start + G.bin_off;
-    sp.a0 = bins[sp.z0 * G.ny + sp.y0];
-    sp.b0 = bins[sp.z0 * G.ny + sp.y1 + 1];
-    if (sp.z1 > sp.z0) {
-        sp.a1 = bins[sp.z1 * G.ny + sp.y0];
-        sp.b1 = bins[sp.z1 * G.ny + sp.y1 + 1];
-    } else {
-        sp.a1 = sp.b1 = 0;
-    }
-    sp.valid = true;
 }
 
 // Seed covariance at the current direction: diagonal, cluster variances for
@@ -278,6 +270,60 @@ __device__ __forceinline__ void seed_cov(Fit& f, const Launch& L)
     f.C[CI(2, 2)] = L.seed_var_s * c2 * c2 * c2;
     f.C[CI(3, 3)] = L.seed_var_t * c2;
     f.C[CI(4, 4)] = L.seed_var_q;
+}
+
+// One thread per start hit: follow its chain of cleaned up-links, record the
+// chain's hits in the tracklet's rowhit slot and the chain in tl_chain
+// (start hit, sector << 8 | row, end hit, end row).  Chains shorter than
+// min_chain get their final (empty) header here.  Every lane walks a chain
+// of its own at the same time, so the serial link loads overlap across the
+// grid instead of stalling a warp of the constructor.
+constexpr int kChThreads = 256;
+
+__global__ void __launch_bounds__(kChThreads) k_chains(Launch L)
+{
+    const int n_st = min(L.cnt->n_starts, L.t_cap);
+    int my_tl = 0, my_hits = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_st; t += gridDim.x * blockDim.x) {
+        const int s = L.starts[t];
+        const int hr = L.hrow[s];
+        const int r0 = hr & 255;
+        int* rowhit = L.tl_rowhit + (size_t)t * L.R;
+        rowhit[r0] = s;
+        int cur = s, rr = r0;
+        while (rr < L.R - 1) {
+            const int u = L.upg[cur];
+            if (u < 0) break;
+            ++rr;
+            cur = u;
+            rowhit[rr] = u;
+        }
+        const int len = rr - r0 + 1;
+        L.tl_chain[t] = make_int4(s, hr, cur, rr);
+        TrackletHdr& H = L.tl[t];
+        H.start = s;
+        H.chain_len = len;
+        my_hits += len;
+        if (len < L.min_chain) {
+            H.valid = 0;
+            H.nhits = 0;
+            H.first = -1;
+            H.last = -1;
+            H.ndf = 0;
+        } else {
+            ++my_tl;
+        }
+    }
+    __shared__ int red[2];
+    if (threadIdx.x == 0) red[0] = red[1] = 0;
+    __syncthreads();
+    if (my_tl) atomicAdd(&red[0], my_tl);
+    if (my_hits) atomicAdd(&red[1], my_hits);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (red[0]) atomicAdd(&L.cnt->n_tracklets, red[0]);
+        if (red[1]) atomicAdd(&L.cnt->n_chain_hits, red[1]);
+    }
 }
 
 // Persistent lanes: every lane owns one tracklet at a time and advances it by
@@ -302,28 +348,32 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
     float chi2 = 0.0f;
     Fit f;
     // The tracklet's rowhit slot holds the hit of every row the forward pass
-    // visits (global index, -1 none) and yz its coordinates; the backward
-    // pass reads both one step ahead and rewrites rowhit in place.
+    // visits (global index, -1 none); the backward pass reads it ahead and
+    // rewrites it in place.
     int* rowhit = nullptr;
-    float2* yz = nullptr;
-    // inputs of the next row to process, loaded one step ahead
+    // Inputs of the next row, loaded one step ahead: for a row whose hit is
+    // known (chain rows forward, rows of the forward range backward) the hit
+    // and its coordinates, for a row to search its hit offset and grid.  The
+    // rowhit entry of the row after next is read one step earlier still, so
+    // that the coordinate load never waits on it.
     bool pknown = false;
-    int pb = 0, ph = -1;
+    int pb = 0, ph = -1, ph2 = -1;
     float2 pyz = make_float2(0.0f, 0.0f);
     RowGrid pG;
-    Spec sp;
-    sp.valid = false;
-    int my_tracklets = 0, my_valid = 0, my_hits = 0;
+    int my_valid = 0, my_hits = 0;
 
-    auto load_row = [&](int rr, bool fwdp) {
-        pknown = fwdp ? rr <= rk : rr >= r0;
-        pb = L.row_off[gbase + rr];
+    // stage row rn of the pass (requires ph2 = rowhit[rn] if rn is known)
+    auto stage = [&](int rn, bool fwdp) {
+        pknown = fwdp ? rn <= rk : rn >= r0;
         if (pknown) {
-            ph = rowhit[rr];
-            pyz = yz[rr];
+            ph = ph2;
+            if (ph >= 0) pyz = L.hyz[ph];
         } else {
-            pG = L.grid[gbase + rr];
+            pb = L.row_off[gbase + rn];
+            pG = L.grid[gbase + rn];
         }
+        const int rn2 = fwdp ? rn + 1 : rn - 1;
+        if (fwdp ? rn2 <= rk : rn2 >= r0) ph2 = rowhit[rn2];
     };
 
     bool exhausted = false;  // no start hit left for this lane
@@ -353,43 +403,20 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
         }
         if (t < 0) continue;
         if (phase == 0) {
-            const int s = L.starts[t];
-            const int hr = L.hrow[s];
-            gbase = (hr >> 8) * L.R;
-            r0 = hr & 255;
-            TrackletHdr& H = L.tl[t];
-            rowhit = L.tl_rowhit + (size_t)t * L.R;
-            yz = L.tl_yz + (size_t)t * L.R;
-            // follow the chain, recording its hits and their coordinates
-            float2 c0 = make_float2(L.hy[s], L.hz[s]);
-            rowhit[r0] = s;
-            yz[r0] = c0;
-            float2 ck = c0;
-            int cur = s, rr = r0;
-            while (rr < L.R - 1) {
-                const int u = L.upg[cur];
-                if (u < 0) break;
-                ++rr;
-                cur = u;
-                ck = make_float2(L.hy[u], L.hz[u]);
-                rowhit[rr] = u;
-                yz[rr] = ck;
-            }
-            rk = rr;
-            const int len = rk - r0 + 1;
-            H.start = s;
-            H.chain_len = len;
-            if (len < L.min_chain) {
-                H.valid = 0;
-                H.nhits = 0;
-                H.first = -1;
-                H.last = -1;
-                H.ndf = 0;
+            // the chain, followed by k_chains: start hit, row, end hit, end row
+            const int4 ch = L.tl_chain[t];
+            gbase = (ch.y >> 8) * L.R;
+            r0 = ch.y & 255;
+            rk = ch.w;
+            if (rk - r0 + 1 < L.min_chain) {  // header already written
                 t = -1;
                 continue;
             }
-            ++my_tracklets;
+            rowhit = L.tl_rowhit + (size_t)t * L.R;
+            const int h1 = rk > r0 ? rowhit[r0 + 1] : -1;
+            const float2 c0 = L.hyz[ch.x];
             // seed from the chord h0 -> hk, update at h0
+            const float2 ck = L.hyz[ch.z];
             const float x0 = xs[r0], x1 = xs[rk];
             const float tphi = (ck.x - c0.x) / (x1 - x0);
             const float dzdx = (ck.y - c0.y) / (x1 - x0);
@@ -408,8 +435,8 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             gap = 0;
             r = r0 + 1;
             phase = 1;
-            sp.valid = false;
-            if (r < L.R) load_row(r, true);
+            ph2 = h1;
+            if (r < L.R) stage(r, true);
         }
         // ---- one row step of the current pass ----
         const bool fwd = phase == 1;
@@ -418,28 +445,22 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             const bool known = pknown;
             const int base = pb;
             const RowGrid G = pG;
-            const Spec spc = sp;
             float my = pyz.x, mz = pyz.y;
             int h = known ? ph : -1;
             const int rn = fwd ? r + 1 : r - 1;
-            const bool has_next = fwd ? rn < L.R : rn >= 0;
-            if (has_next) load_row(rn, fwd);
-            sp.valid = false;
+            if (fwd ? rn < L.R : rn >= 0) stage(rn, fwd);
             if (!transport(f, xs[r], L)) {
                 end_pass = true;
             } else {
                 if (!known) {
                     if (outside(f, L)) end_pass = true;
-                    else h = search(f, G, base, spc, L, my, mz);
+                    else h = search(f, G, base, L, my, mz);
                 }
                 if (!end_pass) {
                     if (h >= 0) {
                         const float dchi2 = update(f, my, mz, L);
                         if (fwd) {
-                            if (!known) {
-                                rowhit[r] = h;
-                                yz[r] = make_float2(my, mz);
-                            }
+                            if (!known) rowhit[r] = h;
                             last = r;
 #pragma unroll
                             for (int i = 0; i < 5; ++i) PL(i) = f.p[i];
@@ -463,7 +484,6 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
                             if (++gap >= L.max_gap) end_pass = true;
                         }
                     }
-                    if (!end_pass && has_next && !pknown) speculate(f, xs[rn], pG, L, sp);
                     r = rn;
                 }
             }
@@ -475,7 +495,7 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             for (int i = 0; i < 5; ++i) f.p[i] = PL(i);
             seed_cov(f, L);
             f.x = xs[last];
-            const float2 c = yz[last];
+            const float2 c = L.hyz[rowhit[last]];
             chi2 = update(f, c.x, c.y, L);
             nupd = 1;
             first = last;
@@ -487,8 +507,10 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             gap = 0;
             phase = 2;
             r = last - 1;
-            sp.valid = false;
-            if (r >= 0) load_row(r, false);
+            if (r >= 0) {
+                ph2 = r >= r0 ? rowhit[r] : -1;
+                stage(r, false);
+            }
             continue;
         }
         // tracklet done: header (the hit weights are raised by k_weights)
@@ -520,17 +542,15 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
 #undef BEST
 #undef PL
     // block totals of the counters
-    __shared__ int red[3];
-    if (threadIdx.x == 0) red[0] = red[1] = red[2] = 0;
+    __shared__ int red[2];
+    if (threadIdx.x == 0) red[0] = red[1] = 0;
     __syncthreads();
-    if (my_tracklets) atomicAdd(&red[0], my_tracklets);
-    if (my_valid) atomicAdd(&red[1], my_valid);
-    if (my_hits) atomicAdd(&red[2], my_hits);
+    if (my_valid) atomicAdd(&red[0], my_valid);
+    if (my_hits) atomicAdd(&red[1], my_hits);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (red[0]) atomicAdd(&L.cnt->n_tracklets, red[0]);
-        if (red[1]) atomicAdd(&L.cnt->n_valid, red[1]);
-        if (red[2]) atomicAdd(&L.cnt->n_tracklet_hits, red[2]);
+        if (red[0]) atomicAdd(&L.cnt->n_valid, red[0]);
+        if (red[1]) atomicAdd(&L.cnt->n_tracklet_hits, red[1]);
     }
 }
 
@@ -569,6 +589,13 @@ void launch_constructor(const Launch& L, void* stream_, const KernelHook* hook)
     int dev = 0, n_sm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    {
+        long long cb = ((long long)L.t_cap + kChThreads - 1) / kChThreads;
+        if (cb > (long long)n_sm * 8) cb = (long long)n_sm * 8;
+        if (cb < 1) cb = 1;
+        k_chains<<<(int)cb, kChThreads, 0, stream>>>(L);
+        hook_after(hook, "k_chains");
+    }
     int blocks = per_sm * n_sm;
     const int need = (L.t_cap + kTlThreads - 1) / kTlThreads;
     if (blocks > need) blocks = need;

@@ -6,7 +6,7 @@
 //   rows        (global sector, row) records: counts, offsets, y-z grids;
 //               a batch is its events' sectors side by side, so every kernel
 //               sees one flat list of sectors
-//   hits        sorted by (sector, row, bin, cid): hy, hz (f32), hcid (event
+//   hits        sorted by (sector, row, bin, cid): hyz (f32 pairs), hcid (event
 //               cid), hrow (sector << 8 | row); bins hold row-local offsets
 //   links       up/dn/upc/dnc as int16 row-local indices into the adjacent row,
 //               upg the cleaned up link as a global hit index
@@ -22,6 +22,9 @@ constexpr int kMaxRows = 256;          // pad rows per sector (row index fits 8 
 constexpr int kMaxRowHits = 4096;      // hits of one (sector,row) handled in shared memory
 constexpr int kMaxSectorTracks = 4096; // emitted tracks per sector sorted in shared memory
 constexpr int kMaxBinsPerDim = 512;
+// y-z bins of a row with cnt hits: max(1, cnt * kBinsPerHitX2 / 2)
+constexpr int kBinsPerHitX2 = 4;
+constexpr int kMaxRowBins = kMaxRowHits * kBinsPerHitX2 / 2;
 constexpr long long kSpinLimit = 1LL << 22;  // bounded look-back waits
 
 struct EventDesc {
@@ -63,7 +66,8 @@ struct Counters {
     int n_bins;
     int ticket_rows, ticket_hits, ticket_sectors;
     int tl_next;          // work counter of the persistent constructor
-    int pad[15];
+    int n_chain_hits;     // hits on the chains of all start hits
+    int pad[14];
 };
 
 // Everything a kernel needs, passed by value.
@@ -97,16 +101,16 @@ struct Launch {
     unsigned long long* tile_state;  // look-back states (rows | hits | sectors)
     int n_row_tiles, n_hit_tiles;
     int* rank;                  // [n_total] arrival rank of a cluster in its row
-    float* tmp_y; float* tmp_z; int* tmp_cid;   // row-scattered
-    float* hy; float* hz; int* hcid; int* hrow; // sorted
+    float2* tmp_yz; int* tmp_cid;   // row-scattered (y, z)
+    float2* hyz; int* hcid; int* hrow; // sorted (y, z), cid, sector << 8 | row
     int* bin_start;
     int16_t* up; int16_t* dn; int16_t* upc; int16_t* dnc;
     int* upg;                   // [N] cleaned up link, global index or -1
     unsigned long long* weight;
     int* starts;                // [t_cap] global sorted index
     TrackletHdr* tl;            // [t_cap]
+    int4* tl_chain;             // [t_cap] start hit, its sector << 8 | row, chain end hit, end row
     int* tl_rowhit;             // [t_cap * R] global hit index or -1
-    float2* tl_yz;              // [t_cap * R] coordinates of the rowhit hits
     unsigned long long* tl_key; // [t_cap] sector-local sort key or ~0
     int* tl_nown;               // [t_cap]
     int* tl_out;                // [t_cap] output track index or -1

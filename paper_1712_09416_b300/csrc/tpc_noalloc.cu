@@ -32,7 +32,7 @@ constexpr int kNaMaxDevices = 64;
 // Layout of the scratch array (every size a multiple of 256 bytes).
 constexpr size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr long long kNaRS = (long long)kNaMaxSectors * kMaxRows;
-constexpr long long kNaBins = kNaMaxClusters / 2 + 2 * kNaRS + 16;
+constexpr long long kNaBins = kNaMaxClusters * kBinsPerHitX2 / 2 + 2 * kNaRS + 16;
 constexpr long long kNaRowTiles = kNaRS / 2048 + 2;
 constexpr long long kNaHitTiles = kNaMaxClusters / 2048 + 2;
 constexpr size_t kNaDesc = up256(sizeof(EventDesc) + 2 * sizeof(long long) +
@@ -41,7 +41,7 @@ constexpr size_t kNaZero = up256(up256(sizeof(Counters)) + 4 * (2 * kNaRS + 2 * 
                                  8 * (kNaRowTiles + kNaHitTiles + kNaMaxSectors) + 1024);
 constexpr size_t kNaBytes =
     kNaDesc + kNaZero + up256(4 * (kNaRS + 1)) + up256(sizeof(RowGrid) * kNaRS) +
-    up256(4 * kNaBins) + 8 * up256(4 * kNaMaxClusters) /* tmp y z cid rank, hy hz hcid hrow */ +
+    up256(4 * kNaBins) + 8 * up256(4 * kNaMaxClusters) /* tmp yz cid rank, hyz hcid hrow */ +
     2 * up256(4 * kNaMaxClusters) /* up dn */ + 2 * up256(4 * kNaMaxClusters) /* upc dnc */ +
     up256(4 * kNaMaxClusters) /* upg */ + up256(8 * kNaMaxClusters) /* weight */ +
     up256(4 * kNaMaxClusters) /* starts */;
@@ -175,12 +175,10 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
     L.row_off = (int*)take(4 * (kNaRS + 1));
     L.grid = (RowGrid*)take(sizeof(RowGrid) * kNaRS);
     L.bin_start = (int*)take(4 * kNaBins);
-    L.tmp_y = (float*)take(4 * kNaMaxClusters);
-    L.tmp_z = (float*)take(4 * kNaMaxClusters);
+    L.tmp_yz = (float2*)take(8 * kNaMaxClusters);
     L.tmp_cid = (int*)take(4 * kNaMaxClusters);
     L.rank = (int*)take(4 * kNaMaxClusters);
-    L.hy = (float*)take(4 * kNaMaxClusters);
-    L.hz = (float*)take(4 * kNaMaxClusters);
+    L.hyz = (float2*)take(8 * kNaMaxClusters);
     L.hcid = (int*)take(4 * kNaMaxClusters);
     L.hrow = (int*)take(4 * kNaMaxClusters);
     L.up = (int16_t*)take(4 * kNaMaxClusters);

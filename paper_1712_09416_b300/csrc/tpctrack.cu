@@ -89,16 +89,16 @@ struct Slot {
     size_t zero_cap = 0;
     int *row_off;
     RowGrid* grid;
-    float *tmp_y, *tmp_z;
+    float2* tmp_yz;
     int *tmp_cid, *rank;
-    float *hy, *hz;
+    float2* hyz;
     int *hcid, *hrow, *bin_start;
     int16_t *up, *dn, *upc, *dnc;
     unsigned long long* weight;
     int* starts;
     TrackletHdr* tl;
+    int4* tl_chain;
     int* tl_rowhit;
-    float2* tl_yz;
     int* upg;
     unsigned long long* tl_key;
     int *tl_nown, *tl_out, *tl_hitoff, *sec_trk_off, *sec_hit_off;
@@ -185,7 +185,7 @@ Caps make_caps(const tpc_track_config& c)
     k.r = c.max_rows > 0 ? c.max_rows : 159;
     k.s = k.e * 36;
     k.rs = (long long)k.s * k.r;
-    k.bins = k.n / 2 + 2 * k.rs + 16;
+    k.bins = k.n * kBinsPerHitX2 / 2 + 2 * k.rs + 16;
     k.t = (int)std::min<long long>(k.n / 8 + 4096, 0x7fffffffLL / 256);
     k.row_tiles = k.rs / kTileRows + 2;
     k.hit_tiles = k.n / kTileHits + 2;
@@ -214,12 +214,10 @@ size_t layout(Slot& s, char* base)
     s.zero_dev = take(s.zero_cap);
     s.row_off = (int*)take(4 * (k.rs + 1));
     s.grid = (RowGrid*)take(sizeof(RowGrid) * k.rs);
-    s.tmp_y = (float*)take(4 * k.n);
-    s.tmp_z = (float*)take(4 * k.n);
+    s.tmp_yz = (float2*)take(8 * k.n);
     s.tmp_cid = (int*)take(4 * k.n);
     s.rank = (int*)take(4 * k.n);
-    s.hy = (float*)take(4 * k.n);
-    s.hz = (float*)take(4 * k.n);
+    s.hyz = (float2*)take(8 * k.n);
     s.hcid = (int*)take(4 * k.n);
     s.hrow = (int*)take(4 * k.n);
     s.bin_start = (int*)take(4 * k.bins);
@@ -230,8 +228,8 @@ size_t layout(Slot& s, char* base)
     s.weight = (unsigned long long*)take(8 * k.n);
     s.starts = (int*)take(4 * (size_t)k.t);
     s.tl = (TrackletHdr*)take(sizeof(TrackletHdr) * (size_t)k.t);
+    s.tl_chain = (int4*)take(16 * (size_t)k.t);
     s.tl_rowhit = (int*)take(4 * (size_t)k.t * k.r);
-    s.tl_yz = (float2*)take(8 * (size_t)k.t * k.r);
     s.upg = (int*)take(4 * k.n);
     s.tl_key = (unsigned long long*)take(8 * (size_t)k.t);
     s.tl_nown = (int*)take(4 * (size_t)k.t);
@@ -455,12 +453,10 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     }
     L.row_off = s.row_off;
     L.grid = s.grid;
-    L.tmp_y = s.tmp_y;
-    L.tmp_z = s.tmp_z;
+    L.tmp_yz = s.tmp_yz;
     L.tmp_cid = s.tmp_cid;
     L.rank = s.rank;
-    L.hy = s.hy;
-    L.hz = s.hz;
+    L.hyz = s.hyz;
     L.hcid = s.hcid;
     L.hrow = s.hrow;
     L.bin_start = s.bin_start;
@@ -471,8 +467,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.weight = s.weight;
     L.starts = s.starts;
     L.tl = s.tl;
+    L.tl_chain = s.tl_chain;
     L.tl_rowhit = s.tl_rowhit;
-    L.tl_yz = s.tl_yz;
     L.upg = s.upg;
     L.tl_key = s.tl_key;
     L.tl_nown = s.tl_nown;
@@ -587,6 +583,7 @@ int collect(tpc_track_ctx* ctx, Slot& s)
     K.n_tracklet_hits = c.n_tracklet_hits;
     K.n_tracks = nt;
     K.n_track_hits = nh;
+    K.n_chain_hits = c.n_chain_hits;
     I.done = true;
     return TPC_OK;
 }
