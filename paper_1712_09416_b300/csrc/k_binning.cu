@@ -59,16 +59,34 @@ __device__ __forceinline__ void load_offsets(const Launch& L, long long* off_s)
     __syncthreads();
 }
 
+// Clusters per thread and loop step: their loads, and then their atomics,
+// are issued together.
+constexpr int kBinIlp = 4;
+
 __global__ void k_count(Launch L)
 {
     __shared__ long long off_s[kEvSmem + 1];
     load_offsets(L, off_s);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n_total; i += stride) {
-        float y, z;
-        int g, cid;
-        if (cluster_of(L, off_s, i, y, z, g, cid)) L.rank[i] = atomicAdd(&L.row_cnt[g], 1);
-        else atomicAdd(&L.cnt->n_invalid, 1);
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < L.n_total;
+         i0 += kBinIlp * stride) {
+        int g[kBinIlp];
+        bool ok[kBinIlp];
+#pragma unroll
+        for (int k = 0; k < kBinIlp; ++k) {
+            const long long i = i0 + k * stride;
+            float y, z;
+            int cid;
+            g[k] = 0;
+            ok[k] = i < L.n_total && cluster_of(L, off_s, i, y, z, g[k], cid);
+        }
+#pragma unroll
+        for (int k = 0; k < kBinIlp; ++k) {
+            const long long i = i0 + k * stride;
+            if (i >= L.n_total) break;
+            if (ok[k]) L.rank[i] = atomicAdd(&L.row_cnt[g[k] * kCntPad], 1);
+            else atomicAdd(&L.cnt->n_invalid, 1);
+        }
     }
 }
 
@@ -107,8 +125,9 @@ __device__ __forceinline__ RowGrid make_grid(const Launch& L, int g, int cnt)
 }
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanItems = kRowTile / kScanThreads;
+constexpr int kScanTile = kRowTile;
+static_assert(kScanItems * kScanThreads == kRowTile, "row tile");
 
 // block-wide exclusive scan of one packed value per thread; returns the
 // exclusive prefix of this thread and the block total in *total
@@ -159,7 +178,7 @@ __global__ void __launch_bounds__(kScanThreads) k_rowscan(Launch L)
         const int g = g0 + k;
         unsigned long long v = 0;
         if (g < L.RS) {
-            const int c = L.row_cnt[g];
+            const int c = L.row_cnt[g * kCntPad];
             RowGrid G = make_grid(L, g, c);
             L.grid[g] = G;
             v = pack2((unsigned)c, (unsigned)(G.ny * G.nz + 1));
@@ -169,7 +188,10 @@ __global__ void __launch_bounds__(kScanThreads) k_rowscan(Launch L)
     }
     unsigned long long total;
     const unsigned long long excl = block_excl_scan(sum, &total);
-    if (threadIdx.x == 0) prefix_s = lookback_exclusive(L.tile_state, tile, total, L.cnt);
+    if (threadIdx.x < 32) {
+        const unsigned long long p = lookback_warp(L.tile_state, tile, total, L.cnt);
+        if (threadIdx.x == 0) prefix_s = p;
+    }
     __syncthreads();
     const unsigned long long base = prefix_s + excl;
 #pragma unroll
@@ -180,7 +202,7 @@ __global__ void __launch_bounds__(kScanThreads) k_rowscan(Launch L)
             L.row_off[g] = (int)unpack_a(v);
             L.grid[g].bin_off = (int)unpack_b(v);
             if (g == L.RS - 1) {
-                const int c = L.row_cnt[g];
+                const int c = L.row_cnt[g * kCntPad];
                 const RowGrid G = L.grid[g];
                 L.row_off[L.RS] = (int)unpack_a(v) + c;
                 L.cnt->n_bins = (int)unpack_b(v) + G.ny * G.nz + 1;
@@ -194,17 +216,28 @@ __global__ void k_scatter(Launch L)
     __shared__ long long off_s[kEvSmem + 1];
     load_offsets(L, off_s);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n_total; i += stride) {
-        float y, z;
-        int g, cid;
-        if (!cluster_of(L, off_s, i, y, z, g, cid)) continue;
-        const int pos = L.row_off[g] + L.rank[i];
-        L.tmp_yz[pos] = make_float2(y, z);
-        L.tmp_cid[pos] = cid;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < L.n_total;
+         i0 += kBinIlp * stride) {
+        float y[kBinIlp], z[kBinIlp];
+        int pos[kBinIlp], cid[kBinIlp];
+#pragma unroll
+        for (int k = 0; k < kBinIlp; ++k) {
+            const long long i = i0 + k * stride;
+            int g = 0;
+            pos[k] = -1;
+            if (i < L.n_total && cluster_of(L, off_s, i, y[k], z[k], g, cid[k]))
+                pos[k] = L.row_off[g] + L.rank[i];
+        }
+#pragma unroll
+        for (int k = 0; k < kBinIlp; ++k) {
+            if (pos[k] < 0) continue;
+            L.tmp_yz[pos[k]] = make_float2(y[k], z[k]);
+            L.tmp_cid[pos[k]] = cid[k];
+        }
     }
 }
 
-constexpr int kSortThreads = 128;
+constexpr int kSortThreads = 512;
 
 __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
 {

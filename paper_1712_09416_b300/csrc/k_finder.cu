@@ -218,8 +218,9 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbours(Launch L)
 }
 
 constexpr int kCsThreads = 256;
-constexpr int kCsItems = 8;
-constexpr int kCsTile = kCsThreads * kCsItems;
+constexpr int kCsItems = kHitTile / kCsThreads;
+constexpr int kCsTile = kHitTile;
+static_assert(kCsItems * kCsThreads == kHitTile, "hit tile");
 
 __global__ void __launch_bounds__(kCsThreads) k_clean_starts(Launch L)
 {
@@ -284,20 +285,26 @@ __global__ void __launch_bounds__(kCsThreads) k_clean_starts(Launch L)
         if (lane == 0) warp_links[wid] = lk;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         int run = 0;
-        for (int k = 0; k < kCsItems; ++k)
-            for (int w = 0; w < kCsThreads / 32; ++w) {
-                const int c = kw_cnt[k][w];
-                kw_cnt[k][w] = run;
-                run += c;
-            }
-        int links = 0;
-        for (int w = 0; w < kCsThreads / 32; ++w) links += warp_links[w];
-        if (links) atomicAdd(&L.cnt->n_links, links);
-        prefix_s = lookback_exclusive(L.tile_state + L.n_row_tiles, tile,
-                                      (unsigned long long)run, L.cnt);
-        if (tile == (int)gridDim.x - 1) L.cnt->n_starts = (int)(prefix_s + run);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kCsItems; ++k)
+                for (int w = 0; w < kCsThreads / 32; ++w) {
+                    const int c = kw_cnt[k][w];
+                    kw_cnt[k][w] = run;
+                    run += c;
+                }
+            int links = 0;
+            for (int w = 0; w < kCsThreads / 32; ++w) links += warp_links[w];
+            if (links) atomicAdd(&L.cnt->n_links, links);
+        }
+        run = __shfl_sync(0xffffffffu, run, 0);
+        const unsigned long long p =
+            lookback_warp(L.tile_state + L.n_row_tiles, tile, (unsigned long long)run, L.cnt);
+        if (threadIdx.x == 0) {
+            prefix_s = p;
+            if (tile == (int)gridDim.x - 1) L.cnt->n_starts = (int)(p + run);
+        }
     }
     __syncthreads();
     const int pre = (int)prefix_s;

@@ -10,8 +10,8 @@
 //                 also marks the tracklet range of every sector (tracklets
 //                 are ordered by sector because start hits are)
 //   k_sel_sort    one block per sector, in sector order: compacts the
-//                 emitted tracklets with a warp ballot, sorts their keys in
-//                 shared memory (bitonic), scans their hit counts and takes
+//                 emitted tracklets, sorts their keys in shared memory (rank
+//                 sort up to 2048 keys, else bitonic), scans their hit counts and takes
 //                 the sector's output offsets from a decoupled look-back
 //   k_sel_write   one warp per emitted tracklet: header and owned hit cids
 // Bytes per cluster: rowhit 2 + weight 8 per assigned hit (decide), about
@@ -69,6 +69,8 @@ __global__ void k_sel_decide(Launch L)
 }
 
 constexpr int kSortThreads = 512;
+// sectors with at most this many emitted tracks are rank-sorted
+constexpr int kRankSortMax = kMaxSectorTracks / 2;
 
 __global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
 {
@@ -100,8 +102,28 @@ __global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
         if (threadIdx.x == 0) atomicExch(&L.cnt->ovf_sector, 1);
         m = kMaxSectorTracks;
     }
+    if (m <= kRankSortMax) {
+        // rank sort (keys are unique): the rank of a key is the number of
+        // smaller keys; the sorted copy goes to the upper half and back
+        unsigned long long* k2 = keys + kRankSortMax;
+        int* i2 = idx + kRankSortMax;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const unsigned long long a = keys[i];
+            int rank = 0;
+            for (int j = 0; j < m; ++j) rank += keys[j] < a ? 1 : 0;
+            k2[rank] = a;
+            i2[rank] = idx[i];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            keys[i] = k2[i];
+            idx[i] = i2[i];
+        }
+        __syncthreads();
+    }
     int P = 1;
     while (P < m) P <<= 1;
+    if (m <= kRankSortMax) P = 1;  // sorted already: no bitonic stage runs
     for (int i = m + threadIdx.x; i < P; i += blockDim.x) {
         keys[i] = kNone;
         idx[i] = -1;
@@ -141,24 +163,30 @@ __global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
     }
     if (lane == 31) warp_sum[wid] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         int run = 0;
-        for (int w = 0; w < kSortThreads / 32; ++w) {
-            const int v = warp_sum[w];
-            warp_sum[w] = run;
-            run += v;
+        if (threadIdx.x == 0) {
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                const int v = warp_sum[w];
+                warp_sum[w] = run;
+                run += v;
+            }
         }
-        prefix_s = lookback_exclusive(L.tile_state + L.n_row_tiles + L.n_hit_tiles, g,
-                                      pack2((unsigned)m, (unsigned)run), L.cnt);
-        const int tb = (int)unpack_a(prefix_s), hb = (int)unpack_b(prefix_s);
-        L.sec_trk_off[g] = tb;
-        L.sec_hit_off[g] = hb;
-        if (g == L.S - 1) {
-            L.sec_trk_off[L.S] = tb + m;
-            L.sec_hit_off[L.S] = hb + run;
-            L.cnt->n_tracks = tb + m;
-            L.cnt->n_track_hits = hb + run;
-            L.k_hit_off[tb + m] = hb + run;
+        run = __shfl_sync(0xffffffffu, run, 0);
+        const unsigned long long p = lookback_warp(L.tile_state + L.n_row_tiles + L.n_hit_tiles,
+                                                   g, pack2((unsigned)m, (unsigned)run), L.cnt);
+        if (threadIdx.x == 0) {
+            prefix_s = p;
+            const int tb = (int)unpack_a(p), hb = (int)unpack_b(p);
+            L.sec_trk_off[g] = tb;
+            L.sec_hit_off[g] = hb;
+            if (g == L.S - 1) {
+                L.sec_trk_off[L.S] = tb + m;
+                L.sec_hit_off[L.S] = hb + run;
+                L.cnt->n_tracks = tb + m;
+                L.cnt->n_track_hits = hb + run;
+                L.k_hit_off[tb + m] = hb + run;
+            }
         }
     }
     __syncthreads();

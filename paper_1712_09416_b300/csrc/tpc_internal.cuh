@@ -26,6 +26,11 @@ constexpr int kMaxBinsPerDim = 512;
 constexpr int kBinsPerHitX2 = 4;
 constexpr int kMaxRowBins = kMaxRowHits * kBinsPerHitX2 / 2;
 constexpr long long kSpinLimit = 1LL << 22;  // bounded look-back waits
+constexpr int kRowTile = 512;    // (sector, row) records per look-back tile of k_rowscan
+constexpr int kHitTile = 2048;   // sorted hits per look-back tile of k_clean_starts
+// Row counters one per 32-byte sector: the clusters of an event hit a few
+// thousand counters with atomics, and counters sharing a sector serialise.
+constexpr int kCntPad = 8;
 
 struct EventDesc {
     const float* y;
@@ -94,8 +99,7 @@ struct Launch {
     EventDesc* ev;              // [n_events]
     long long* ev_off;          // [n_events + 1] cluster offsets
     int* sec_event;             // [S] event of a global sector
-    int* row_cnt;               // [RS]
-    int* row_fill;              // [RS]
+    int* row_cnt;               // [RS * kCntPad] hit count of row g at g * kCntPad
     int* row_off;               // [RS + 1]
     RowGrid* grid;              // [RS]
     unsigned long long* tile_state;  // look-back states (rows | hits | sectors)
@@ -126,7 +130,7 @@ struct Launch {
 };
 
 // ---------------------------------------------------------------------------
-// ordered prefix across thread blocks (decoupled look-back), one thread calls.
+// ordered prefix across thread blocks (decoupled look-back), one warp calls.
 // The 64-bit state holds a 2-bit status (1 aggregate, 2 inclusive) over a
 // 62-bit payload; payloads are two packed 31-bit counts (a << 31 | b) whose
 // sums never carry.  Waits are bounded; on timeout cnt->timeout is set.
@@ -155,34 +159,47 @@ __device__ __forceinline__ unsigned unpack_b(unsigned long long v)
     return (unsigned)(v & 0x7FFFFFFFULL);
 }
 
-__device__ inline unsigned long long lookback_exclusive(unsigned long long* state, int tile,
-                                                        unsigned long long aggregate,
-                                                        Counters* cnt)
+// Called by all 32 lanes of one warp (the same arguments on every lane);
+// returns the exclusive prefix of `tile` on every lane.  Each round reads the
+// states of the 32 nearest unread predecessors at once (lane j reads tile
+// base - j): when every state up to the nearest inclusive one is published,
+// their payloads are summed; the walk ends at an inclusive state.
+__device__ inline unsigned long long lookback_warp(unsigned long long* state, int tile,
+                                                   unsigned long long aggregate, Counters* cnt)
 {
+    const int lane = threadIdx.x & 31;
     if (tile == 0) {
-        st_release(&state[0], (2ULL << 62) | aggregate);
+        if (lane == 0) st_release(&state[0], (2ULL << 62) | aggregate);
         return 0;
     }
-    st_release(&state[tile], (1ULL << 62) | aggregate);
+    if (lane == 0) st_release(&state[tile], (1ULL << 62) | aggregate);
     unsigned long long excl = 0;
-    int t = tile - 1;
+    int base = tile - 1;
     long long spins = 0;
-    while (t >= 0) {
-        const unsigned long long v = ld_acquire(&state[t]);
+    for (;;) {
+        const int t = base - lane;
+        const unsigned long long v = t >= 0 ? ld_acquire(&state[t]) : (2ULL << 62);
         const unsigned f = (unsigned)(v >> 62);
-        if (f == 0) {
+        const unsigned pm = __ballot_sync(0xffffffffu, f == 2);
+        const unsigned zm = __ballot_sync(0xffffffffu, f == 0);
+        const int first_p = pm ? __ffs(pm) - 1 : 31;
+        const unsigned upto = first_p == 31 ? 0xffffffffu : ((2u << first_p) - 1u);
+        if (zm & upto) {
             if (++spins > kSpinLimit) {
-                atomicExch(&cnt->timeout, 1);
+                if (lane == 0) atomicExch(&cnt->timeout, 1);
                 break;
             }
             __nanosleep(20);
             continue;
         }
-        excl += v & kPayload;
-        if (f == 2) break;
-        --t;
+        unsigned long long part = (lane <= first_p) ? (v & kPayload) : 0ULL;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        excl += part;
+        if (pm) break;
+        base -= 32;
     }
-    st_release(&state[tile], (2ULL << 62) | (excl + aggregate));
+    if (lane == 0) st_release(&state[tile], (2ULL << 62) | (excl + aggregate));
     return excl;
 }
 

@@ -33,11 +33,11 @@ constexpr int kNaMaxDevices = 64;
 constexpr size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr long long kNaRS = (long long)kNaMaxSectors * kMaxRows;
 constexpr long long kNaBins = kNaMaxClusters * kBinsPerHitX2 / 2 + 2 * kNaRS + 16;
-constexpr long long kNaRowTiles = kNaRS / 2048 + 2;
-constexpr long long kNaHitTiles = kNaMaxClusters / 2048 + 2;
+constexpr long long kNaRowTiles = kNaRS / kRowTile + 2;
+constexpr long long kNaHitTiles = kNaMaxClusters / kHitTile + 2;
 constexpr size_t kNaDesc = up256(sizeof(EventDesc) + 2 * sizeof(long long) +
                                  sizeof(int) * kNaMaxSectors + sizeof(float) * kMaxRows);
-constexpr size_t kNaZero = up256(up256(sizeof(Counters)) + 4 * (2 * kNaRS + 2 * kNaMaxSectors) +
+constexpr size_t kNaZero = up256(up256(sizeof(Counters)) + 4 * (kNaRS * kCntPad + 2 * kNaMaxSectors) +
                                  8 * (kNaRowTiles + kNaHitTiles + kNaMaxSectors) + 1024);
 constexpr size_t kNaBytes =
     kNaDesc + kNaZero + up256(4 * (kNaRS + 1)) + up256(sizeof(RowGrid) * kNaRS) +
@@ -162,12 +162,11 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
             return p;
         };
         L.cnt = (Counters*)z(sizeof(Counters));
-        L.row_cnt = (int*)z(4 * (size_t)L.RS);
-        L.row_fill = (int*)z(4 * (size_t)L.RS);
+        L.row_cnt = (int*)z(4 * (size_t)L.RS * kCntPad);
         L.sec_first = (int*)z(4 * (size_t)n_sec);
         L.sec_end = (int*)z(4 * (size_t)n_sec);
-        L.n_row_tiles = (int)((L.RS + 2047) / 2048);
-        L.n_hit_tiles = (int)((n + 2047) / 2048);
+        L.n_row_tiles = (int)((L.RS + kRowTile - 1) / kRowTile);
+        L.n_hit_tiles = (int)((n + kHitTile - 1) / kHitTile);
         if (L.n_hit_tiles < 1) L.n_hit_tiles = 1;
         L.tile_state = (unsigned long long*)z(8 * ((size_t)L.n_row_tiles + L.n_hit_tiles + n_sec));
         if (cudaMemsetAsync(zero, 0, zo, st) != cudaSuccess) return TPC_ECUDA;

@@ -33,8 +33,6 @@ namespace tpc {
 namespace {
 
 constexpr double kKappa = 0.299792458e-2;  // cm^-1 per (GeV/c)^-1 per tesla
-constexpr int kTileRows = 2048;            // rows per look-back tile (k_rowscan)
-constexpr int kTileHits = 2048;            // hits per look-back tile (k_clean_starts)
 constexpr int kMaxEventsPerLaunch = 1024;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -85,7 +83,7 @@ struct Slot {
     float *in_y, *in_z;
     uint16_t *in_row, *in_sec;
     void* desc_dev;      // EventDesc[e] | ev_off[e+1] | sec_event[s]
-    char* zero_dev;      // counters | row_cnt | row_fill | sec_first | sec_end | tile_state
+    char* zero_dev;      // counters | row_cnt | sec_first | sec_end | tile_state
     size_t zero_cap = 0;
     int *row_off;
     RowGrid* grid;
@@ -187,8 +185,8 @@ Caps make_caps(const tpc_track_config& c)
     k.rs = (long long)k.s * k.r;
     k.bins = k.n * kBinsPerHitX2 / 2 + 2 * k.rs + 16;
     k.t = (int)std::min<long long>(k.n / 8 + 4096, 0x7fffffffLL / 256);
-    k.row_tiles = k.rs / kTileRows + 2;
-    k.hit_tiles = k.n / kTileHits + 2;
+    k.row_tiles = k.rs / kRowTile + 2;
+    k.hit_tiles = k.n / kHitTile + 2;
     return k;
 }
 
@@ -210,7 +208,7 @@ size_t layout(Slot& s, char* base)
     s.desc_bytes = sizeof(EventDesc) * k.e + sizeof(long long) * (k.e + 1) + sizeof(int) * k.s +
                    sizeof(float) * kMaxRows + 64;
     s.desc_dev = take(s.desc_bytes);
-    s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (2 * k.rs + 2 * k.s) + 8 * (k.row_tiles + k.hit_tiles + k.s) + 4096;
+    s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (k.rs * kCntPad + 2 * k.s) + 8 * (k.row_tiles + k.hit_tiles + k.s) + 4096;
     s.zero_dev = take(s.zero_cap);
     s.row_off = (int*)take(4 * (k.rs + 1));
     s.grid = (RowGrid*)take(sizeof(RowGrid) * k.rs);
@@ -438,13 +436,12 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
             return p;
         };
         L.cnt = (Counters*)take(sizeof(Counters));
-        L.row_cnt = (int*)take(4 * (size_t)L.RS);
-        L.row_fill = (int*)take(4 * (size_t)L.RS);
+        L.row_cnt = (int*)take(4 * (size_t)L.RS * kCntPad);
         L.sec_first = (int*)take(4 * (size_t)S);
         L.sec_end = (int*)take(4 * (size_t)S);
-        L.n_row_tiles = (int)((L.RS + kTileRows - 1) / kTileRows);
+        L.n_row_tiles = (int)((L.RS + kRowTile - 1) / kRowTile);
         if (L.n_row_tiles < 1) L.n_row_tiles = 1;
-        L.n_hit_tiles = (int)((n_total + kTileHits - 1) / kTileHits);
+        L.n_hit_tiles = (int)((n_total + kHitTile - 1) / kHitTile);
         if (L.n_hit_tiles < 1) L.n_hit_tiles = 1;
         L.tile_state = (unsigned long long*)take(8 * ((size_t)L.n_row_tiles + L.n_hit_tiles + S));
         zo = align_up(zo, 16);
