@@ -23,7 +23,7 @@ namespace tpc {
 
 namespace {
 
-constexpr int kNbThreads = 256;
+constexpr int kNbThreads = 128;
 
 struct RowView {      // one adjacent row
     const float2* yz;
@@ -41,14 +41,13 @@ struct CandList {
     int n;
 };
 
-__device__ __forceinline__ void push(CandList& c, float sy, float sz, int cid, int k)
+__device__ __forceinline__ void push(CandList& c, float sy, float sz, int k)
 {
 #pragma unroll
     for (int j = 0; j < kList; ++j) {
         if (c.n == j) {
             c.sy[j] = sy;
             c.sz[j] = sz;
-            c.cid[j] = cid;
             c.k[j] = k;
         }
     }
@@ -58,7 +57,9 @@ __device__ __forceinline__ void push(CandList& c, float sy, float sz, int cid, i
 // Scan one side's window: admissible candidates and their slopes.  up = true
 // gives slopes (c - h) * inv, up = false gives (h - c) * inv.  The hit ranges
 // of the window's z-bins (up to four) are walked as one flat index space so
-// that lanes with different bin counts stay together.
+// that lanes with different bin counts stay together, four candidates per
+// step with their loads issued together; the cids of the kept candidates are
+// read at the end.
 __device__ __forceinline__ void collect(const RowView& V, float yh, float zh, float inv, float wy,
                                        float wz, bool up, CandList& c)
 {
@@ -66,12 +67,11 @@ __device__ __forceinline__ void collect(const RowView& V, float yh, float zh, fl
     const int y0 = bin_y(V.G, yh - wy - my), y1 = bin_y(V.G, yh + wy + my);
     const int z0 = bin_z(V.G, zh - wz - mz), z1 = bin_z(V.G, zh + wz + mz);
     c.n = 0;
-    auto test = [&](int k) {
-        const float2 v = V.yz[k];
+    auto test = [&](int k, float2 v) {
         const float ddy = up ? __fsub_rn(v.x, yh) : __fsub_rn(yh, v.x);
         const float ddz = up ? __fsub_rn(v.y, zh) : __fsub_rn(zh, v.y);
         if (fabsf(ddy) <= wy && fabsf(ddz) <= wz)
-            push(c, __fmul_rn(ddy, inv), __fmul_rn(ddz, inv), V.cid[k], k);
+            push(c, __fmul_rn(ddy, inv), __fmul_rn(ddz, inv), k);
     };
     if (z1 - z0 < 4) {
         int a[4], n[4];
@@ -86,17 +86,29 @@ __device__ __forceinline__ void collect(const RowView& V, float yh, float zh, fl
             }
         }
         const int c1 = n[0], c2 = c1 + n[1], c3 = c2 + n[2], tot = c3 + n[3];
-        for (int q = 0; q < tot; ++q) {
-            const int k = q < c1 ? a[0] + q : q < c2 ? a[1] + (q - c1) : q < c3 ? a[2] + (q - c2)
-                                                                               : a[3] + (q - c3);
-            test(k);
+        for (int q = 0; q < tot; q += 4) {
+            int kk[4];
+            float2 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int qj = q + j < tot ? q + j : q;
+                kk[j] = qj < c1 ? a[0] + qj : qj < c2 ? a[1] + (qj - c1)
+                                          : qj < c3 ? a[2] + (qj - c2) : a[3] + (qj - c3);
+                v[j] = V.yz[kk[j]];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (q + j < tot) test(kk[j], v[j]);
         }
     } else {
         for (int bz = z0; bz <= z1; ++bz) {
             const int ka = V.bins[bz * V.G.ny + y0], kb = V.bins[bz * V.G.ny + y1 + 1];
-            for (int k = ka; k < kb; ++k) test(k);
+            for (int k = ka; k < kb; ++k) test(k, V.yz[k]);
         }
     }
+#pragma unroll
+    for (int j = 0; j < kList; ++j)
+        if (j < c.n) c.cid[j] = V.cid[c.k[j]];
 }
 
 __device__ __forceinline__ void consider(float syu, float szu, int cu, int ku, float syd, float szd,

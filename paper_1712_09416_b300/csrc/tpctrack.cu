@@ -133,10 +133,17 @@ struct Request {
     std::chrono::steady_clock::time_point t_submit;
 };
 
+// A served ticket's tracks live in a pinned host buffer of the context's
+// pool, written by device-to-host copies; the buffer goes back to the pool
+// when the ticket is released.
+struct PinnedBuf {
+    char* p = nullptr;
+    size_t cap = 0;
+};
+
 struct TicketResult {
     int status = TPC_EBUSY;
-    std::vector<int32_t> sector, ndf, hit_off, hit_cid;
-    std::vector<float> x, param, cov, chi2;
+    PinnedBuf buf;
     tpc_tracks view{};
 };
 
@@ -153,6 +160,8 @@ struct tpc_track_ctx {
     std::deque<tpc::Request> queue;
     std::map<uint64_t, std::unique_ptr<tpc::TicketResult>> results;
     std::vector<std::thread> workers;
+    std::mutex pool_mu;
+    std::vector<tpc::PinnedBuf> pool;  // free pinned result buffers
     bool stop = false;
     uint64_t next_ticket = 1;
     std::atomic<int> direct_busy{0};
@@ -519,7 +528,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
 }
 
 // Wait for the slot's launch, check the device status, copy the results.
-int collect(tpc_track_ctx* ctx, Slot& s)
+// Wait for the slot's launch and turn its device status into a code.
+int launch_status(tpc_track_ctx* ctx, Slot& s)
 {
     LaunchInfo& I = s.info;
     if (!I.pending) return fail(ctx, TPC_EINVAL, "no launch pending");
@@ -527,13 +537,41 @@ int collect(tpc_track_ctx* ctx, Slot& s)
     CUDA_TRY(ctx, cudaEventSynchronize(s.done_ev));
     CUDA_TRY(ctx, cudaGetLastError());
     const Counters& c = *s.cnt_host;
-    s.tracks.assign(I.n_ev, tpc_tracks{});
     if (c.n_invalid) return fail(ctx, TPC_EINVAL, std::to_string(c.n_invalid) + " invalid clusters (row, sector or coordinate)");
     if (c.timeout) return fail(ctx, TPC_ETIMEOUT, "a bounded device wait gave up");
     if (c.ovf_row) return fail(ctx, TPC_ECAPACITY, "a pad row holds more than 4096 clusters");
     if (c.ovf_tracklets || c.n_starts > s.caps.t)
         return fail(ctx, TPC_ECAPACITY, "start hits exceed the tracklet slots");
     if (c.ovf_sector) return fail(ctx, TPC_ECAPACITY, "a sector emits more than 4096 tracks");
+    return TPC_OK;
+}
+
+void fill_counters(Slot& s)
+{
+    LaunchInfo& I = s.info;
+    const Counters& c = *s.cnt_host;
+    tpc_track_counters& K = I.counters;
+    K.n_clusters = 0;
+    for (long long n : I.ev_n) K.n_clusters += n;
+    K.n_rows_total = (int64_t)I.S * I.R;
+    K.n_bins = c.n_bins;
+    K.n_links = c.n_links;
+    K.n_starts = c.n_starts;
+    K.n_tracklets = c.n_tracklets;
+    K.n_valid_tracklets = c.n_valid;
+    K.n_tracklet_hits = c.n_tracklet_hits;
+    K.n_tracks = c.n_tracks;
+    K.n_track_hits = c.n_track_hits;
+    K.n_chain_hits = c.n_chain_hits;
+    I.done = true;
+}
+
+int collect(tpc_track_ctx* ctx, Slot& s)
+{
+    LaunchInfo& I = s.info;
+    s.tracks.assign(I.n_ev, tpc_tracks{});
+    if (int rc = launch_status(ctx, s)) return rc;
+    const Counters& c = *s.cnt_host;
     const int nt = c.n_tracks, nh = c.n_track_hits;
     cudaStream_t st = s.stream;
     if (nt > 0) {
@@ -568,20 +606,99 @@ int collect(tpc_track_ctx* ctx, Slot& s)
         T.hit_off = eho;
         eho += (t1 - t0) + 1;
     }
-    tpc_track_counters& K = I.counters;
-    K.n_clusters = 0;
-    for (long long n : I.ev_n) K.n_clusters += n;
-    K.n_rows_total = (int64_t)I.S * I.R;
-    K.n_bins = c.n_bins;
-    K.n_links = c.n_links;
-    K.n_starts = c.n_starts;
-    K.n_tracklets = c.n_tracklets;
-    K.n_valid_tracklets = c.n_valid;
-    K.n_tracklet_hits = c.n_tracklet_hits;
-    K.n_tracks = nt;
-    K.n_track_hits = nh;
-    K.n_chain_hits = c.n_chain_hits;
-    I.done = true;
+    fill_counters(s);
+    return TPC_OK;
+}
+
+PinnedBuf pool_get(tpc_track_ctx* ctx, size_t need)
+{
+    {
+        std::lock_guard<std::mutex> lk(ctx->pool_mu);
+        for (size_t i = 0; i < ctx->pool.size(); ++i)
+            if (ctx->pool[i].cap >= need) {
+                PinnedBuf b = ctx->pool[i];
+                ctx->pool[i] = ctx->pool.back();
+                ctx->pool.pop_back();
+                return b;
+            }
+    }
+    PinnedBuf b;
+    const size_t cap = align_up(need + need / 4 + 4096, 1 << 20);
+    if (cudaHostAlloc((void**)&b.p, cap, cudaHostAllocDefault) == cudaSuccess) b.cap = cap;
+    else b.p = nullptr;
+    return b;
+}
+
+void pool_put(tpc_track_ctx* ctx, PinnedBuf b)
+{
+    if (!b.p) return;
+    std::lock_guard<std::mutex> lk(ctx->pool_mu);
+    ctx->pool.push_back(b);
+}
+
+// Served form: wait for the slot's launch and copy every event's tracks from
+// the device straight into a pinned buffer of its ticket (no host copy).
+int collect_to_tickets(tpc_track_ctx* ctx, Slot& s, std::vector<std::unique_ptr<TicketResult>>& out)
+{
+    LaunchInfo& I = s.info;
+    if (int rc = launch_status(ctx, s)) return rc;
+    const Counters& c = *s.cnt_host;
+    const int nt = c.n_tracks;
+    cudaStream_t st = s.stream;
+    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_trk_off, s.sec_trk_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_hit_off, s.sec_hit_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    std::vector<int> h0s(I.n_ev);
+    for (int e = 0; e < I.n_ev; ++e) {
+        const int sb = I.ev_sec_base[e], se = sb + I.ev_n_sec[e];
+        const int t0 = nt > 0 ? s.out.sec_trk_off[sb] : 0, t1 = nt > 0 ? s.out.sec_trk_off[se] : 0;
+        const int h0 = nt > 0 ? s.out.sec_hit_off[sb] : 0, h1 = nt > 0 ? s.out.sec_hit_off[se] : 0;
+        const size_t m = (size_t)(t1 - t0), mh = (size_t)(h1 - h0);
+        size_t off = 0;
+        auto place = [&](size_t bytes) {
+            const size_t o = off;
+            off = align_up(off + bytes, 16);
+            return o;
+        };
+        const size_t o_sec = place(4 * m), o_x = place(4 * m), o_par = place(20 * m),
+                     o_cov = place(60 * m), o_chi = place(4 * m), o_ndf = place(4 * m),
+                     o_ho = place(4 * (m + 1)), o_hc = place(4 * mh);
+        TicketResult& R = *out[e];
+        R.buf = pool_get(ctx, off);
+        if (!R.buf.p) return fail(ctx, TPC_ENOMEM, "pinned result buffer");
+        char* b = R.buf.p;
+        if (m > 0) {
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_sec, s.k_sector + t0, 4 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_x, s.k_x + t0, 4 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_par, s.k_param + 5 * (size_t)t0, 20 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_cov, s.k_cov + 15 * (size_t)t0, 60 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_chi, s.k_chi2 + t0, 4 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_ndf, s.k_ndf + t0, 4 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_ho, s.k_hit_off + t0, 4 * (m + 1), cudaMemcpyDeviceToHost, st));
+        }
+        if (mh > 0)
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_hc, s.k_hit_cid + h0, 4 * mh, cudaMemcpyDeviceToHost, st));
+        tpc_tracks& V = R.view;
+        V.n_tracks = (int64_t)m;
+        V.sector = (const int32_t*)(b + o_sec);
+        V.x = (const float*)(b + o_x);
+        V.param = (const float*)(b + o_par);
+        V.cov = (const float*)(b + o_cov);
+        V.chi2 = (const float*)(b + o_chi);
+        V.ndf = (const int32_t*)(b + o_ndf);
+        V.hit_off = (const int32_t*)(b + o_ho);
+        V.hit_cid = (const int32_t*)(b + o_hc);
+        h0s[e] = h0;
+        if (m == 0) *(int32_t*)(b + o_ho) = 0;
+    }
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    for (int e = 0; e < I.n_ev; ++e) {  // hit offsets relative to the event
+        TicketResult& R = *out[e];
+        int32_t* ho = (int32_t*)R.view.hit_off;
+        if (R.view.n_tracks > 0)
+            for (int64_t j = 0; j <= R.view.n_tracks; ++j) ho[j] -= h0s[e];
+    }
+    fill_counters(s);
     return TPC_OK;
 }
 
@@ -717,38 +834,19 @@ void worker(tpc_track_ctx* ctx, Slot* s)
         tpc_geometry g = batch.front().geom;
         g.row_x = batch.front().row_x.data();
         const auto t0 = std::chrono::steady_clock::now();
+        std::vector<std::unique_ptr<TicketResult>> done(batch.size());
+        for (auto& d : done) d = std::make_unique<TicketResult>();
         int rc = enqueue(ctx, *s, (int)evs.size(), evs.data(), &g, batch.front().bz);
         const auto t1 = std::chrono::steady_clock::now();
-        if (rc == TPC_OK) rc = collect(ctx, *s);
+        if (rc == TPC_OK) rc = collect_to_tickets(ctx, *s, done);
         const auto t2 = std::chrono::steady_clock::now();
-        // copy each event's tracks into its own buffers outside the lock
-        std::vector<std::unique_ptr<TicketResult>> done(batch.size());
-        for (size_t i = 0; i < batch.size(); ++i) {
-            auto R = std::make_unique<TicketResult>();
-            if (rc == TPC_OK) {
-                const tpc_tracks& T = s->tracks[i];
-                const size_t n = (size_t)T.n_tracks;
-                const size_t nh = n ? (size_t)T.hit_off[n] : 0;
-                R->sector.assign(T.sector, T.sector + n);
-                R->x.assign(T.x, T.x + n);
-                R->param.assign(T.param, T.param + 5 * n);
-                R->cov.assign(T.cov, T.cov + 15 * n);
-                R->chi2.assign(T.chi2, T.chi2 + n);
-                R->ndf.assign(T.ndf, T.ndf + n);
-                R->hit_off.assign(T.hit_off, T.hit_off + n + 1);
-                R->hit_cid.assign(T.hit_cid, T.hit_cid + nh);
-                R->view.n_tracks = (int64_t)n;
-                R->view.sector = R->sector.data();
-                R->view.x = R->x.data();
-                R->view.param = R->param.data();
-                R->view.cov = R->cov.data();
-                R->view.chi2 = R->chi2.data();
-                R->view.ndf = R->ndf.data();
-                R->view.hit_off = R->hit_off.data();
-                R->view.hit_cid = R->hit_cid.data();
+        for (auto& d : done) {
+            d->status = rc;
+            if (rc != TPC_OK) {  // no partial result: buffers back to the pool
+                pool_put(ctx, d->buf);
+                d->buf = PinnedBuf{};
+                d->view = tpc_tracks{};
             }
-            R->status = rc;
-            done[i] = std::move(R);
         }
         // fill the tickets' own result objects in place (pollers hold pointers
         // to them); the swapped-out placeholders are freed outside the lock
@@ -766,6 +864,7 @@ void worker(tpc_track_ctx* ctx, Slot* s)
         }
         ctx->cv_done.notify_all();
         lk.unlock();
+        for (auto& d : done) pool_put(ctx, d->buf);  // tickets released meanwhile
         done.clear();
     }
 }
@@ -951,6 +1050,7 @@ int tpc_track_release(tpc_track_ctx* ctx, uint64_t ticket)
     if (it->second->status == TPC_EBUSY) return fail(ctx, TPC_EBUSY, "ticket still in flight");
     gone = std::move(it->second);
     ctx->results.erase(it);
+    pool_put(ctx, gone->buf);
     return TPC_OK;
 }
 
@@ -1026,6 +1126,9 @@ void tpc_track_destroy(tpc_track_ctx* ctx)
     for (auto& t : ctx->workers) t.join();
     cudaSetDevice(ctx->cfg.device);
     for (auto& s : ctx->slots) free_slot(*s);
+    for (auto& r : ctx->results)
+        if (r.second->buf.p) cudaFreeHost(r.second->buf.p);
+    for (auto& b : ctx->pool) cudaFreeHost(b.p);
     delete ctx;
 }
 

@@ -182,13 +182,16 @@ class Tracks:
         return self.hit_cid[self.hit_off[j]:self.hit_off[j + 1]]
 
 
-def tracks_to_numpy(t: tpc_tracks) -> Tracks:
+def tracks_to_numpy(t: tpc_tracks, copy: bool = True) -> Tracks:
+    """numpy arrays of a result; copy=False gives views of the library's
+    buffers, valid until the buffers are released or reused."""
     n = int(t.n_tracks)
 
     def arr(p, count, dt):
         if count == 0 or not p:
             return np.zeros(count, dtype=dt)
-        return np.ctypeslib.as_array(p, shape=(count,)).astype(dt, copy=True)
+        a = np.ctypeslib.as_array(p, shape=(count,))
+        return a.astype(dt, copy=True) if copy else a
     hit_off = arr(t.hit_off, n + 1, np.int32) if n else np.zeros(1, np.int32)
     nh = int(hit_off[-1]) if n else 0
     return Tracks(sector=arr(t.sector, n, np.int32), x=arr(t.x, n, np.float32),
@@ -234,17 +237,21 @@ def tpc_track_create(max_clusters_per_event: int, *, device: int = 0, mem_budget
     return ctx
 
 
-def tpc_track_event(ctx, clusters: tpc_clusters, geom: tpc_geometry, bz: float) -> Tracks:
+def tpc_track_event(ctx, clusters: tpc_clusters, geom: tpc_geometry, bz: float, *,
+                    copy: bool = True) -> Tracks:
+    """Track one event; copy=False returns views of the context's buffers,
+    valid until its next call."""
     out = tpc_tracks()
     _check(ctx, lib().tpc_track_event(ctx, C.byref(clusters), C.byref(geom), bz, C.byref(out)))
-    return tracks_to_numpy(out)
+    return tracks_to_numpy(out, copy)
 
 
-def tpc_track_batch(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz: float) -> list[Tracks]:
+def tpc_track_batch(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz: float, *,
+                    copy: bool = True) -> list[Tracks]:
     arr = (tpc_clusters * len(clusters))(*clusters)
     outs = (tpc_tracks * len(clusters))()
     _check(ctx, lib().tpc_track_batch(ctx, len(clusters), arr, C.byref(geom), bz, outs))
-    return [tracks_to_numpy(o) for o in outs]
+    return [tracks_to_numpy(o, copy) for o in outs]
 
 
 def tpc_track_launch(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz: float):
@@ -265,13 +272,15 @@ def tpc_track_submit(ctx, clusters: tpc_clusters, geom: tpc_geometry, bz: float)
     return t.value
 
 
-def tpc_track_poll(ctx, ticket: int, timeout_us: int = -1) -> Tracks | None:
+def tpc_track_poll(ctx, ticket: int, timeout_us: int = -1, *, copy: bool = True) -> Tracks | None:
+    """Tracks of a finished ticket (None while it runs); copy=False returns
+    views of the ticket's buffers, valid until tpc_track_release."""
     out = tpc_tracks()
     rc = lib().tpc_track_poll(ctx, ticket, timeout_us, C.byref(out))
     if rc == TPC_EBUSY:
         return None
     _check(ctx, rc)
-    return tracks_to_numpy(out)
+    return tracks_to_numpy(out, copy)
 
 
 def tpc_track_release(ctx, ticket: int):
