@@ -331,20 +331,25 @@ size_t rowsort_smem_bytes()
            3 * sizeof(int16_t) * kMaxRowHits;
 }
 
-void launch_binning(const Launch& L, void* stream_, const KernelHook* hook)
+void prepare_binning()
+{
+    cudaFuncSetAttribute(k_rowsort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rowsort_smem_bytes());
+}
+
+void launch_binning(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
-    const int blocks = 148 * 4;
+    const int blocks = S.n_sm * S.bin_blocks_per_sm;
     k_count<<<blocks, 256, 0, stream>>>(L);
     hook_after(hook, "k_count");
     k_rowscan<<<L.n_row_tiles, kScanThreads, 0, stream>>>(L);
     hook_after(hook, "k_rowscan");
     k_scatter<<<blocks, 256, 0, stream>>>(L);
     hook_after(hook, "k_scatter");
-    const size_t sm = rowsort_smem_bytes();
-    cudaFuncSetAttribute(k_rowsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const int rows_blocks = L.RS < 148 * 16 ? L.RS : 148 * 16;
-    k_rowsort<<<rows_blocks > 0 ? rows_blocks : 1, kSortThreads, sm, stream>>>(L);
+    const int rows_blocks = L.RS < S.n_sm * 16 ? L.RS : S.n_sm * 16;
+    const int threads = S.sort_threads == 256 ? 256 : kSortThreads;
+    k_rowsort<<<rows_blocks > 0 ? rows_blocks : 1, threads, rowsort_smem_bytes(), stream>>>(L);
     hook_after(hook, "k_rowsort");
 }
 

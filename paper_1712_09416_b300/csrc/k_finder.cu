@@ -23,7 +23,7 @@ namespace tpc {
 
 namespace {
 
-constexpr int kNbThreads = 128;
+constexpr int kNbThreads = 256;  // largest block; the schedule picks 64, 128 or 256
 
 struct RowView {      // one adjacent row
     const float2* yz;
@@ -333,13 +333,14 @@ __global__ void __launch_bounds__(kCsThreads) k_clean_starts(Launch L)
 
 }  // namespace
 
-void launch_finder(const Launch& L, void* stream_, const KernelHook* hook)
+void launch_finder(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
-    long long nb = (L.n_total + kNbThreads - 1) / kNbThreads;
-    if (nb > 148 * 64) nb = 148 * 64;
+    const int th = (S.nb_threads == 64 || S.nb_threads == 256) ? S.nb_threads : 128;
+    long long nb = (L.n_total + th - 1) / th;
+    if (nb > (long long)S.n_sm * 64) nb = (long long)S.n_sm * 64;
     if (nb < 1) nb = 1;
-    k_neighbours<<<(int)nb, kNbThreads, 0, stream>>>(L);
+    k_neighbours<<<(int)nb, th, 0, stream>>>(L);
     hook_after(hook, "k_neighbours");
     k_clean_starts<<<L.n_hit_tiles, kCsThreads, 0, stream>>>(L);
     hook_after(hook, "k_clean_starts");

@@ -243,17 +243,22 @@ __global__ void k_sel_write(Launch L)
 
 }  // namespace
 
-void launch_selector(const Launch& L, void* stream_, const KernelHook* hook)
+constexpr size_t kSelSortSmem = kMaxSectorTracks * (sizeof(unsigned long long) + sizeof(int));
+
+void prepare_selector()
+{
+    cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSelSortSmem);
+}
+
+void launch_selector(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
     int blocks = (L.t_cap + 7) / 8;  // one warp per tracklet, 8 warps per block
-    if (blocks > 148 * 16) blocks = 148 * 16;
+    if (blocks > S.n_sm * 16) blocks = S.n_sm * 16;
     if (blocks < 1) blocks = 1;
     k_sel_decide<<<blocks, 256, 0, stream>>>(L);
     hook_after(hook, "k_sel_decide");
-    const size_t sm = kMaxSectorTracks * (sizeof(unsigned long long) + sizeof(int));
-    cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_sel_sort<<<L.S, kSortThreads, sm, stream>>>(L);
+    k_sel_sort<<<L.S, kSortThreads, kSelSortSmem, stream>>>(L);
     hook_after(hook, "k_sel_sort");
     k_sel_write<<<blocks, 256, 0, stream>>>(L);
     hook_after(hook, "k_sel_write");

@@ -576,19 +576,21 @@ __global__ void k_weights(Launch L)
 
 }  // namespace
 
-void launch_constructor(const Launch& L, void* stream_, const KernelHook* hook)
+int constructor_occupancy()
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_constructor, kTlThreads, 0);
+    return per_sm < 1 ? 1 : per_sm;
+}
+
+void launch_constructor(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
-    const size_t sm = 0;
-    // persistent: as many blocks as fit on the GPU at once
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_constructor, kTlThreads, sm);
-        if (per_sm < 1) per_sm = 1;
-    }
-    int dev = 0, n_sm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int n_sm = S.n_sm;
+    // persistent: up to as many blocks as fit on the GPU at once
+    int per_sm = S.tl_blocks_per_sm;
+    if (per_sm < 1 || (S.tl_max_per_sm > 0 && per_sm > S.tl_max_per_sm)) per_sm = S.tl_max_per_sm;
+    if (per_sm < 1) per_sm = 1;
     {
         long long cb = ((long long)L.t_cap + kChThreads - 1) / kChThreads;
         if (cb > (long long)n_sm * 8) cb = (long long)n_sm * 8;
@@ -600,7 +602,7 @@ void launch_constructor(const Launch& L, void* stream_, const KernelHook* hook)
     const int need = (L.t_cap + kTlThreads - 1) / kTlThreads;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    k_constructor<<<blocks, kTlThreads, sm, stream>>>(L);
+    k_constructor<<<blocks, kTlThreads, 0, stream>>>(L);
     hook_after(hook, "k_constructor");
     int wblocks = (L.t_cap + 7) / 8;
     if (wblocks > n_sm * 16) wblocks = n_sm * 16;

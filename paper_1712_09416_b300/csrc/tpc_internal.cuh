@@ -227,10 +227,29 @@ inline void hook_after(const KernelHook* h, const char* name)
     if (h && h->after) h->after(h->user, name);
 }
 
+// Launch schedule of the kernels on one device: grid and block shapes that
+// do not change the results, only the speed (the autotuner picks them).
+struct Schedule {
+    int n_sm = 148;            // multiprocessors of the device
+    int bin_blocks_per_sm = 4; // k_count / k_scatter grid
+    int sort_threads = 512;    // k_rowsort block (256 or 512)
+    int nb_threads = 128;      // k_neighbours block (64, 128 or 256)
+    int tl_blocks_per_sm = 0;  // persistent k_constructor blocks per SM (<= tl_max_per_sm)
+    int tl_max_per_sm = 0;     // occupancy limit of k_constructor
+};
+
+// Once per device (current device): kernel attributes and the default
+// schedule.  Launchers make no other runtime calls than kernel launches, so
+// a launch sequence can be captured into a CUDA graph.
+void prepare_kernels(Schedule* s);
+void prepare_binning();
+void prepare_selector();
+int constructor_occupancy();
+
 // host-side launchers (one translation unit each)
-void launch_binning(const Launch& L, void* stream, const KernelHook* hook);
-void launch_finder(const Launch& L, void* stream, const KernelHook* hook);
-void launch_constructor(const Launch& L, void* stream, const KernelHook* hook);
-void launch_selector(const Launch& L, void* stream, const KernelHook* hook);
+void launch_binning(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
+void launch_finder(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
+void launch_constructor(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
+void launch_selector(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
 
 }  // namespace tpc

@@ -52,6 +52,7 @@ static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
 
 std::mutex g_na_mu;
 void* g_na_ptr[kNaMaxDevices] = {nullptr};
+Schedule g_na_sched[kNaMaxDevices];
 
 // Links of every sorted hit as input cluster ids (or -1).
 __global__ void k_links_by_cid(Launch L, int32_t* up_cid, int32_t* dn_cid)
@@ -100,10 +101,12 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
                 cudaGetLastError();
                 return TPC_ECUDA;
             }
+            prepare_kernels(&g_na_sched[dev]);
             g_na_ptr[dev] = p;
         }
         base = (unsigned char*)g_na_ptr[dev];
     }
+    const Schedule& sched = g_na_sched[dev];
     size_t off = 0;
     auto take = [&](size_t bytes) {
         unsigned char* p = base + off;
@@ -190,8 +193,8 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
     if (off > kNaBytes) return TPC_EINVAL;  // layout and size disagree (cannot happen)
     if (cudaMemcpyAsync(desc, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return TPC_ECUDA;
-    launch_binning(L, st, nullptr);
-    launch_finder(L, st, nullptr);
+    launch_binning(L, sched, st, nullptr);
+    launch_finder(L, sched, st, nullptr);
     const int blocks = (int)((n + 255) / 256) > 0 ? (int)((n + 255) / 256) : 1;
     k_links_by_cid<<<blocks < 1184 ? blocks : 1184, 256, 0, st>>>(L, up_cid, dn_cid);
     if (cudaGetLastError() != cudaSuccess) return TPC_ECUDA;

@@ -122,6 +122,10 @@ struct Slot {
     cudaEvent_t done_ev = nullptr;
     LaunchInfo info;
     std::vector<tpc_tracks> tracks;  // per event of the last results
+    // the kernel sequence of the last launch shape, captured as a CUDA graph
+    cudaGraphExec_t graph = nullptr;
+    Launch graph_L{};
+    Schedule graph_sched{};
 };
 
 struct Request {
@@ -166,6 +170,8 @@ struct tpc_track_ctx {
     uint64_t next_ticket = 1;
     std::atomic<int> direct_busy{0};
     bool trace = false;  // TPC_TRACE=1: one stderr line per served launch
+    bool graphs = true;  // TPC_NO_GRAPH=1: launch the kernels one by one
+    tpc::Schedule sched;
 };
 
 namespace tpc {
@@ -305,6 +311,7 @@ void free_slot(Slot& s)
     for (void* p : hp)
         if (p) cudaFreeHost(p);
     if (s.done_ev) cudaEventDestroy(s.done_ev);
+    if (s.graph) cudaGraphExecDestroy(s.graph);
     if (s.own_stream && s.stream) cudaStreamDestroy(s.stream);
     s = Slot();
 }
@@ -336,6 +343,58 @@ size_t prof_event(Slot& s)
     }
     cudaEventRecord(s.prof_pool[s.prof_used], s.stream);
     return s.prof_used++;
+}
+
+void launch_all(const Launch& L, const Schedule& S, cudaStream_t st, const KernelHook* hk)
+{
+    launch_binning(L, S, st, hk);
+    launch_finder(L, S, st, hk);
+    launch_constructor(L, S, st, hk);
+    launch_selector(L, S, st, hk);
+}
+
+// The kernel sequence as one CUDA graph launch.  The graph of the slot is
+// captured again only when the launch record or the schedule changed (a new
+// event shape), and then updated in place when its topology allows.
+int launch_graph(tpc_track_ctx* ctx, Slot& s, const Launch& L)
+{
+    const bool same = s.graph && std::memcmp(&s.graph_L, &L, sizeof(Launch)) == 0 &&
+                      std::memcmp(&s.graph_sched, &ctx->sched, sizeof(Schedule)) == 0;
+    if (!same) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();  // stream cannot be captured: launch directly
+            launch_all(L, ctx->sched, s.stream, nullptr);
+            return TPC_OK;
+        }
+        launch_all(L, ctx->sched, s.stream, nullptr);
+        if (cudaStreamEndCapture(s.stream, &g) != cudaSuccess || !g) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            return fail(ctx, TPC_ECUDA, "graph capture of the kernel sequence failed");
+        }
+        bool ok = false;
+        if (s.graph) {
+            cudaGraphExecUpdateResultInfo info;
+            ok = cudaGraphExecUpdate(s.graph, g, &info) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(s.graph);
+                s.graph = nullptr;
+            }
+        }
+        if (!ok && cudaGraphInstantiate(&s.graph, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            s.graph = nullptr;
+            cudaGraphDestroy(g);
+            return fail(ctx, TPC_ECUDA, "graph instantiation failed");
+        }
+        cudaGraphDestroy(g);
+        s.graph_L = L;
+        s.graph_sched = ctx->sched;
+    }
+    CUDA_TRY(ctx, cudaGraphLaunch(s.graph, s.stream));
+    return TPC_OK;
 }
 
 // Enqueue the whole device pipeline of one launch on the slot's stream.
@@ -516,10 +575,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
         s.prof_last = prof_event(s);
     }
     const KernelHook* hk = s.prof ? &hook : nullptr;
-    launch_binning(L, s.stream, hk);
-    launch_finder(L, s.stream, hk);
-    launch_constructor(L, s.stream, hk);
-    launch_selector(L, s.stream, hk);
+    if (s.prof || !ctx->graphs) launch_all(L, ctx->sched, s.stream, hk);
+    else if (int rc = launch_graph(ctx, s, L)) return rc;
     CUDA_TRY(ctx, cudaGetLastError());
     CUDA_TRY(ctx, cudaMemcpyAsync(s.cnt_host, L.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s.stream));
     CUDA_TRY(ctx, cudaEventRecord(s.done_ev, s.stream));
@@ -527,7 +584,6 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     return TPC_OK;
 }
 
-// Wait for the slot's launch, check the device status, copy the results.
 // Wait for the slot's launch and turn its device status into a code.
 int launch_status(tpc_track_ctx* ctx, Slot& s)
 {
@@ -566,6 +622,7 @@ void fill_counters(Slot& s)
     I.done = true;
 }
 
+// Wait for the slot's launch, check the device status, copy the results.
 int collect(tpc_track_ctx* ctx, Slot& s)
 {
     LaunchInfo& I = s.info;
@@ -609,6 +666,22 @@ int collect(tpc_track_ctx* ctx, Slot& s)
     fill_counters(s);
     return TPC_OK;
 }
+
+}  // namespace
+
+void prepare_kernels(Schedule* s)
+{
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n_sm > 0)
+        s->n_sm = n_sm;
+    prepare_binning();
+    prepare_selector();
+    s->tl_max_per_sm = constructor_occupancy();
+    s->tl_blocks_per_sm = s->tl_max_per_sm;
+}
+
+namespace {
 
 PinnedBuf pool_get(tpc_track_ctx* ctx, size_t need)
 {
@@ -916,10 +989,14 @@ int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out)
     ctx->cfg = *cfg;
     const char* tr = std::getenv("TPC_TRACE");
     ctx->trace = tr && tr[0] == '1';
+    const char* ng = std::getenv("TPC_NO_GRAPH");
+    ctx->graphs = !(ng && ng[0] == '1');
     if (cudaSetDevice(cfg->device) != cudaSuccess) {
         cudaGetLastError();
         return TPC_ECUDA;
     }
+    prepare_kernels(&ctx->sched);
+    if (cudaGetLastError() != cudaSuccess) return TPC_ECUDA;
     const int n_slots = cfg->max_events_in_flight;
     size_t total = 0;
     for (int i = 0; i < n_slots; ++i) {
