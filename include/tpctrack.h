@@ -198,6 +198,34 @@ typedef struct {
 int tpc_track_set_profiling(tpc_track_ctx* ctx, int on);
 int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, int* n);
 
+/* Launch schedule: grid and block shapes of the kernels.  It changes the
+ * speed only, never the results.  n_sm and tl_max_per_sm describe the device
+ * and the constructor's occupancy limit (read-only); the others are:
+ *   bin_blocks_per_sm  blocks per SM of the count and scatter kernels (1..32)
+ *   sort_threads       threads of a row-sort block (256 or 512)
+ *   nb_threads         threads of a neighbour-finder block (64, 128 or 256)
+ *   tl_blocks_per_sm   persistent constructor blocks per SM (1..tl_max_per_sm)
+ * tpc_track_set_schedule rejects other values with TPC_EINVAL and returns
+ * TPC_EBUSY while the context serves submitted events. */
+typedef struct {
+    int n_sm, tl_max_per_sm;
+    int bin_blocks_per_sm, sort_threads, nb_threads, tl_blocks_per_sm;
+} tpc_track_schedule;
+int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out);
+int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);
+
+/* Autotuner: runs the launch of n_ev events (arguments as for
+ * tpc_track_batch) with each candidate value of every schedule field, reps
+ * times each (1..50), times the kernel that the field shapes with CUDA
+ * events, and keeps the fastest value per field (fields shape different
+ * kernels, so they are tuned one after the other).  Writes the chosen
+ * schedule to *out (may be NULL) and makes it the context's schedule.  The
+ * results of the tuning launches are discarded.  Same errors as
+ * tpc_track_batch, TPC_EBUSY while serving submitted events. */
+int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
+                       const tpc_geometry* geom, float bz_tesla, int reps,
+                       tpc_track_schedule* out);
+
 /* Debug dump of an intermediate stage of event 0 of the last completed
  * launch, for parity tests.  Writes at most cap bytes to host_buf and the
  * size needed to *used (call with cap = 0 to query).  Stages:

@@ -1170,6 +1170,115 @@ int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, in
     return TPC_OK;
 }
 
+int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out)
+{
+    if (!ctx || !out) return TPC_EINVAL;
+    const Schedule& S = ctx->sched;
+    out->n_sm = S.n_sm;
+    out->tl_max_per_sm = S.tl_max_per_sm;
+    out->bin_blocks_per_sm = S.bin_blocks_per_sm;
+    out->sort_threads = S.sort_threads;
+    out->nb_threads = S.nb_threads;
+    out->tl_blocks_per_sm = S.tl_blocks_per_sm;
+    return TPC_OK;
+}
+
+int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* q)
+{
+    if (!ctx || !q) return TPC_EINVAL;
+    if (!ctx->workers.empty()) return fail(ctx, TPC_EBUSY, "context is serving submitted events");
+    const Schedule& S = ctx->sched;
+    if (q->bin_blocks_per_sm < 1 || q->bin_blocks_per_sm > 32 ||
+        (q->sort_threads != 256 && q->sort_threads != 512) ||
+        (q->nb_threads != 64 && q->nb_threads != 128 && q->nb_threads != 256) ||
+        q->tl_blocks_per_sm < 1 || q->tl_blocks_per_sm > S.tl_max_per_sm)
+        return fail(ctx, TPC_EINVAL, "schedule value out of range");
+    ctx->sched.bin_blocks_per_sm = q->bin_blocks_per_sm;
+    ctx->sched.sort_threads = q->sort_threads;
+    ctx->sched.nb_threads = q->nb_threads;
+    ctx->sched.tl_blocks_per_sm = q->tl_blocks_per_sm;
+    return TPC_OK;
+}
+
+int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
+                       const tpc_geometry* geom, float bz, int reps, tpc_track_schedule* out)
+{
+    if (!ctx) return TPC_EINVAL;
+    if (!ctx->workers.empty()) return fail(ctx, TPC_EBUSY, "context is serving submitted events");
+    if (reps < 1 || reps > 50) return fail(ctx, TPC_EINVAL, "reps out of range (1..50)");
+    cudaSetDevice(ctx->cfg.device);
+    Slot& s = *ctx->slots[0];
+    const Schedule start = ctx->sched;
+    // median over reps launches (after one warm-up) of the summed device time
+    // of the named kernels under schedule S
+    auto time_kernels = [&](const Schedule& S, const std::vector<std::string>& names,
+                            double* ms) -> int {
+        if (s.stream) CUDA_TRY(ctx, cudaStreamSynchronize(s.stream));
+        ctx->sched = S;
+        s.prof = true;
+        std::vector<double> t;
+        int rc = TPC_OK;
+        for (int r = 0; r <= reps && rc == TPC_OK; ++r) {
+            s.prof_used = 0;
+            s.prof_marks.clear();
+            s.info.pending = false;
+            rc = enqueue(ctx, s, n_ev, ev, geom, bz);
+            if (rc == TPC_OK) rc = launch_status(ctx, s);
+            if (rc != TPC_OK || r == 0) continue;
+            double sum = 0.0;
+            for (auto& m : s.prof_marks) {
+                bool want = false;
+                for (auto& nm : names) want = want || m.first == nm;
+                if (!want) continue;
+                float x = 0.0f;
+                if (cudaEventElapsedTime(&x, s.prof_pool[m.second.first], s.prof_pool[m.second.second]) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = fail(ctx, TPC_ECUDA, "autotune timing event");
+                }
+                sum += x;
+            }
+            t.push_back(sum);
+        }
+        s.prof = false;
+        s.prof_used = 0;
+        s.prof_marks.clear();
+        ctx->sched = start;
+        if (rc != TPC_OK) return rc;
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return TPC_OK;
+    };
+    Schedule best = start;
+    auto tune = [&](int Schedule::*field, std::vector<int> cands, std::vector<std::string> names) -> int {
+        double best_ms = 1e30;
+        int best_v = best.*field;
+        for (int v : cands) {
+            Schedule S = best;
+            S.*field = v;
+            double ms = 0.0;
+            if (int rc = time_kernels(S, names, &ms)) return rc;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_v = v;
+            }
+        }
+        best.*field = best_v;
+        return TPC_OK;
+    };
+    const int mx = start.tl_max_per_sm;
+    std::vector<int> tl = {mx};
+    for (int v : {mx * 3 / 4, mx / 2})
+        if (v >= 1 && std::find(tl.begin(), tl.end(), v) == tl.end()) tl.push_back(v);
+    int rc = tune(&Schedule::tl_blocks_per_sm, tl, {"k_constructor"});
+    if (!rc) rc = tune(&Schedule::nb_threads, {64, 128, 256}, {"k_neighbours"});
+    if (!rc) rc = tune(&Schedule::sort_threads, {256, 512}, {"k_rowsort"});
+    if (!rc) rc = tune(&Schedule::bin_blocks_per_sm, {2, 4, 8, 16}, {"k_count", "k_scatter"});
+    if (rc) return rc;
+    ctx->sched = best;
+    s.info.done = false;  // the tuning launches' results are not offered
+    return out ? tpc_track_get_schedule(ctx, out) : TPC_OK;
+}
+
 int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c)
 {
     if (!ctx || !c) return TPC_EINVAL;

@@ -24,6 +24,7 @@ EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "
             "tpc_track_launch", "tpc_track_results", "tpc_track_submit", "tpc_track_poll",
             "tpc_track_release", "tpc_track_get_counters", "tpc_track_stream",
             "tpc_track_set_profiling", "tpc_track_kernel_times",
+            "tpc_track_get_schedule", "tpc_track_set_schedule", "tpc_track_autotune",
             "tpc_track_debug_dump", "tpc_track_last_error", "tpc_track_destroy",
             "tpc_track_links_noalloc"]
 
@@ -78,6 +79,11 @@ class tpc_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("total_ms", C.c_double), ("launches", C.c_int64)]
 
 
+class tpc_track_schedule(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("n_sm", "tl_max_per_sm", "bin_blocks_per_sm",
+                                       "sort_threads", "nb_threads", "tl_blocks_per_sm")]
+
+
 class tpc_dump_tracklet(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("start_cid", "sector", "valid", "nhits", "first_row",
                                          "last_row", "ndf", "pad")] + \
@@ -114,6 +120,11 @@ def lib():
         L.tpc_track_set_profiling.argtypes = [P, C.c_int]
         L.tpc_track_kernel_times.argtypes = [P, C.POINTER(tpc_kernel_time), C.c_int,
                                              C.POINTER(C.c_int)]
+        L.tpc_track_get_schedule.argtypes = [P, C.POINTER(tpc_track_schedule)]
+        L.tpc_track_set_schedule.argtypes = [P, C.POINTER(tpc_track_schedule)]
+        L.tpc_track_autotune.argtypes = [P, C.c_int, C.POINTER(tpc_clusters),
+                                         C.POINTER(tpc_geometry), C.c_float, C.c_int,
+                                         C.POINTER(tpc_track_schedule)]
         L.tpc_track_debug_dump.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_size_t)]
         L.tpc_track_last_error.argtypes = [P]
         L.tpc_track_last_error.restype = C.c_char_p
@@ -307,6 +318,34 @@ def tpc_track_kernel_times(ctx) -> dict:
     n = C.c_int()
     _check(ctx, lib().tpc_track_kernel_times(ctx, arr, 64, C.byref(n)))
     return {arr[i].name.decode(): (arr[i].total_ms, int(arr[i].launches)) for i in range(n.value)}
+
+
+def _schedule_dict(s: tpc_track_schedule) -> dict:
+    return {k: int(getattr(s, k)) for k, _ in s._fields_}
+
+
+def tpc_track_get_schedule(ctx) -> dict:
+    s = tpc_track_schedule()
+    _check(ctx, lib().tpc_track_get_schedule(ctx, C.byref(s)))
+    return _schedule_dict(s)
+
+
+def tpc_track_set_schedule(ctx, **fields):
+    """Change schedule fields by name (the others keep their values)."""
+    s = tpc_track_schedule()
+    _check(ctx, lib().tpc_track_get_schedule(ctx, C.byref(s)))
+    for k, v in fields.items():
+        setattr(s, k, int(v))
+    _check(ctx, lib().tpc_track_set_schedule(ctx, C.byref(s)))
+
+
+def tpc_track_autotune(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz: float,
+                       reps: int = 3) -> dict:
+    arr = (tpc_clusters * len(clusters))(*clusters)
+    s = tpc_track_schedule()
+    _check(ctx, lib().tpc_track_autotune(ctx, len(clusters), arr, C.byref(geom), bz, reps,
+                                         C.byref(s)))
+    return _schedule_dict(s)
 
 
 def tpc_track_debug_dump(ctx, stage: int) -> bytes:

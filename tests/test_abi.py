@@ -60,11 +60,35 @@ def test_create_rejects_bad_config_before_touching_the_device(lib):
     assert lib.tpc_track_create(None, ctypes.byref(ctx)) == tpctrack.TPC_EINVAL
 
 
-def test_struct_sizes_match_the_header(lib):
+def test_struct_layouts_match_the_header(lib, tmp_path):
+    """Every record of tpctrack.h, compiled by gcc: its size and the offset of
+    each field equal those of the ctypes mirror in the binding."""
+    import shutil
+    import subprocess
     from paper_1712_09416_b300 import tpctrack
-    # sizes on x86-64 of the records in tpctrack.h
-    assert ctypes.sizeof(tpctrack.tpc_clusters) == 48
-    assert ctypes.sizeof(tpctrack.tpc_tracks) == 72
-    assert ctypes.sizeof(tpctrack.tpc_geometry) == 32
-    assert ctypes.sizeof(tpctrack.tpc_track_params) == 60
-    assert ctypes.sizeof(tpctrack.tpc_dump_tracklet) == 32 + 4 * 22
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    recs = [tpctrack.tpc_geometry, tpctrack.tpc_clusters, tpctrack.tpc_tracks,
+            tpctrack.tpc_track_params, tpctrack.tpc_track_config, tpctrack.tpc_track_counters,
+            tpctrack.tpc_kernel_time, tpctrack.tpc_track_schedule, tpctrack.tpc_dump_tracklet]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tpctrack.h"', 'int main(void) {']
+    for r in recs:
+        n = r.__name__
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in r._fields_:
+            lines.append(f'printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, "-o", str(exe), str(src)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        rec, key, val = ln.split()
+        got[(rec, key)] = int(val)
+    for r in recs:
+        n = r.__name__
+        assert got[(n, "size")] == ctypes.sizeof(r), n
+        for f, _ in r._fields_:
+            assert got[(n, f)] == getattr(r, f).offset, (n, f)

@@ -160,6 +160,40 @@ def test_graph_replay_equals_direct_launches(tp, monkeypatch):
         graph.close()
 
 
+def test_schedule_changes_speed_not_results(tp):
+    """Every schedule value (grid and block shapes) gives the same tracks;
+    out-of-range values are rejected; the autotuner returns a valid schedule
+    and leaves the results unchanged."""
+    evs = synth.batch_events(n_events=2, seed0=4200)
+    with tp.Tracker(2_000_000, max_events_per_launch=2) as t:
+        ref = t.batch(evs)
+        s0 = tp.tpc_track_get_schedule(t.ctx)
+        assert s0["tl_blocks_per_sm"] == s0["tl_max_per_sm"] >= 1 and s0["n_sm"] >= 1
+        variants = [dict(nb_threads=64), dict(nb_threads=256), dict(sort_threads=256),
+                    dict(bin_blocks_per_sm=1), dict(bin_blocks_per_sm=16),
+                    dict(tl_blocks_per_sm=1), dict(tl_blocks_per_sm=max(1, s0["tl_max_per_sm"] // 2))]
+        for v in variants:
+            tp.tpc_track_set_schedule(t.ctx, **{**s0, **v})
+            got = t.batch(evs)
+            for a, b in zip(ref, got):
+                for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+                    assert np.array_equal(getattr(a, f), getattr(b, f)), (v, f)
+        for bad in (dict(nb_threads=96), dict(sort_threads=128), dict(bin_blocks_per_sm=0),
+                    dict(tl_blocks_per_sm=s0["tl_max_per_sm"] + 1)):
+            with pytest.raises(tp.TpcError):
+                tp.tpc_track_set_schedule(t.ctx, **{**s0, **bad})
+        g, keep_x = tp.geometry_of(evs[0])
+        cs = [tp.clusters_of(e.y, e.z, e.row, e.sector) for e in evs]
+        tuned = tp.tpc_track_autotune(t.ctx, [c for c, _ in cs], g, float(evs[0].bz), reps=1)
+        assert tuned["nb_threads"] in (64, 128, 256) and tuned["sort_threads"] in (256, 512)
+        assert 1 <= tuned["tl_blocks_per_sm"] <= tuned["tl_max_per_sm"]
+        assert tp.tpc_track_get_schedule(t.ctx) == tuned
+        got = t.batch(evs)
+        for a, b in zip(ref, got):
+            for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+                assert np.array_equal(getattr(a, f), getattr(b, f)), ("tuned", f)
+
+
 def test_batch_equals_single_events(tp, trk):
     evs = synth.batch_events(n_events=6)
     alone = [trk.event(e) for e in evs]
