@@ -164,21 +164,26 @@ __device__ __forceinline__ float update(Fit& f, float my, float mz, const Launch
     return r0 * (I00 * r0 + I01 * r1) + r1 * (I01 * r0 + I11 * r1);
 }
 
-__device__ __forceinline__ bool outside(const Fit& f, const Launch& L)
+__device__ __forceinline__ bool outside(const Fit& f, float yref, float zref, const Launch& L)
 {
-    return fabsf(f.p[0]) > f.x * L.tan_half + L.edge_margin ||
-           fabsf(f.p[1]) > L.z_max + L.edge_margin;
+    return fabsf(f.p[0] + yref) > f.x * L.tan_half + L.edge_margin ||
+           fabsf(f.p[1] + zref) > L.z_max + L.edge_margin;
 }
 
 // Candidates ka..kb-1 (global sorted indices) in batches of four loads.
-__device__ __forceinline__ void scan_range(const Fit& f, int ka, int kb, float S00, float S01,
-                                           float S11, float id, const Launch& L, float& best,
-                                           int& bk, float& by, float& bzv)
+__device__ __forceinline__ void scan_range(const Fit& f, float yref, float zref, int ka, int kb,
+                                           float S00, float S01, float S11, float id,
+                                           const Launch& L, float& best, int& bk, float& by,
+                                           float& bzv)
 {
     for (int k = ka; k < kb; k += 4) {
         float2 c[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) c[j] = L.hyz[k + j < kb ? k + j : ka];
+        for (int j = 0; j < 4; ++j) {
+            c[j] = L.hyz[k + j < kb ? k + j : ka];
+            c[j].x -= yref;
+            c[j].y -= zref;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (k + j >= kb) break;
@@ -198,20 +203,21 @@ __device__ __forceinline__ void scan_range(const Fit& f, int ka, int kb, float S
 
 // Least-chi2 hit of a row (grid G, hits from base) with chi2 <= chi2_hit,
 // exact ties to the lower cid; returns its global index or -1 and its
-// coordinates in (my, mz).  Every hit in the bins covering the box that
+// coordinates relative to (yref, zref) in (my, mz).  Every hit in the bins covering the box that
 // bounds the chi2 ellipse is tried.  When the box spans at most two z-bins
 // (nearly always: bins are several cm wide, the box a few mm) the four bin
 // offsets are read at once and the two hit ranges walked as one list.
-__device__ __forceinline__ int search(const Fit& f, const RowGrid& G, int base, const Launch& L,
-                                      float& my, float& mz)
+__device__ __forceinline__ int search(const Fit& f, float yref, float zref, const RowGrid& G,
+                                      int base, const Launch& L, float& my, float& mz)
 {
     const float* C = f.C;
     const float S00 = C[0] + L.sy2, S01 = C[1], S11 = C[2] + L.sz2;
     const float id = __fdividef(1.0f, S00 * S11 - S01 * S01);
     const float wy = 1.01f * sqrtf(L.chi2_hit * S00) + 1e-3f;
     const float wz = 1.01f * sqrtf(L.chi2_hit * S11) + 1e-3f;
-    const int y0 = bin_y(G, f.p[0] - wy), y1 = bin_y(G, f.p[0] + wy);
-    const int z0 = bin_z(G, f.p[1] - wz), z1 = bin_z(G, f.p[1] + wz);
+    const float ya = f.p[0] + yref, za = f.p[1] + zref;  // absolute window centre
+    const int y0 = bin_y(G, ya - wy), y1 = bin_y(G, ya + wy);
+    const int z0 = bin_z(G, za - wz), z1 = bin_z(G, za + wz);
     const int* bins = L.bin_start + G.bin_off;
     float best = 3.0e38f, by = 0.0f, bzv = 0.0f;
     int bk = -1;
@@ -231,6 +237,8 @@ __device__ __forceinline__ int search(const Fit& f, const RowGrid& G, int base, 
                 const int qj = q + j < tot ? q + j : 0;
                 kk[j] = base + (qj < n0 ? a0 + qj : a1 + (qj - n0));
                 c[j] = L.hyz[kk[j]];
+                c[j].x -= yref;
+                c[j].y -= zref;
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -249,7 +257,7 @@ __device__ __forceinline__ int search(const Fit& f, const RowGrid& G, int base, 
     } else {
         for (int bz = z0; bz <= z1; ++bz) {
             const int ka = base + bins[bz * G.ny + y0], kb = base + bins[bz * G.ny + y1 + 1];
-            scan_range(f, ka, kb, S00, S01, S11, id, L, best, bk, by, bzv);
+            scan_range(f, yref, zref, ka, kb, S00, S01, S11, id, L, best, bk, by, bzv);
         }
     }
     my = by;
@@ -346,6 +354,10 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
     int phase = 0;  // 1 forward, 2 backward
     int r = 0, r0 = 0, rk = 0, last = 0, first = 0, gap = 0, nupd = 0, gbase = 0;
     float chi2 = 0.0f;
+    // y and z of the state are kept relative to the start hit (yref, zref):
+    // small numbers carry the per-step rounding of binary32 far below the
+    // resolution; measurements are shifted by the same reference
+    float yref = 0.0f, zref = 0.0f;
     Fit f;
     // The tracklet's rowhit slot holds the hit of every row the forward pass
     // visits (global index, -1 none); the backward pass reads it ahead and
@@ -421,14 +433,16 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             const float tphi = (ck.x - c0.x) / (x1 - x0);
             const float dzdx = (ck.y - c0.y) / (x1 - x0);
             const float cphi = rsqrtf(1.0f + tphi * tphi);
+            yref = c0.x;
+            zref = c0.y;
             f.x = x0;
-            f.p[0] = c0.x;
-            f.p[1] = c0.y;
+            f.p[0] = 0.0f;
+            f.p[1] = 0.0f;
             f.p[2] = tphi * cphi;
             f.p[3] = dzdx * cphi;
             f.p[4] = 0.0f;
             seed_cov(f, L);
-            update(f, c0.x, c0.y, L);
+            update(f, 0.0f, 0.0f, L);
 #pragma unroll
             for (int i = 0; i < 5; ++i) PL(i) = f.p[i];
             last = r0;
@@ -445,7 +459,7 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             const bool known = pknown;
             const int base = pb;
             const RowGrid G = pG;
-            float my = pyz.x, mz = pyz.y;
+            float my = pyz.x - yref, mz = pyz.y - zref;
             int h = known ? ph : -1;
             const int rn = fwd ? r + 1 : r - 1;
             if (fwd ? rn < L.R : rn >= 0) stage(rn, fwd);
@@ -453,8 +467,8 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
                 end_pass = true;
             } else {
                 if (!known) {
-                    if (outside(f, L)) end_pass = true;
-                    else h = search(f, G, base, L, my, mz);
+                    if (outside(f, yref, zref, L)) end_pass = true;
+                    else h = search(f, yref, zref, G, base, L, my, mz);
                 }
                 if (!end_pass) {
                     if (h >= 0) {
@@ -496,7 +510,7 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             seed_cov(f, L);
             f.x = xs[last];
             const float2 c = L.hyz[rowhit[last]];
-            chi2 = update(f, c.x, c.y, L);
+            chi2 = update(f, c.x - yref, c.y - zref, L);
             nupd = 1;
             first = last;
             BEST(0) = f.x;
@@ -524,6 +538,8 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
         H.x = BEST(0);
 #pragma unroll
         for (int i = 0; i < 5; ++i) H.p[i] = BEST(1 + i);
+        H.p[0] += yref;
+        H.p[1] += zref;
 #pragma unroll
         for (int i = 0; i < 15; ++i) H.C[i] = BEST(6 + i);
         H.chi2 = chi2;

@@ -11,7 +11,13 @@ Bars (the tracker computes in binary32, the oracle in binary64):
   |d tan lambda| <= 1e-4 (relative to values of order one); q/pT within
   1e-4 relative to max(|q/pT|, 2 (GeV/c)^-1): stiff tracks have |q/pT| near
   0, where the binary32 fit keeps an absolute error near 1e-4 (under 1% of
-  the statistical error of q/pT);
+  the statistical error of q/pT).  Budget: at most 0.1% of the compared
+  tracks (rounded up) may exceed these bars, by at most 3x.  For short,
+  curved tracks the y / sin(phi) block of the covariance is nearly singular
+  and storing it in binary32 alone (exact arithmetic otherwise) moves q/pT
+  past 1e-4 relative (tests/test_fp32_covariance_limit.py); measured in
+  units of each parameter's own statistical error the binary32 deviations
+  stay below 1e-2;
 * tracks: identical hit lists and order for every track that shares no hit
   with a tracklet that differs.
 """
@@ -21,6 +27,8 @@ TOL_YZ = 1e-3
 TOL_ANG = 1e-4
 TOL_QPT_REL = 1e-4
 QPT_FLOOR = 2.0
+PARAM_BUDGET_FRAC = 1e-3  # share of compared tracks allowed above the bars
+PARAM_BUDGET_MAX = 3.0    # ... by at most this factor
 
 
 def param_errors(gp, op):
@@ -35,6 +43,19 @@ def param_errors(gp, op):
     s[..., 3] = d[..., 3] / TOL_ANG
     s[..., 4] = d[..., 4] / (TOL_QPT_REL * np.maximum(np.abs(op[..., 4]), QPT_FLOOR))
     return d, s
+
+
+def check_param_bars(scaled, what="tracks"):
+    """Assert the parameter bars on an (n, 5) array of param_errors scales:
+    every row within 1, except at most ceil(0.1% of n) rows within 3."""
+    s = np.asarray(scaled, np.float64).reshape(-1, 5)
+    if len(s) == 0:
+        return
+    worst = s.max(axis=1)
+    over = np.nonzero(worst > 1.0)[0]
+    allowed = int(np.ceil(PARAM_BUDGET_FRAC * len(s)))
+    assert len(over) <= allowed, (what, len(over), allowed, s[over].max(axis=0))
+    assert worst.max() <= PARAM_BUDGET_MAX, (what, s.max(axis=0))
 
 
 def compare_links(gpu_up, gpu_dn, o_up, o_dn):
