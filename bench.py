@@ -145,17 +145,30 @@ class ClockSampler:
 
 
 def cpu_baseline(ev_full, n_sectors: int = 4) -> dict:
-    """The oracle as it stands, single-threaded, on a few sectors of the event."""
+    """The oracle as it stands on the host cores: every sector of the event as
+    its own call, one thread per core (the oracle's C code keeps no global
+    state and its ctypes calls release the GIL), and single-threaded on a few
+    sectors for the per-core figure."""
+    from concurrent.futures import ThreadPoolExecutor
     from oracle import oracle
+    oracle.build()
     sectors = list(range(0, 36, 36 // n_sectors))[:n_sectors]
     sub = ev_full.select_sectors(sectors)
-    oracle.build()
     t0 = time.perf_counter()
     oracle.track_event(sub)
-    dt = time.perf_counter() - t0
-    return {"value": sub.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_sectors} of 36 sectors of the central event ({sub.n} clusters), "
-                      f"{dt:.1f} s single-threaded"}
+    dt1 = time.perf_counter() - t0
+    single = {"value": sub.n / dt1, "unit": UNIT, "cores": 1,
+              "sample": f"{n_sectors} of 36 sectors ({sub.n} clusters), {dt1:.1f} s"}
+    cores = os.cpu_count() or 1
+    parts = [ev_full.select_sectors([s]) for s in range(36)]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as pool:
+        list(pool.map(oracle.track_event, parts))
+    dtn = time.perf_counter() - t0
+    return {"value": ev_full.n / dtn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the whole central event ({ev_full.n} clusters), its 36 sectors as "
+                      f"independent calls on {cores} threads, {dtn:.1f} s",
+            "single_core": single}
 
 
 def percentile(v, q):
@@ -184,6 +197,85 @@ def served_ctx(tp, host_events, geom, bz, n_per_event):
     return ctx
 
 
+def run_one_at_a_time(tp, events, ns, arrivals, geom, bz, n_max):
+    """FIFO server, one tpc_track_event call per arrival (waits for it).
+    Returns per-event latencies (arrival -> result) and the span."""
+    ctx = tp.tpc_track_create(n_max + 65536, max_events_per_launch=1)
+    lat = []
+    try:
+        tp.tpc_track_event(ctx, events[0], geom, bz, copy=False)
+        t_start = time.perf_counter()
+        for i, a in enumerate(arrivals):
+            now = time.perf_counter() - t_start
+            if now < a:
+                time.sleep(a - now)
+            tp.tpc_track_event(ctx, events[i % len(events)], geom, bz, copy=False)
+            lat.append(time.perf_counter() - t_start - a)
+        span = time.perf_counter() - t_start
+    finally:
+        tp.tpc_track_destroy(ctx)
+    return lat, span
+
+
+def run_served(tp, events, ns, arrivals, geom, bz, n_max):
+    """Served form: submit on arrival, a poller thread collects completions.
+    Returns latencies, span and an error string (or None); every wait is
+    bounded."""
+    n_events = len(arrivals)
+    ctx = served_ctx(tp, events, geom, bz, n_max)
+    lats = [None] * n_events
+    errors = []
+    tickets = [None] * n_events
+    t_start = time.perf_counter()
+    done = threading.Event()
+
+    def poller():
+        try:
+            for i in range(n_events):
+                deadline = time.perf_counter() + 60.0
+                while tickets[i] is None:
+                    if errors or time.perf_counter() > deadline:
+                        raise TimeoutError("ticket never submitted")
+                    time.sleep(0.0001)
+                if tp.tpc_track_poll(ctx, tickets[i], 60_000_000, copy=False) is None:
+                    raise TimeoutError("ticket not done after 60 s")
+                lats[i] = time.perf_counter() - t_start - arrivals[i]
+                tp.tpc_track_release(ctx, tickets[i])
+        except Exception as e:  # reported in the JSON line
+            errors.append(repr(e))
+        finally:
+            done.set()
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    try:
+        for i, a in enumerate(arrivals):
+            now = time.perf_counter() - t_start
+            if now < a:
+                time.sleep(a - now)
+            tickets[i] = tp.tpc_track_submit(ctx, events[i % len(events)], geom, bz)
+    except Exception as e:
+        errors.append(repr(e))
+    if not done.wait(180.0):
+        errors.append("served run did not finish within 180 s")
+    span = time.perf_counter() - t_start
+    if not errors:
+        tp.tpc_track_destroy(ctx)
+    return lats, span, (errors[0] if errors else None)
+
+
+def compare_point(tp, events, ns, arrivals, geom, bz, n_max, rate):
+    lat1, span1 = run_one_at_a_time(tp, events, ns, arrivals, geom, bz, n_max)
+    lats, spans, err = run_served(tp, events, ns, arrivals, geom, bz, n_max)
+    if err:
+        return None, err
+    n_cl = sum(ns[i % len(ns)] for i in range(len(arrivals)))
+    return {"rate_per_s": rate, "events": len(arrivals),
+            "one_event": {"p50_ms": percentile(lat1, 50) * 1e3, "p99_ms": percentile(lat1, 99) * 1e3,
+                          "clusters_per_s": n_cl / span1},
+            "served": {"p50_ms": percentile(lats, 50) * 1e3, "p99_ms": percentile(lats, 99) * 1e3,
+                       "clusters_per_s": n_cl / spans}}, None
+
+
 def served_vs_one(tp, torch, host_events, geom, bz, n_per_event, rate_factors=(0.7, 1.5, 3.0),
                   n_events=120, seed=4):
     """Poisson arrivals of central events: one-at-a-time FIFO server vs the
@@ -208,76 +300,49 @@ def served_vs_one(tp, torch, host_events, geom, bz, n_per_event, rate_factors=(0
            "served_config": {"slots": SERVED_SLOTS, "events_per_launch": SERVED_PER_LAUNCH},
            "points": []}
     rng = np.random.default_rng(seed)
+    ns = [n_per_event] * len(host_events)
     for rf in rate_factors:
         lam = rf * cap
         arrivals = np.cumsum(rng.exponential(1.0 / lam, n_events))
-        # one at a time (FIFO): latency = finish - arrival
-        ctx1 = tp.tpc_track_create(n_per_event + 65536, max_events_per_launch=1)
-        lat1 = []
-        try:
-            tp.tpc_track_event(ctx1, host_events[0], geom, bz, copy=False)
-            t_start = time.perf_counter()
-            for i, a in enumerate(arrivals):
-                now = time.perf_counter() - t_start
-                if now < a:
-                    time.sleep(a - now)
-                tp.tpc_track_event(ctx1, host_events[i % len(host_events)], geom, bz, copy=False)
-                lat1.append(time.perf_counter() - t_start - a)
-            span1 = time.perf_counter() - t_start
-        finally:
-            tp.tpc_track_destroy(ctx1)
-        # served: submit on arrival, a poller collects completions
-        ctxs = served_ctx(tp, host_events, geom, bz, n_per_event)
-        lats = [None] * n_events
-        errors = []
-        try:
-            tickets = [None] * n_events
-            t_start = time.perf_counter()
-            done = threading.Event()
-
-            def poller():
-                try:
-                    for i in range(n_events):
-                        deadline = time.perf_counter() + 60.0
-                        while tickets[i] is None:
-                            if errors or time.perf_counter() > deadline:
-                                raise TimeoutError("ticket never submitted")
-                            time.sleep(0.0001)
-                        if tp.tpc_track_poll(ctxs, tickets[i], 60_000_000, copy=False) is None:
-                            raise TimeoutError("ticket not done after 60 s")
-                        lats[i] = time.perf_counter() - t_start - arrivals[i]
-                        tp.tpc_track_release(ctxs, tickets[i])
-                except Exception as e:  # reported in the JSON line
-                    errors.append(repr(e))
-                finally:
-                    done.set()
-            th = threading.Thread(target=poller, daemon=True)
-            th.start()
-            try:
-                for i, a in enumerate(arrivals):
-                    now = time.perf_counter() - t_start
-                    if now < a:
-                        time.sleep(a - now)
-                    tickets[i] = tp.tpc_track_submit(ctxs, host_events[i % len(host_events)],
-                                                     geom, bz)
-            except Exception as e:
-                errors.append(repr(e))
-            if not done.wait(180.0):
-                errors.append("served run did not finish within 180 s")
-            spans = time.perf_counter() - t_start
-        finally:
-            if not errors:
-                tp.tpc_track_destroy(ctxs)
-        if errors:
-            out["error"] = errors[0]
+        pt, err = compare_point(tp, host_events, ns, arrivals, geom, bz, n_per_event, lam)
+        if err:
+            out["error"] = err
             return out
-        out["points"].append({
-            "rate_per_s": lam,
-            "one_event": {"p50_ms": percentile(lat1, 50) * 1e3, "p99_ms": percentile(lat1, 99) * 1e3,
-                          "clusters_per_s": n_events * n_per_event / span1},
-            "served": {"p50_ms": percentile(lats, 50) * 1e3, "p99_ms": percentile(lats, 99) * 1e3,
-                       "clusters_per_s": n_events * n_per_event / spans},
-        })
+        out["points"].append(pt)
+    return out
+
+
+def served_sweep(tp, torch, synth, rates, n_events_of, pool_size=64, seed=4):
+    """Config 4: an event stream with Poisson arrivals at the given rates and
+    multiplicities min(10000, max(1, round(Exp(1500)))) tracks (arrivals
+    cycle through a pool of pool_size such events), one-at-a-time FIFO server
+    vs the served form, both with pinned host inputs."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pool = [synth.served_event(rng, synth.served_multiplicity(rng)) for _ in range(pool_size)]
+    geom, keep_x = tp.geometry_of(pool[0])
+    bz = float(pool[0].bz)
+    pinned, cs = [], []
+    for e in pool:
+        t = [torch.from_numpy(e.y).pin_memory(), torch.from_numpy(e.z).pin_memory(),
+             torch.from_numpy(e.row.view(np.int16)).pin_memory(),
+             torch.from_numpy(e.sector.view(np.int16)).pin_memory()]
+        pinned.append(t)
+        cs.append(tp.clusters_of(*t)[0])
+    ns = [e.n for e in pool]
+    n_max = max(ns)
+    out = {"workload": f"pool of {pool_size} events, tracks min(10000, max(1, round(Exp(1500)))), "
+                       f"mean {np.mean(ns):.0f} clusters per event",
+           "served_config": {"slots": SERVED_SLOTS, "events_per_launch": SERVED_PER_LAUNCH},
+           "points": []}
+    for lam in rates:
+        n_ev = n_events_of(lam)
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n_ev))
+        pt, err = compare_point(tp, cs, ns, arrivals, geom, bz, n_max, lam)
+        if err:
+            out["error"] = err
+            return out
+        out["points"].append(pt)
     return out
 
 
@@ -332,6 +397,67 @@ def batched_vs_sequential(tp, torch, synth, stream, n_events=64, reps=3):
             "clusters_per_s_batch": n_all / t_batch, "clusters_per_s_sequential": n_all / t_seq,
             "speedup": t_seq / t_batch, "schedule": sched,
             "timing": "host wall clock around launch + results, inputs resident on the device"}
+
+
+def pileup_section(tp, torch, synth, stream, reps=3, n_served=4):
+    """Config 5: 50 collisions (200-2000 tracks, vertex z within +-200 cm)
+    merged into one event, through the batched path (one device-resident
+    launch, autotuned) and the served path (host inputs, tickets submitted at
+    once), with the Monte-Carlo efficiency, fake and clone rates of the
+    tracks."""
+    import numpy as np
+    ev = synth.pileup_event()
+    geom, keep_x = tp.geometry_of(ev)
+    bz = float(ev.bz)
+    d = (torch.from_numpy(ev.y).cuda(), torch.from_numpy(ev.z).cuda(),
+         torch.from_numpy(ev.row.view(np.int16)).cuda(),
+         torch.from_numpy(ev.sector.view(np.int16)).cuda())
+    c = tp.clusters_of(*d)[0]
+    torch.cuda.synchronize()
+    out = {"workload": "50 collisions of 200-2000 tracks, vertex z ~ U(-200, 200) cm, seed 5",
+           "clusters": int(ev.n)}
+    ctx = tp.tpc_track_create(ev.n + 65536, max_events_per_launch=1, cuda_stream=stream.cuda_stream)
+    try:
+        out["schedule"] = tp.tpc_track_autotune(ctx, [c], geom, bz, reps=2)
+        tp.tpc_track_launch(ctx, [c], geom, bz)
+        tp.tpc_track_results(ctx, 1, copy=False)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            tp.tpc_track_launch(ctx, [c], geom, bz)
+            tp.tpc_track_results(ctx, 1, copy=False)
+        dt = (time.perf_counter() - t0) / reps
+        tr = tp.tracks_to_numpy(tp.tpc_track_results(ctx, 1, copy=False)[0])
+        out["batched"] = {"ms": dt * 1e3, "clusters_per_s": ev.n / dt,
+                          "timing": "host wall clock around launch + results, device inputs"}
+        out["tracks"] = int(tr.n_tracks)
+        out["mc"] = synth.mc_performance(ev, tr.sector, tr.hit_off, tr.hit_cid)
+    finally:
+        tp.tpc_track_destroy(ctx)
+    pinned = [torch.from_numpy(ev.y).pin_memory(), torch.from_numpy(ev.z).pin_memory(),
+              torch.from_numpy(ev.row.view(np.int16)).pin_memory(),
+              torch.from_numpy(ev.sector.view(np.int16)).pin_memory()]
+    hc = tp.clusters_of(*pinned)[0]
+    sctx = tp.tpc_track_create(ev.n + 1024, max_events_in_flight=2, max_events_per_launch=1)
+    try:
+        t = tp.tpc_track_submit(sctx, hc, geom, bz)  # warm-up
+        if tp.tpc_track_poll(sctx, t, 60_000_000, copy=False) is None:
+            raise TimeoutError("pile-up ticket not done after 60 s")
+        tp.tpc_track_release(sctx, t)
+        t0 = time.perf_counter()
+        tks = [tp.tpc_track_submit(sctx, hc, geom, bz) for _ in range(n_served)]
+        lat = []
+        for t in tks:
+            if tp.tpc_track_poll(sctx, t, 60_000_000, copy=False) is None:
+                raise TimeoutError("pile-up ticket not done after 60 s")
+            lat.append(time.perf_counter() - t0)
+            tp.tpc_track_release(sctx, t)
+        span = time.perf_counter() - t0
+        out["served"] = {"events": n_served, "slots": 2, "clusters_per_s": n_served * ev.n / span,
+                         "first_result_ms": lat[0] * 1e3, "last_result_ms": lat[-1] * 1e3,
+                         "timing": "host wall clock, pinned host inputs, tickets submitted at once"}
+    finally:
+        tp.tpc_track_destroy(sctx)
+    return out
 
 
 def traffic_for(kernel: str, counters: dict):
@@ -430,6 +556,8 @@ def run_ours(args):
     dom_ms = ktimes[dom][0] / ktimes[dom][1]
     achieved = kb[dom] / (dom_ms * 1e-3) / 1e9
     b_alg = sum(kb.values()) / n
+    # I/O-only lower bound: the clusters in (12 B) and the tracks out
+    io_b = (12 * n + 100 * counters["n_tracks"] + 4 * counters["n_track_hits"]) / n
 
     # end to end through the C ABI with pinned host inputs
     pinned = [torch.from_numpy(ev.y).pin_memory(), torch.from_numpy(ev.z).pin_memory(),
@@ -479,6 +607,16 @@ def run_ours(args):
             served = served_vs_one(tp, torch, [hc], geom, bz, n)
         except Exception as e:  # reported, the bench line still goes out
             served = {"error": repr(e)}
+        try:
+            if args.served_sweep == "full":  # rates and lengths of config 4
+                rates = (10, 20, 50, 100, 200, 500, 1000, 2000)
+                n_of = lambda lam: int(min(2000, 30 * lam))
+            else:
+                rates = (100, 500, 1000, 2000)
+                n_of = lambda lam: int(min(300, 10 * lam))
+            served["stream"] = served_sweep(tp, torch, synth, rates, n_of)
+        except Exception as e:
+            served["stream"] = {"error": repr(e)}
 
     batched = None
     if not args.no_batched and rank == 0:
@@ -486,6 +624,13 @@ def run_ours(args):
             batched = batched_vs_sequential(tp, torch, synth, stream)
         except Exception as e:  # reported, the bench line still goes out
             batched = {"error": repr(e)}
+
+    pileup = None
+    if not args.no_pileup and rank == 0:
+        try:
+            pileup = pileup_section(tp, torch, synth, stream)
+        except Exception as e:  # reported, the bench line still goes out
+            pileup = {"error": repr(e)}
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -513,10 +658,12 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": kb[dom], "launch_ms": dom_ms},
             "path_roofline": {"bytes_per_cluster": b_alg,
                               "clusters_per_s_at_peak": peak * 1e9 / b_alg,
-                              "frac": value / world / (peak * 1e9 / b_alg)},
+                              "frac": value / world / (peak * 1e9 / b_alg),
+                              "io_bytes_per_cluster": io_b,
+                              "io_bound_clusters_per_s": peak * 1e9 / io_b},
             "kernels_ms": {k: v[0] / v[1] for k, v in ktimes.items()},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-            "cpu_baseline": cpu, "served": served, "batched": batched,
+            "cpu_baseline": cpu, "served": served, "batched": batched, "pileup": pileup,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -565,6 +712,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-pileup", action="store_true")
+    ap.add_argument("--served-sweep", default="short", choices=["short", "full"],
+                    help="event-stream sweep: 4 rates x <=300 events (short) or the 8 rates "
+                         "10-2000/s with 30 s or 2000 events each (full)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -305,3 +305,52 @@ def noiseless_track(q: float, pt: float, tanl: float, phi0: float, *, vx=0.0, vy
     rng = np.random.default_rng(0)
     return make_event(rng, p, n_sectors_phi=n_sectors_phi, split_z=False, sigma=0.0,
                       noise_frac=0.0, dtype=np.float64, shuffle=False)
+
+
+def mc_performance(ev: Event, sector, hit_off, hit_cid, *, min_clusters: int = 30,
+                   match_frac: float = 0.9, pt_min: float = 0.2) -> dict:
+    """Tracks against the generator's labels, per particle segment in a sector.
+
+    A track matches particle P when at least match_frac of its hits carry P's
+    label; it then matches the segment (P, its sector).  A segment is
+    reconstructable when it holds at least min_clusters clusters.  Returns
+    efficiency (all segments and pT >= pt_min), fake rate (unmatched tracks)
+    and clone rate (extra matches of a segment), over all tracks given.
+    """
+    sector = np.asarray(sector, np.int64)
+    hit_off = np.asarray(hit_off, np.int64)
+    hit_cid = np.asarray(hit_cid, np.int64)
+    n_tr = len(sector)
+    n_seg_sec = int(ev.n_sectors_phi * (2 if ev.split_z else 1))
+    lab = ev.label.astype(np.int64)
+    res = {"n_tracks": n_tr}
+    matched = np.zeros(0, np.int64)
+    fakes = n_tr
+    if n_tr:
+        nh = np.diff(hit_off)
+        tid = np.repeat(np.arange(n_tr), nh)
+        l = lab[hit_cid] + 1  # 0 = noise
+        key = tid * (int(lab.max()) + 2) + l
+        k, c = np.unique(key, return_counts=True)
+        kt, kl = k // (int(lab.max()) + 2), k % (int(lab.max()) + 2)
+        order = np.lexsort((-c, kt))  # per track, largest count first
+        first = np.ones(len(order), bool)
+        first[1:] = kt[order][1:] != kt[order][:-1]
+        best_t, best_l, best_c = kt[order][first], kl[order][first], c[order][first]
+        ok = (best_l > 0) & (best_c >= match_frac * nh[best_t])
+        matched = (best_l[ok] - 1) * n_seg_sec + sector[best_t[ok]]
+        fakes = n_tr - int(ok.sum())
+    sig = lab >= 0
+    seg = lab[sig] * n_seg_sec + ev.sector[sig].astype(np.int64)
+    sk, sc = np.unique(seg, return_counts=True)
+    recble = sk[sc >= min_clusters]
+    mk, mc = np.unique(matched, return_counts=True)
+    found = np.isin(recble, mk)
+    pt = ev.particles.pt[recble // n_seg_sec]
+    res["n_reconstructable"] = int(len(recble))
+    res["efficiency"] = float(found.mean()) if len(recble) else float("nan")
+    sel = pt >= pt_min
+    res[f"efficiency_pt{pt_min:g}"] = float(found[sel].mean()) if sel.any() else float("nan")
+    res["fake_rate"] = fakes / max(1, n_tr)
+    res["clone_rate"] = int(np.sum(mc - 1)) / max(1, n_tr)
+    return res
