@@ -52,6 +52,25 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_time(ms_local: float, world: int) -> float:
+    """The job's time over replicas: the max over ranks of each rank's time,
+    through the initialised process group (a CUDA tensor under nccl, a host
+    tensor under gloo)."""
+    if world <= 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_total: float) -> float:
+    """Whole-job units per second: every rank's units over the max time."""
+    return world * units_per_rank / (ms_total * 1e-3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -540,13 +559,9 @@ def run_ours(args):
     tp.tpc_track_results(ctx, 1, copy=False)
     ktimes = tp.tpc_track_kernel_times(ctx)
     tp.tpc_track_set_profiling(ctx, False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = replica_time(ms_total, world)
     ms_step = ms_total / args.steps
-    value = world * n * args.steps / (ms_total * 1e-3)
+    value = job_throughput(n * args.steps, world, ms_total)
     launches = sum(v[1] for v in ktimes.values())
 
     # roofline of the dominant kernel
