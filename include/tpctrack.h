@@ -27,7 +27,10 @@
  *   - Cluster id (cid): the index of a cluster in its event's input arrays.
  *   - Every call returns a status code; nothing aborts or prints.  On error
  *     tpc_track_last_error() gives a one-line reason.
- *   - Thread safety: one context is driven by one host thread at a time.
+ *   - Thread safety: one context is driven by one host thread at a time,
+ *     except tpc_track_submit, tpc_track_poll, tpc_track_release and
+ *     tpc_track_last_error, which may be called from several threads at
+ *     once (a submitting thread and a polling thread, say).
  */
 #ifndef TPCTRACK_H
 #define TPCTRACK_H
@@ -156,11 +159,13 @@ int tpc_track_launch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
                      const tpc_geometry* geom, float bz_tesla);
 int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs);
 
-/* Served form: queue one event.  A dispatcher thread admits queued events
- * into free slots while their device memory fits the budget, batching all
- * admitted events into the next launch; launches on different slots overlap
- * on the device.  *ticket identifies the request.  Returns TPC_EINVAL for
- * an event larger than one slot. */
+/* Served form: queue one event.  Every slot (a device arena, all of them
+ * allocated at creation within mem_budget) has a worker thread that takes
+ * the queued events, as many as fit the slot, into its next launch;
+ * launches on different slots overlap on the device.  The caller's input
+ * buffers must stay valid until the ticket is polled done.  *ticket
+ * identifies the request.  Returns TPC_EINVAL for an event larger than one
+ * slot. */
 int tpc_track_submit(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geometry* geom,
                      float bz_tesla, uint64_t* ticket);
 
@@ -276,7 +281,9 @@ int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometry* geom,
                             const tpc_track_params* params, int32_t* up_cid, int32_t* dn_cid,
                             void* cuda_stream);
 
-/* One-line description of the last error on the context (never NULL). */
+/* One-line description of the last error on the context (never NULL).  The
+ * string belongs to the calling thread and stays valid until its next call
+ * of tpc_track_last_error. */
 const char* tpc_track_last_error(const tpc_track_ctx* ctx);
 
 /* Release every resource of the context (waits for its device work). */

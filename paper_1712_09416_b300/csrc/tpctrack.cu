@@ -158,6 +158,7 @@ struct tpc_track_ctx {
     tpc_track_config cfg;
     std::vector<std::unique_ptr<tpc::Slot>> slots;
     std::string err;
+    mutable std::mutex err_mu;  // err is written by worker threads too
     // served form
     std::mutex mu;
     std::condition_variable cv_req, cv_done;
@@ -179,7 +180,10 @@ namespace {
 
 int fail(tpc_track_ctx* ctx, int code, const std::string& msg)
 {
-    if (ctx) ctx->err = msg;
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
+        ctx->err = msg;
+    }
     return code;
 }
 
@@ -1298,7 +1302,11 @@ int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t c
 const char* tpc_track_last_error(const tpc_track_ctx* ctx)
 {
     if (!ctx) return "NULL context";
-    return ctx->err.c_str();
+    // a copy owned by the calling thread: stays valid while workers report
+    thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(ctx->err_mu);
+    copy = ctx->err;
+    return copy.c_str();
 }
 
 void tpc_track_destroy(tpc_track_ctx* ctx)
