@@ -163,7 +163,8 @@ int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs);
  * allocated at creation within mem_budget) has a worker thread that takes
  * the queued events, as many as fit the slot, into its next launch;
  * launches on different slots overlap on the device.  The caller's input
- * buffers must stay valid until the ticket is polled done.  *ticket
+ * buffers must stay valid until the ticket is polled done.  An event with
+ * invalid clusters fails its own ticket (TPC_EINVAL) and no other.  *ticket
  * identifies the request.  Returns TPC_EINVAL for an event larger than one
  * slot. */
 int tpc_track_submit(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geometry* geom,

@@ -38,9 +38,9 @@ __device__ __forceinline__ int find_event(const long long* off, int n_ev, long l
 }
 
 __device__ __forceinline__ bool cluster_of(const Launch& L, const long long* off_s, long long i,
-                                           float& y, float& z, int& g, int& cid)
+                                           float& y, float& z, int& g, int& cid, int& e)
 {
-    const int e = find_event(off_s, L.n_events, i);
+    e = find_event(off_s, L.n_events, i);
     const EventDesc d = L.ev[e];
     const long long j = i - d.cl_off;
     y = d.y[j];
@@ -70,7 +70,7 @@ __global__ void k_count(Launch L)
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < L.n_total;
          i0 += kBinIlp * stride) {
-        int g[kBinIlp];
+        int g[kBinIlp], e[kBinIlp];
         bool ok[kBinIlp];
 #pragma unroll
         for (int k = 0; k < kBinIlp; ++k) {
@@ -78,14 +78,19 @@ __global__ void k_count(Launch L)
             float y, z;
             int cid;
             g[k] = 0;
-            ok[k] = i < L.n_total && cluster_of(L, off_s, i, y, z, g[k], cid);
+            e[k] = 0;
+            ok[k] = i < L.n_total && cluster_of(L, off_s, i, y, z, g[k], cid, e[k]);
         }
 #pragma unroll
         for (int k = 0; k < kBinIlp; ++k) {
             const long long i = i0 + k * stride;
             if (i >= L.n_total) break;
-            if (ok[k]) L.rank[i] = atomicAdd(&L.row_cnt[g[k] * kCntPad], 1);
-            else atomicAdd(&L.cnt->n_invalid, 1);
+            if (ok[k]) {
+                L.rank[i] = atomicAdd(&L.row_cnt[g[k] * kCntPad], 1);
+            } else {  // skipped (never binned); counted for its event
+                atomicAdd(&L.cnt->n_invalid, 1);
+                atomicAdd(&L.ev_invalid[e[k]], 1);
+            }
         }
     }
 }
@@ -223,9 +228,9 @@ __global__ void k_scatter(Launch L)
 #pragma unroll
         for (int k = 0; k < kBinIlp; ++k) {
             const long long i = i0 + k * stride;
-            int g = 0;
+            int g = 0, e = 0;
             pos[k] = -1;
-            if (i < L.n_total && cluster_of(L, off_s, i, y[k], z[k], g, cid[k]))
+            if (i < L.n_total && cluster_of(L, off_s, i, y[k], z[k], g, cid[k], e))
                 pos[k] = L.row_off[g] + L.rank[i];
         }
 #pragma unroll

@@ -100,6 +100,7 @@ struct Launch {
     long long* ev_off;          // [n_events + 1] cluster offsets
     int* sec_event;             // [S] event of a global sector
     int* row_cnt;               // [RS * kCntPad] hit count of row g at g * kCntPad
+    int* ev_invalid;            // [n_events] invalid clusters per event
     int* row_off;               // [RS + 1]
     RowGrid* grid;              // [RS]
     unsigned long long* tile_state;  // look-back states (rows | hits | sectors)

@@ -37,7 +37,7 @@ constexpr long long kNaRowTiles = kNaRS / kRowTile + 2;
 constexpr long long kNaHitTiles = kNaMaxClusters / kHitTile + 2;
 constexpr size_t kNaDesc = up256(sizeof(EventDesc) + 2 * sizeof(long long) +
                                  sizeof(int) * kNaMaxSectors + sizeof(float) * kMaxRows);
-constexpr size_t kNaZero = up256(up256(sizeof(Counters)) + 4 * (kNaRS * kCntPad + 2 * kNaMaxSectors) +
+constexpr size_t kNaZero = up256(up256(sizeof(Counters)) + 4 * (kNaRS * kCntPad + 2 * kNaMaxSectors + 4) +
                                  8 * (kNaRowTiles + kNaHitTiles + kNaMaxSectors) + 1024);
 constexpr size_t kNaBytes =
     kNaDesc + kNaZero + up256(4 * (kNaRS + 1)) + up256(sizeof(RowGrid) * kNaRS) +
@@ -166,6 +166,7 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
         };
         L.cnt = (Counters*)z(sizeof(Counters));
         L.row_cnt = (int*)z(4 * (size_t)L.RS * kCntPad);
+        L.ev_invalid = (int*)z(4);
         L.sec_first = (int*)z(4 * (size_t)n_sec);
         L.sec_end = (int*)z(4 * (size_t)n_sec);
         L.n_row_tiles = (int)((L.RS + kRowTile - 1) / kRowTile);

@@ -227,7 +227,7 @@ size_t layout(Slot& s, char* base)
     s.desc_bytes = sizeof(EventDesc) * k.e + sizeof(long long) * (k.e + 1) + sizeof(int) * k.s +
                    sizeof(float) * kMaxRows + 64;
     s.desc_dev = take(s.desc_bytes);
-    s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (k.rs * kCntPad + 2 * k.s) + 8 * (k.row_tiles + k.hit_tiles + k.s) + 4096;
+    s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (k.rs * kCntPad + 2 * k.s + k.e) + 8 * (k.row_tiles + k.hit_tiles + k.s) + 4096;
     s.zero_dev = take(s.zero_cap);
     s.row_off = (int*)take(4 * (k.rs + 1));
     s.grid = (RowGrid*)take(sizeof(RowGrid) * k.rs);
@@ -509,6 +509,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
         };
         L.cnt = (Counters*)take(sizeof(Counters));
         L.row_cnt = (int*)take(4 * (size_t)L.RS * kCntPad);
+        L.ev_invalid = (int*)take(4 * (size_t)n_ev);
         L.sec_first = (int*)take(4 * (size_t)S);
         L.sec_end = (int*)take(4 * (size_t)S);
         L.n_row_tiles = (int)((L.RS + kRowTile - 1) / kRowTile);
@@ -589,7 +590,10 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
 }
 
 // Wait for the slot's launch and turn its device status into a code.
-int launch_status(tpc_track_ctx* ctx, Slot& s)
+// Invalid clusters fail the launch unless per_event (the served form, where
+// they fail only their own event's ticket: they are never binned, so the
+// other events of the launch are unaffected).
+int launch_status(tpc_track_ctx* ctx, Slot& s, bool per_event = false)
 {
     LaunchInfo& I = s.info;
     if (!I.pending) return fail(ctx, TPC_EINVAL, "no launch pending");
@@ -597,7 +601,8 @@ int launch_status(tpc_track_ctx* ctx, Slot& s)
     CUDA_TRY(ctx, cudaEventSynchronize(s.done_ev));
     CUDA_TRY(ctx, cudaGetLastError());
     const Counters& c = *s.cnt_host;
-    if (c.n_invalid) return fail(ctx, TPC_EINVAL, std::to_string(c.n_invalid) + " invalid clusters (row, sector or coordinate)");
+    if (c.n_invalid && !per_event)
+        return fail(ctx, TPC_EINVAL, std::to_string(c.n_invalid) + " invalid clusters (row, sector or coordinate)");
     if (c.timeout) return fail(ctx, TPC_ETIMEOUT, "a bounded device wait gave up");
     if (c.ovf_row) return fail(ctx, TPC_ECAPACITY, "a pad row holds more than 4096 clusters");
     if (c.ovf_tracklets || c.n_starts > s.caps.t)
@@ -718,12 +723,15 @@ void pool_put(tpc_track_ctx* ctx, PinnedBuf b)
 int collect_to_tickets(tpc_track_ctx* ctx, Slot& s, std::vector<std::unique_ptr<TicketResult>>& out)
 {
     LaunchInfo& I = s.info;
-    if (int rc = launch_status(ctx, s)) return rc;
+    if (int rc = launch_status(ctx, s, true)) return rc;
     const Counters& c = *s.cnt_host;
     const int nt = c.n_tracks;
     cudaStream_t st = s.stream;
+    std::vector<int> inv(I.n_ev, 0);
     CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_trk_off, s.sec_trk_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_hit_off, s.sec_hit_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
+    if (c.n_invalid)
+        CUDA_TRY(ctx, cudaMemcpyAsync(inv.data(), I.L.ev_invalid, 4 * (size_t)I.n_ev, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
     std::vector<int> h0s(I.n_ev);
     for (int e = 0; e < I.n_ev; ++e) {
@@ -741,6 +749,12 @@ int collect_to_tickets(tpc_track_ctx* ctx, Slot& s, std::vector<std::unique_ptr<
                      o_cov = place(60 * m), o_chi = place(4 * m), o_ndf = place(4 * m),
                      o_ho = place(4 * (m + 1)), o_hc = place(4 * mh);
         TicketResult& R = *out[e];
+        if (inv[e]) {  // this event had invalid clusters: no result for it
+            R.status = fail(ctx, TPC_EINVAL, std::to_string(inv[e]) +
+                                                 " invalid clusters (row, sector or coordinate)");
+            continue;
+        }
+        R.status = TPC_OK;
         R.buf = pool_get(ctx, off);
         if (!R.buf.p) return fail(ctx, TPC_ENOMEM, "pinned result buffer");
         char* b = R.buf.p;
@@ -771,6 +785,7 @@ int collect_to_tickets(tpc_track_ctx* ctx, Slot& s, std::vector<std::unique_ptr<
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
     for (int e = 0; e < I.n_ev; ++e) {  // hit offsets relative to the event
         TicketResult& R = *out[e];
+        if (R.status != TPC_OK) continue;
         int32_t* ho = (int32_t*)R.view.hit_off;
         if (R.view.n_tracks > 0)
             for (int64_t j = 0; j <= R.view.n_tracks; ++j) ho[j] -= h0s[e];
@@ -918,8 +933,8 @@ void worker(tpc_track_ctx* ctx, Slot* s)
         if (rc == TPC_OK) rc = collect_to_tickets(ctx, *s, done);
         const auto t2 = std::chrono::steady_clock::now();
         for (auto& d : done) {
-            d->status = rc;
-            if (rc != TPC_OK) {  // no partial result: buffers back to the pool
+            if (rc != TPC_OK) d->status = rc;  // launch-wide error
+            if (d->status != TPC_OK) {  // no partial result: buffers back to the pool
                 pool_put(ctx, d->buf);
                 d->buf = PinnedBuf{};
                 d->view = tpc_tracks{};

@@ -236,6 +236,54 @@ def test_schedule_changes_speed_not_results(tp):
                 assert np.array_equal(getattr(a, f), getattr(b, f)), ("tuned", f)
 
 
+def test_served_mix_with_an_invalid_event_and_a_polling_thread(tp):
+    """Tickets polled from another thread while events are submitted, up to
+    four events per launch: every valid event's tracks equal a single call's,
+    and the event with an invalid cluster fails its own ticket only."""
+    import threading
+    evs = synth.batch_events(n_events=7, seed0=3300)
+    bad = 3
+    ys = [e.y.copy() for e in evs]
+    ys[bad][len(ys[bad]) // 2] = np.nan
+    with tp.Tracker(2_000_000) as t:
+        alone = {i: t.event(e) for i, e in enumerate(evs) if i != bad}
+    s = tp.Tracker(4 * 2_000_000, max_events_in_flight=2, max_events_per_launch=4)
+    try:
+        keep, tickets, got, errors = [], [None] * len(evs), {}, []
+
+        def poller():
+            try:
+                for i in range(len(evs)):
+                    for _ in range(600000):
+                        if tickets[i] is not None:
+                            break
+                        threading.Event().wait(0.0001)
+                    try:
+                        got[i] = tp.tpc_track_poll(s.ctx, tickets[i], 60_000_000)
+                    except tp.TpcError as e:
+                        got[i] = e
+                    tp.tpc_track_release(s.ctx, tickets[i])
+            except Exception as e:  # surfaced below
+                errors.append(e)
+        th = threading.Thread(target=poller)
+        th.start()
+        for i, e in enumerate(evs):
+            g, kx = tp.geometry_of(e)
+            c, k = tp.clusters_of(ys[i], e.z, e.row, e.sector)
+            keep.append((g, kx, c, k))
+            tickets[i] = tp.tpc_track_submit(s.ctx, c, g, float(e.bz))
+        th.join(120)
+        assert not th.is_alive() and not errors, errors
+        assert isinstance(got[bad], tp.TpcError) and got[bad].code == tp.TPC_EINVAL
+        for i, a in alone.items():
+            b = got[i]
+            assert b is not None and not isinstance(b, Exception), (i, b)
+            for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+                assert np.array_equal(getattr(a, f), getattr(b, f)), (i, f)
+    finally:
+        s.close()
+
+
 def test_batch_equals_single_events(tp, trk):
     evs = synth.batch_events(n_events=6)
     alone = [trk.event(e) for e in evs]
