@@ -101,7 +101,7 @@ def kernel_bytes(c: dict) -> dict:
         "k_weights": 20 * Th + 32 * Tl,
         "k_sel_decide": 10 * Th + 32 * T,
         "k_sel_sort": 12 * T + 8 * K,
-        "k_sel_write": 212 * K + 18 * Kh,
+        "k_sel_write": 244 * K + 12 * Kh,
     }
 
 

@@ -6,14 +6,16 @@
 // min_track_hits hits and at least half of its hits; the track keeps the
 // owned hits and the tracklet's parameters.  Tracks are emitted in the order
 // (sector, row of the first owned hit, cid of h0).
-//   k_sel_decide  one warp per tracklet: owned hits, decision, sort key;
-//                 also marks the tracklet range of every sector (tracklets
-//                 are ordered by sector because start hits are)
+//   k_sel_decide  one warp per tracklet: owned hits (kept as one bit per
+//                 row), decision, sort key; also marks the tracklet range of
+//                 every sector (tracklets are ordered by sector because start
+//                 hits are)
 //   k_sel_sort    one block per sector, in sector order: compacts the
 //                 emitted tracklets, sorts their keys in shared memory (rank
 //                 sort up to 2048 keys, else bitonic), scans their hit counts and takes
 //                 the sector's output offsets from a decoupled look-back
 //   k_sel_write   one warp per emitted tracklet: header and owned hit cids
+//                 (from the owned-row bits, no second read of the weights)
 // Bytes per cluster: rowhit 2 + weight 8 per assigned hit (decide), about
 // 100 B per track header and 4 B per output hit (write).
 #include <cuda_runtime.h>
@@ -54,6 +56,7 @@ __global__ void k_sel_decide(Launch L)
                     own = h >= 0 && L.weight[h] == key;
                 }
                 const unsigned b = __ballot_sync(0xffffffffu, own);
+                if (lane == 0) L.tl_own[(size_t)t * kOwnWords + (r0 - H.first) / 32] = b;
                 if (b && first_own < 0) first_own = r0 + __ffs(b) - 1;
                 nown += __popc(b);
             }
@@ -222,20 +225,14 @@ __global__ void k_sel_write(Launch L)
             L.k_ndf[j] = H.ndf;
             L.k_hit_off[j] = off0;
         }
-        const unsigned long long key = ((unsigned long long)H.nhits << 32) |
-                                       (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
+        // owned rows from the bits k_sel_decide left (no weight reads here)
         const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
+        const unsigned* ownw = L.tl_own + (size_t)t * kOwnWords;
         int off = off0;
-        for (int r0 = H.first; r0 <= H.last; r0 += 32) {
-            const int r = r0 + lane;
-            int h = -1;
-            bool own = false;
-            if (r <= H.last) {
-                h = rowhit[r];
-                own = h >= 0 && L.weight[h] == key;
-            }
-            const unsigned b = __ballot_sync(0xffffffffu, own);
-            if (own) L.k_hit_cid[off + __popc(b & ((1u << lane) - 1))] = L.hcid[h];
+        for (int r0 = H.first, c = 0; r0 <= H.last; r0 += 32, ++c) {
+            const unsigned b = ownw[c];
+            if ((b >> lane) & 1u)
+                L.k_hit_cid[off + __popc(b & ((1u << lane) - 1))] = L.hcid[rowhit[r0 + lane]];
             off += __popc(b);
         }
     }

@@ -19,6 +19,7 @@
 namespace tpc {
 
 constexpr int kMaxRows = 256;          // pad rows per sector (row index fits 8 bits)
+constexpr int kOwnWords = kMaxRows / 32;
 constexpr int kMaxRowHits = 4096;      // hits of one (sector,row) handled in shared memory
 constexpr int kMaxSectorTracks = 4096; // emitted tracks per sector sorted in shared memory
 constexpr int kMaxBinsPerDim = 512;
@@ -118,6 +119,7 @@ struct Launch {
     int* tl_rowhit;             // [t_cap * R] global hit index or -1
     unsigned long long* tl_key; // [t_cap] sector-local sort key or ~0
     int* tl_nown;               // [t_cap]
+    unsigned* tl_own;           // [t_cap * kOwnWords] owned-row bits, 32 rows per word from first
     int* tl_out;                // [t_cap] output track index or -1
     int* tl_hitoff;             // [t_cap] output hit offset
     int* sec_first;             // [S] first tracklet of a sector

@@ -100,6 +100,7 @@ struct Slot {
     int* upg;
     unsigned long long* tl_key;
     int *tl_nown, *tl_out, *tl_hitoff, *sec_trk_off, *sec_hit_off;
+    unsigned* tl_own;
     int *k_sector, *k_ndf, *k_hit_off, *k_hit_cid;
     float *k_x, *k_param, *k_cov, *k_chi2;
     // host side
@@ -250,6 +251,7 @@ size_t layout(Slot& s, char* base)
     s.upg = (int*)take(4 * k.n);
     s.tl_key = (unsigned long long*)take(8 * (size_t)k.t);
     s.tl_nown = (int*)take(4 * (size_t)k.t);
+    s.tl_own = (unsigned*)take(4 * (size_t)kOwnWords * k.t);
     s.tl_out = (int*)take(4 * (size_t)k.t);
     s.tl_hitoff = (int*)take(4 * (size_t)k.t);
     s.sec_trk_off = (int*)take(4 * (k.s + 1));
@@ -542,6 +544,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.upg = s.upg;
     L.tl_key = s.tl_key;
     L.tl_nown = s.tl_nown;
+    L.tl_own = s.tl_own;
     L.tl_out = s.tl_out;
     L.tl_hitoff = s.tl_hitoff;
     L.sec_trk_off = s.sec_trk_off;
