@@ -85,6 +85,15 @@ def test_one_sector_event_stage_parity(tp, trk, orc):
     assert s["eff_pt02"] >= 0.95 and s["fake_rate"] < 0.02, s
 
 
+def test_sparse_pp_like_event_stage_parity(tp, trk, orc):
+    """A 20-track event over all 36 sectors (the low end of the batched
+    workload's multiplicities): every stage against the oracle."""
+    rng = np.random.default_rng(3999)
+    ev = synth.served_event(rng, 20)
+    g, o, rep, trep = check_event(tp, trk, ev, orc)
+    assert g["counters"]["n_tracks"] > 0
+
+
 def test_isolated_tracks(tp, trk, orc):
     ev = _util.isolated_event()
     check_event(tp, trk, ev, orc, max_diff_frac=0.0)
