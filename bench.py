@@ -94,6 +94,7 @@ def kernel_bytes(c: dict) -> dict:
         "k_rowscan": 4 * RS + 4 * RS + 32 * RS,
         "k_scatter": 12 * N + 12 * N,
         "k_rowsort": 12 * N + 16 * N + 8 * N + 4 * (B + RS) + 32 * RS,
+        "k_rowsort_big": 0,  # its rows' bytes are counted in k_rowsort
         "k_neighbours": 8 * N + 4 * N + 4 * B,
         "k_clean_starts": 4 * N + 4 * N + 4 * N + 4 * N + 4 * T,
         "k_chains": 8 * c["n_chain_hits"] + 32 * T,

@@ -13,7 +13,9 @@
 //   k_scatter  moves every cluster to row offset + rank
 //   k_rowsort  one block per row: counting sort by bin in shared memory,
 //              cid order inside a bin, writes the sorted hits and the bin
-//              offsets (and clears the hit weights for the fit)
+//              offsets (and clears the hit weights for the fit); rows above
+//              1024 hits are listed and sorted by a second launch with a
+//              larger shared-memory footprint
 // Bytes per cluster (read + write): count 12, scatter 12 + 12, rowsort 12 +
 // 16 + 8 (weights), plus the row and bin tables.
 #include <cuda_runtime.h>
@@ -244,17 +246,35 @@ __global__ void k_scatter(Launch L)
 
 constexpr int kSortThreads = 512;
 
+// Shared memory of a row sort for rows of up to cap hits.
+constexpr size_t sort_smem(int cap)
+{
+    return sizeof(int) * (cap * kBinsPerHitX2 / 2 + 2) + sizeof(int) * cap +
+           3 * sizeof(int16_t) * cap;
+}
+
+// One block per row: counting sort by bin, cid order inside a bin.  BIG =
+// false sorts the rows of up to kSmallRowHits hits and lists the larger ones
+// in big_rows; BIG = true sorts the listed rows (up to kMaxRowHits each).
+template <bool BIG>
 __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
 {
+    constexpr int CAP = BIG ? kMaxRowHits : kSmallRowHits;
     extern __shared__ unsigned char smem[];
-    int* hist = reinterpret_cast<int*>(smem);                                // [nb + 1]
-    int* scid = hist + (kMaxRowBins + 2);                                // [n]
-    int16_t* sbin = reinterpret_cast<int16_t*>(scid + kMaxRowHits);          // [n]
-    int16_t* sslot = sbin + kMaxRowHits;                                     // [n]
-    int16_t* sorder = sslot + kMaxRowHits;                                   // [n]
-    for (int g = blockIdx.x; g < L.RS; g += gridDim.x) {
+    int* hist = reinterpret_cast<int*>(smem);                           // [nb + 1]
+    int* scid = hist + (CAP * kBinsPerHitX2 / 2 + 2);                   // [n]
+    int16_t* sbin = reinterpret_cast<int16_t*>(scid + CAP);             // [n]
+    int16_t* sslot = sbin + CAP;                                        // [n]
+    int16_t* sorder = sslot + CAP;                                      // [n]
+    const int n_items = BIG ? min(L.cnt->n_big_rows, L.RS) : L.RS;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int g = BIG ? L.big_rows[it] : it;
         const int base = L.row_off[g];
         const int n = L.row_off[g + 1] - base;
+        if (!BIG && n > CAP) {
+            if (threadIdx.x == 0) L.big_rows[atomicAdd(&L.cnt->n_big_rows, 1)] = g;
+            continue;
+        }
         const RowGrid G = L.grid[g];
         const int nb = G.ny * G.nz;
         const int gs = g / L.R;
@@ -330,16 +350,12 @@ __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
 
 }  // namespace
 
-size_t rowsort_smem_bytes()
-{
-    return sizeof(int) * (kMaxRowBins + 2) + sizeof(int) * kMaxRowHits +
-           3 * sizeof(int16_t) * kMaxRowHits;
-}
-
 void prepare_binning()
 {
-    cudaFuncSetAttribute(k_rowsort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)rowsort_smem_bytes());
+    cudaFuncSetAttribute(k_rowsort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem(kSmallRowHits));
+    cudaFuncSetAttribute(k_rowsort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem(kMaxRowHits));
 }
 
 void launch_binning(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
@@ -354,8 +370,12 @@ void launch_binning(const Launch& L, const Schedule& S, void* stream_, const Ker
     hook_after(hook, "k_scatter");
     const int rows_blocks = L.RS < S.n_sm * 16 ? L.RS : S.n_sm * 16;
     const int threads = S.sort_threads == 256 ? 256 : kSortThreads;
-    k_rowsort<<<rows_blocks > 0 ? rows_blocks : 1, threads, rowsort_smem_bytes(), stream>>>(L);
+    k_rowsort<false><<<rows_blocks > 0 ? rows_blocks : 1, threads, sort_smem(kSmallRowHits),
+                       stream>>>(L);
     hook_after(hook, "k_rowsort");
+    // the rows above kSmallRowHits hits, listed by the first pass
+    k_rowsort<true><<<S.n_sm * 2, kSortThreads, sort_smem(kMaxRowHits), stream>>>(L);
+    hook_after(hook, "k_rowsort_big");
 }
 
 }  // namespace tpc

@@ -26,6 +26,9 @@ constexpr int kMaxBinsPerDim = 512;
 // y-z bins of a row with cnt hits: max(1, cnt * kBinsPerHitX2 / 2)
 constexpr int kBinsPerHitX2 = 4;
 constexpr int kMaxRowBins = kMaxRowHits * kBinsPerHitX2 / 2;
+// rows up to kSmallRowHits hits are sorted with a small shared-memory
+// footprint (more rows in flight); larger rows go to a second pass
+constexpr int kSmallRowHits = 1024;
 constexpr long long kSpinLimit = 1LL << 22;  // bounded look-back waits
 constexpr int kRowTile = 512;    // (sector, row) records per look-back tile of k_rowscan
 constexpr int kHitTile = 2048;   // sorted hits per look-back tile of k_clean_starts
@@ -73,7 +76,8 @@ struct Counters {
     int ticket_rows, ticket_hits, ticket_sectors;
     int tl_next;          // work counter of the persistent constructor
     int n_chain_hits;     // hits on the chains of all start hits
-    int pad[14];
+    int n_big_rows;       // rows too large for the small row sort
+    int pad[13];
 };
 
 // Everything a kernel needs, passed by value.
@@ -102,6 +106,7 @@ struct Launch {
     int* sec_event;             // [S] event of a global sector
     int* row_cnt;               // [RS * kCntPad] hit count of row g at g * kCntPad
     int* ev_invalid;            // [n_events] invalid clusters per event
+    int* big_rows;              // [RS] rows left by the small row sort
     int* row_off;               // [RS + 1]
     RowGrid* grid;              // [RS]
     unsigned long long* tile_state;  // look-back states (rows | hits | sectors)

@@ -40,7 +40,7 @@ constexpr size_t kNaDesc = up256(sizeof(EventDesc) + 2 * sizeof(long long) +
 constexpr size_t kNaZero = up256(up256(sizeof(Counters)) + 4 * (kNaRS * kCntPad + 2 * kNaMaxSectors + 4) +
                                  8 * (kNaRowTiles + kNaHitTiles + kNaMaxSectors) + 1024);
 constexpr size_t kNaBytes =
-    kNaDesc + kNaZero + up256(4 * (kNaRS + 1)) + up256(sizeof(RowGrid) * kNaRS) +
+    kNaDesc + kNaZero + up256(4 * (kNaRS + 1)) + up256(4 * kNaRS) + up256(sizeof(RowGrid) * kNaRS) +
     up256(4 * kNaBins) + 8 * up256(4 * kNaMaxClusters) /* tmp yz cid rank, hyz hcid hrow */ +
     2 * up256(4 * kNaMaxClusters) /* up dn */ + 2 * up256(4 * kNaMaxClusters) /* upc dnc */ +
     up256(4 * kNaMaxClusters) /* upg */ + up256(8 * kNaMaxClusters) /* weight */ +
@@ -176,6 +176,7 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
         if (cudaMemsetAsync(zero, 0, zo, st) != cudaSuccess) return TPC_ECUDA;
     }
     L.row_off = (int*)take(4 * (kNaRS + 1));
+    L.big_rows = (int*)take(4 * kNaRS);
     L.grid = (RowGrid*)take(sizeof(RowGrid) * kNaRS);
     L.bin_start = (int*)take(4 * kNaBins);
     L.tmp_yz = (float2*)take(8 * kNaMaxClusters);

@@ -85,7 +85,7 @@ struct Slot {
     void* desc_dev;      // EventDesc[e] | ev_off[e+1] | sec_event[s]
     char* zero_dev;      // counters | row_cnt | sec_first | sec_end | tile_state
     size_t zero_cap = 0;
-    int *row_off;
+    int *row_off, *big_rows;
     RowGrid* grid;
     float2* tmp_yz;
     int *tmp_cid, *rank;
@@ -231,6 +231,7 @@ size_t layout(Slot& s, char* base)
     s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (k.rs * kCntPad + 2 * k.s + k.e) + 8 * (k.row_tiles + k.hit_tiles + k.s) + 4096;
     s.zero_dev = take(s.zero_cap);
     s.row_off = (int*)take(4 * (k.rs + 1));
+    s.big_rows = (int*)take(4 * k.rs);
     s.grid = (RowGrid*)take(sizeof(RowGrid) * k.rs);
     s.tmp_yz = (float2*)take(8 * k.n);
     s.tmp_cid = (int*)take(4 * k.n);
@@ -524,6 +525,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
         CUDA_TRY(ctx, cudaMemsetAsync(s.zero_dev, 0, zo, s.stream));
     }
     L.row_off = s.row_off;
+    L.big_rows = s.big_rows;
     L.grid = s.grid;
     L.tmp_yz = s.tmp_yz;
     L.tmp_cid = s.tmp_cid;
