@@ -296,6 +296,19 @@ def compare_point(tp, events, ns, arrivals, geom, bz, n_max, rate):
                        "clusters_per_s": n_cl / spans}}, None
 
 
+def at_equal_p99(points, targets_ms=(10.0, 20.0)) -> list:
+    """For each p99 target: the highest clusters/s each server sustained
+    among the measured rates whose p99 latency met the target."""
+    out = []
+    for tgt in targets_ms:
+        row = {"p99_target_ms": tgt}
+        for side in ("one_event", "served"):
+            ok = [p[side]["clusters_per_s"] for p in points if p[side]["p99_ms"] <= tgt]
+            row[side + "_clusters_per_s"] = max(ok) if ok else None
+        out.append(row)
+    return out
+
+
 def served_vs_one(tp, torch, host_events, geom, bz, n_per_event, rate_factors=(0.7, 1.5, 3.0),
                   n_events=120, seed=4):
     """Poisson arrivals of central events: one-at-a-time FIFO server vs the
@@ -329,6 +342,7 @@ def served_vs_one(tp, torch, host_events, geom, bz, n_per_event, rate_factors=(0
             out["error"] = err
             return out
         out["points"].append(pt)
+    out["at_equal_p99"] = at_equal_p99(out["points"])
     return out
 
 
@@ -363,6 +377,7 @@ def served_sweep(tp, torch, synth, rates, n_events_of, pool_size=64, seed=4):
             out["error"] = err
             return out
         out["points"].append(pt)
+    out["at_equal_p99"] = at_equal_p99(out["points"])
     return out
 
 
