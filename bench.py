@@ -202,13 +202,16 @@ def percentile(v, q):
 SERVED_SLOTS, SERVED_PER_LAUNCH = 3, 2
 
 
-def served_ctx(tp, host_events, geom, bz, n_per_event):
-    """A served context whose pinned result pool is warm (two full bursts)."""
+def served_ctx(tp, host_events, geom, bz, n_per_event, sizes=None):
+    """A served context whose pinned result pool is warm: two full bursts of
+    the largest events (sizes = their cluster counts, when they differ)."""
     ctx = tp.tpc_track_create(SERVED_PER_LAUNCH * n_per_event + 1024,
                               max_events_in_flight=SERVED_SLOTS,
                               max_events_per_launch=SERVED_PER_LAUNCH)
+    order = sorted(range(len(host_events)), key=lambda i: -sizes[i]) if sizes else \
+        list(range(len(host_events)))
     for _ in range(2):
-        tks = [tp.tpc_track_submit(ctx, host_events[i % len(host_events)], geom, bz)
+        tks = [tp.tpc_track_submit(ctx, host_events[order[i % len(order)]], geom, bz)
                for i in range(SERVED_SLOTS * SERVED_PER_LAUNCH + 4)]
         for t in tks:
             if tp.tpc_track_poll(ctx, t, 60_000_000, copy=False) is None:
@@ -242,7 +245,7 @@ def run_served(tp, events, ns, arrivals, geom, bz, n_max):
     Returns latencies, span and an error string (or None); every wait is
     bounded."""
     n_events = len(arrivals)
-    ctx = served_ctx(tp, events, geom, bz, n_max)
+    ctx = served_ctx(tp, events, geom, bz, n_max, ns)
     lats = [None] * n_events
     errors = []
     tickets = [None] * n_events
@@ -459,9 +462,9 @@ def pileup_section(tp, torch, synth, stream, reps=3, n_served=4):
         t0 = time.perf_counter()
         for _ in range(reps):
             tp.tpc_track_launch(ctx, [c], geom, bz)
-            tp.tpc_track_results(ctx, 1, copy=False)
+            outs = tp.tpc_track_results(ctx, 1, copy=False)
         dt = (time.perf_counter() - t0) / reps
-        tr = tp.tracks_to_numpy(tp.tpc_track_results(ctx, 1, copy=False)[0])
+        tr = tp.tracks_to_numpy(outs[0])
         out["batched"] = {"ms": dt * 1e3, "clusters_per_s": ev.n / dt,
                           "timing": "host wall clock around launch + results, device inputs"}
         out["tracks"] = int(tr.n_tracks)
@@ -474,10 +477,11 @@ def pileup_section(tp, torch, synth, stream, reps=3, n_served=4):
     hc = tp.clusters_of(*pinned)[0]
     sctx = tp.tpc_track_create(ev.n + 1024, max_events_in_flight=2, max_events_per_launch=1)
     try:
-        t = tp.tpc_track_submit(sctx, hc, geom, bz)  # warm-up
-        if tp.tpc_track_poll(sctx, t, 60_000_000, copy=False) is None:
-            raise TimeoutError("pile-up ticket not done after 60 s")
-        tp.tpc_track_release(sctx, t)
+        # warm-up: the same burst, so that its pinned result buffers exist
+        for t in [tp.tpc_track_submit(sctx, hc, geom, bz) for _ in range(n_served)]:
+            if tp.tpc_track_poll(sctx, t, 60_000_000, copy=False) is None:
+                raise TimeoutError("pile-up ticket not done after 60 s")
+            tp.tpc_track_release(sctx, t)
         t0 = time.perf_counter()
         tks = [tp.tpc_track_submit(sctx, hc, geom, bz) for _ in range(n_served)]
         lat = []
@@ -595,42 +599,44 @@ def run_ours(args):
               torch.from_numpy(ev.row.view(np.int16)).pin_memory(),
               torch.from_numpy(ev.sector.view(np.int16)).pin_memory()]
     hc, hkeep = tp.clusters_of(*pinned)
-    k_e2e = max(8, min(args.steps, 40))
-    # (a) one event per call (tpc_track_event): copies, launch and result
-    # read strictly one after the other
-    ctx_h = tp.tpc_track_create(n + 65536, max_events_per_launch=1)
-    for _ in range(3):
-        tr = tp.tpc_track_event(ctx_h, hc, geom, bz, copy=False)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        tr = tp.tpc_track_event(ctx_h, hc, geom, bz, copy=False)
-    barrier()
-    seq_s = time.perf_counter() - t0
-    n_tr, n_hits = tr.n_tracks, len(tr.hit_cid)
-    tp.tpc_track_destroy(ctx_h)
-    # (b) the served API (tpc_track_submit / poll) with every event submitted
-    # at once: each event's host inputs are copied in and its tracks copied
-    # out inside the timed region, overlapped across slots
-    ctx_s = served_ctx(tp, [hc], geom, bz, n)
-    barrier()
-    t0 = time.perf_counter()
-    tks = [tp.tpc_track_submit(ctx_s, hc, geom, bz) for _ in range(k_e2e)]
-    for t in tks:
-        if tp.tpc_track_poll(ctx_s, t, 60_000_000, copy=False) is None:
-            raise TimeoutError("served ticket not done after 60 s")
-        tp.tpc_track_release(ctx_s, t)
-    barrier()
-    srv_s = time.perf_counter() - t0
-    tp.tpc_track_destroy(ctx_s)
-    h2d = 12 * n + 4096
-    d2h = 256 + n_tr * (4 + 4 + 20 + 60 + 4 + 4 + 4) + 4 * n_hits + 4 * 37
-    e2e = {"value": world * n * k_e2e / srv_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "steps": k_e2e,
-           "api": f"tpc_track_submit/poll, {SERVED_SLOTS} slots x {SERVED_PER_LAUNCH} events, "
-                  "pinned host inputs, results read from pinned buffers",
-           "one_event_calls": {"value": world * n * k_e2e / seq_s, "unit": UNIT,
-                               "api": "tpc_track_event, one call per event"}}
+    e2e = None
+    if not args.no_e2e:
+        k_e2e = max(8, min(args.steps, 40))
+        # (a) one event per call (tpc_track_event): copies, launch and result
+        # read strictly one after the other
+        ctx_h = tp.tpc_track_create(n + 65536, max_events_per_launch=1)
+        for _ in range(3):
+            tr = tp.tpc_track_event(ctx_h, hc, geom, bz, copy=False)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            tr = tp.tpc_track_event(ctx_h, hc, geom, bz, copy=False)
+        barrier()
+        seq_s = time.perf_counter() - t0
+        n_tr, n_hits = tr.n_tracks, len(tr.hit_cid)
+        tp.tpc_track_destroy(ctx_h)
+        # (b) the served API (tpc_track_submit / poll) with every event submitted
+        # at once: each event's host inputs are copied in and its tracks copied
+        # out inside the timed region, overlapped across slots
+        ctx_s = served_ctx(tp, [hc], geom, bz, n)
+        barrier()
+        t0 = time.perf_counter()
+        tks = [tp.tpc_track_submit(ctx_s, hc, geom, bz) for _ in range(k_e2e)]
+        for t in tks:
+            if tp.tpc_track_poll(ctx_s, t, 60_000_000, copy=False) is None:
+                raise TimeoutError("served ticket not done after 60 s")
+            tp.tpc_track_release(ctx_s, t)
+        barrier()
+        srv_s = time.perf_counter() - t0
+        tp.tpc_track_destroy(ctx_s)
+        h2d = 12 * n + 4096
+        d2h = 256 + n_tr * (4 + 4 + 20 + 60 + 4 + 4 + 4) + 4 * n_hits + 4 * 37
+        e2e = {"value": world * n * k_e2e / srv_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": k_e2e,
+               "api": f"tpc_track_submit/poll, {SERVED_SLOTS} slots x {SERVED_PER_LAUNCH} events, "
+                      "pinned host inputs, results read from pinned buffers",
+               "one_event_calls": {"value": world * n * k_e2e / seq_s, "unit": UNIT,
+                                   "api": "tpc_track_event, one call per event"}}
 
     served = None
     if not args.no_served and rank == 0:
@@ -744,6 +750,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pileup", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-input runs (profiling)")
     ap.add_argument("--served-sweep", default="short", choices=["short", "full"],
                     help="event-stream sweep: 4 rates x <=300 events (short) or the 8 rates "
                          "10-2000/s with 30 s or 2000 events each (full)")

@@ -709,8 +709,10 @@ PinnedBuf pool_get(tpc_track_ctx* ctx, size_t need)
                 return b;
             }
     }
+    // twice the size asked for (at least 4 MB): later, larger events reuse
+    // the buffer instead of pinning new host memory in the middle of a run
     PinnedBuf b;
-    const size_t cap = align_up(need + need / 4 + 4096, 1 << 20);
+    const size_t cap = align_up(std::max<size_t>(2 * need, 4u << 20), 1 << 20);
     if (cudaHostAlloc((void**)&b.p, cap, cudaHostAllocDefault) == cudaSuccess) b.cap = cap;
     else b.p = nullptr;
     return b;
