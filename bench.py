@@ -708,6 +708,9 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+REF_MAX_STEPS = 120
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -720,22 +723,26 @@ def run_reference(args):
     sub = ev.select_sectors(sectors)
     for _ in range(args.warmup if args.warmup < 1 else 1):
         oracle.track_event(sub.select_sectors([0]))
+    # one sector per step (~0.5 s of one core); at most REF_MAX_STEPS steps so
+    # that the arm stays within about a minute whatever --steps asks for
+    steps = min(args.steps, REF_MAX_STEPS)
     t0 = time.perf_counter()
     n_total = 0
-    for i in range(args.steps):
+    for i in range(steps):
         s = sub.select_sectors([sectors[i % len(sectors)]])
         oracle.track_event(s)
         n_total += s.n
     dt = time.perf_counter() - t0
     v = n_total / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": steps, "steps_requested": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "clusters_per_event": ev.n,
                        "sample": "each step tracks one of sectors 0, 9, 18, 27 of the event"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} single sectors of the central event, "
+                             "sample": f"{steps} single sectors of the central event, "
                                        "single-threaded"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -744,7 +751,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-served", action="store_true")
