@@ -499,6 +499,81 @@ def pileup_section(tp, torch, synth, stream, reps=3, n_served=4):
     return out
 
 
+def calib_loop(tp, ctx, ev, geom, bz, n_cl, n_events, every_n, inline, depth=4):
+    """Served stream with the chi^2-scale side task: `depth` events in
+    flight; each finished event's tracks are added to the fit; a finished
+    fit is fed back with tpc_track_set_params.  inline=True waits for every
+    fit where it starts (the task run inside the event loop, Fig. 4);
+    inline=False only checks at every event (Sect. 5.1, Fig. 5)."""
+    from collections import deque
+    cal = tp.Chi2Calib(every_n, 3.0, 2)
+    lat, gaps, fits, q = [], [], [], deque()
+    sigma_of = {0: float(tp.tpc_track_get_params(ctx)[0].meas_sigma_y)}
+    added = 0
+
+    def feed_back(f):
+        fits.append(f)
+        s = sigma_of[f["params_version"]] * math.sqrt(f["scale2"])
+        p = tp.tpc_track_default_params()
+        p.meas_sigma_y = p.meas_sigma_z = s
+        _, ver = tp.tpc_track_set_params(ctx, p)
+        sigma_of[ver] = float(p.meas_sigma_y)
+    try:
+        t0 = t_prev = time.perf_counter()
+        for i in range(n_events + depth - 1):
+            if i < n_events:
+                q.append((tp.tpc_track_submit(ctx, ev, geom, bz), time.perf_counter()))
+            if len(q) < depth and i < n_events:
+                continue
+            tk, ts = q.popleft()
+            tr = tp.tpc_track_poll(ctx, tk, 60_000_000, copy=False)
+            if tr is None:
+                raise TimeoutError("ticket not done after 60 s")
+            _, ver = tp.tpc_track_ticket_params(ctx, tk)
+            cal.add(tr.chi2, tr.ndf, ver)
+            added += 1
+            tp.tpc_track_release(ctx, tk)
+            now = time.perf_counter()
+            lat.append(now - ts)
+            gaps.append(now - t_prev)
+            t_prev = now
+            if inline and added % every_n == 0:
+                f = cal.poll(-1)
+                if f is not None:
+                    feed_back(f)
+            elif not inline:
+                f = cal.poll(0)
+                if f is not None:
+                    feed_back(f)
+        span = time.perf_counter() - t0
+        st = cal.stats()
+    finally:
+        cal.close()
+    return {"events": n_events, "fits": len(fits),
+            "fit_ms_max": st["max_task_ms"], "fit_ms_mean": st["busy_ms"] / max(1, st["finished"]),
+            "tracks_per_fit": fits[0]["n_tracks"] if fits else 0,
+            "clusters_per_s": n_events * n_cl / span,
+            "latency_p50_ms": percentile(lat, 50) * 1e3, "latency_p99_ms": percentile(lat, 99) * 1e3,
+            "latency_max_ms": max(lat) * 1e3, "max_gap_between_events_ms": max(gaps) * 1e3,
+            "sigma_after": sigma_of[max(sigma_of)]}
+
+
+def async_section(tp, torch, host_ev, geom, bz, n_cl, n_events=600, every_n=100):
+    """The side task inline vs asynchronous on the same served stream."""
+    out = {"workload": f"{n_events} central events served back to back (4 in flight); "
+                       f"chi^2-scale fit of the tracks of every {every_n} events, fed back "
+                       "as the cluster error"}
+    for mode in ("inline", "async"):
+        ctx = served_ctx(tp, [host_ev], geom, bz, n_cl)
+        try:
+            calib_loop(tp, ctx, host_ev, geom, bz, n_cl, 2 * every_n, every_n, mode == "inline")
+            out[mode] = calib_loop(tp, ctx, host_ev, geom, bz, n_cl, n_events, every_n,
+                                   mode == "inline")
+        finally:
+            tp.tpc_track_destroy(ctx)
+    return out
+
+
 def traffic_for(kernel: str, counters: dict):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current source of that kernel."""
@@ -669,6 +744,13 @@ def run_ours(args):
         except Exception as e:  # reported, the bench line still goes out
             pileup = {"error": repr(e)}
 
+    side_task = None
+    if not args.no_served and rank == 0:
+        try:
+            side_task = async_section(tp, torch, hc, geom, bz, n)
+        except Exception as e:  # reported, the bench line still goes out
+            side_task = {"error": repr(e)}
+
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(ev)
@@ -701,6 +783,7 @@ def run_ours(args):
             "kernels_ms": {k: v[0] / v[1] for k, v in ktimes.items()},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "cpu_baseline": cpu, "served": served, "batched": batched, "pileup": pileup,
+            "side_task": side_task,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -28,8 +28,9 @@
  *   - Every call returns a status code; nothing aborts or prints.  On error
  *     tpc_track_last_error() gives a one-line reason.
  *   - Thread safety: one context is driven by one host thread at a time,
- *     except tpc_track_submit, tpc_track_poll, tpc_track_release and
- *     tpc_track_last_error, which may be called from several threads at
+ *     except tpc_track_submit, tpc_track_poll, tpc_track_release,
+ *     tpc_track_set_params, tpc_track_get_params, tpc_track_ticket_params
+ *     and tpc_track_last_error, which may be called from several threads at
  *     once (a submitting thread and a polling thread, say).
  */
 #ifndef TPCTRACK_H
@@ -177,6 +178,100 @@ int tpc_track_poll(tpc_track_ctx* ctx, uint64_t ticket, int timeout_us, tpc_trac
 
 /* Free the host memory of a finished ticket. */
 int tpc_track_release(tpc_track_ctx* ctx, uint64_t ticket);
+
+/* Event-synchronous parameter updates (Sect. 3, item 2; Sect. 5.2, 5.3: new
+ * calibration data enter the chain in step with an event, and it is known
+ * which event was processed with which data).
+ *
+ * tpc_track_set_params makes *p the context's parameter set (the same range
+ * checks as tpc_track_create; TPC_EINVAL leaves the current set).  Every
+ * event submitted afterwards, and every later direct call, uses it; events
+ * already submitted keep the set they were submitted with, and no launch mixes
+ * two sets.  *first_ticket (may be NULL) receives the first ticket tracked
+ * with the new set, *version (may be NULL) its version number (the count of
+ * tpc_track_set_params calls on the context; 0 is the creation set).
+ * tpc_track_get_params returns the current set and its version.
+ * tpc_track_ticket_params returns the set and version a submitted ticket is
+ * tracked with (until the ticket is released), for reproducing the event. */
+int tpc_track_set_params(tpc_track_ctx* ctx, const tpc_track_params* p, uint64_t* first_ticket,
+                         uint64_t* version);
+int tpc_track_get_params(tpc_track_ctx* ctx, tpc_track_params* p, uint64_t* version);
+int tpc_track_ticket_params(tpc_track_ctx* ctx, uint64_t ticket, tpc_track_params* p,
+                            uint64_t* version);
+
+/* Asynchronous long-running side tasks (Sect. 3, item 4; Sect. 5.1).
+ *
+ * A runner owns one host thread.  It calls init(user) once on that thread
+ * before any job (init may be NULL; a non-zero return is returned by
+ * tpc_async_create, which then creates nothing), then run(user, job, &result)
+ * for every started job, one at a time, in start order.  The event loop
+ * starts a job while processing an event and checks at every event whether a
+ * job has finished, so no event waits for the job (the event queue does not
+ * fill up behind a long fit: Fig. 4 against Fig. 5).
+ *   tpc_async_create   max_unfinished (1..1024) bounds the jobs started and
+ *                      not yet finished; drop (may be NULL) is called by
+ *                      tpc_async_destroy with (user, job, NULL) for every job
+ *                      never run and (user, NULL, result) for every result
+ *                      never polled, so that their memory can be freed.
+ *   tpc_async_start    queues job (owned by the runner until run returns)
+ *                      and never waits: TPC_EBUSY when max_unfinished jobs
+ *                      are unfinished.  *task (may be NULL) gets its id
+ *                      (1, 2, ... in start order).
+ *   tpc_async_poll     the oldest finished job not yet polled: its id, the
+ *                      result pointer run produced (now the caller's) and the
+ *                      status run returned.  Waits up to timeout_us (0 = just
+ *                      test; < 0 = while any job is queued or running).
+ *                      TPC_EBUSY if none has finished.
+ *   tpc_async_destroy  lets the running job finish (jobs are not cancelled),
+ *                      runs no queued job, joins the thread.
+ * Every function may be called from any thread; one runner's jobs never run
+ * concurrently with each other. */
+typedef struct tpc_async tpc_async;
+typedef int (*tpc_async_init_fn)(void* user);
+typedef int (*tpc_async_run_fn)(void* user, void* job, void** result);
+typedef void (*tpc_async_drop_fn)(void* user, void* job, void* result);
+typedef struct {
+    int64_t started, finished, refused;  /* refused: tpc_async_start returned TPC_EBUSY */
+    int64_t queued, running, unpolled;   /* now */
+    double busy_ms, max_task_ms;         /* summed and longest run time of finished jobs */
+} tpc_async_stats;
+int tpc_async_create(tpc_async_init_fn init, tpc_async_run_fn run, tpc_async_drop_fn drop,
+                     void* user, int max_unfinished, tpc_async** out);
+int tpc_async_start(tpc_async* a, void* job, uint64_t* task);
+int tpc_async_poll(tpc_async* a, int timeout_us, uint64_t* task, void** result, int* task_status);
+int tpc_async_get_stats(tpc_async* a, tpc_async_stats* out);
+void tpc_async_destroy(tpc_async* a);
+
+/* Built-in accumulate-then-fit side task: the chi^2 scale of the tracks.
+ * tpc_chi2_calib_add (called once per event, never waits) appends the chi2
+ * and ndf of the event's tracks with ndf > 0 (of *t it reads n_tracks, chi2
+ * and ndf only); once every_n_events events
+ * tracked with one parameter version have been added it hands them to its
+ * runner's thread as one fit (if max_unfinished fits are still unfinished it
+ * keeps accumulating and tries again at the next event).  Adding an event of
+ * another parameter version drops the partial accumulation: every fit covers
+ * events tracked with one parameter set.  Events are numbered 0, 1, ... in
+ * the order added.
+ * The fit: s2 = sum chi2 / sum ndf over all tracks; then repeatedly keep the
+ * tracks with chi2 <= trim * s2 * ndf and set s2 = sum chi2 / sum ndf over the
+ * kept ones, until the kept set repeats (at most 100 rounds).  s2 estimates
+ * (true cluster error / assumed cluster error)^2 when the assumed error is
+ * wrong, so sigma * sqrt(s2) is the corrected cluster error to feed back
+ * with tpc_track_set_params.  trim > 1.  A fit of no track gives s2 = NaN.
+ * tpc_chi2_calib_poll returns the oldest finished fit as tpc_async_poll does. */
+typedef struct tpc_chi2_calib tpc_chi2_calib;
+typedef struct {
+    uint64_t first_event, last_event, n_events, params_version;
+    int64_t n_tracks, n_kept;
+    int32_t n_iter, pad;
+    double scale2;
+} tpc_chi2_fit;
+int tpc_chi2_calib_create(int every_n_events, double trim, int max_unfinished,
+                          tpc_chi2_calib** out);
+int tpc_chi2_calib_add(tpc_chi2_calib* c, const tpc_tracks* t, uint64_t params_version);
+int tpc_chi2_calib_poll(tpc_chi2_calib* c, int timeout_us, tpc_chi2_fit* out);
+int tpc_chi2_calib_stats(tpc_chi2_calib* c, tpc_async_stats* out);
+void tpc_chi2_calib_destroy(tpc_chi2_calib* c);
 
 /* Per-launch counters of the last tpc_track_results (for the byte model
  * of the benchmark and for tests).  n_chain_hits is the number of hits on

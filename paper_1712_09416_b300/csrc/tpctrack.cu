@@ -135,6 +135,8 @@ struct Request {
     std::vector<float> row_x;
     tpc_geometry geom;
     float bz;
+    tpc_track_params prm;   // the parameter set current when the event was submitted
+    uint64_t prm_version;
     std::chrono::steady_clock::time_point t_submit;
 };
 
@@ -148,6 +150,8 @@ struct PinnedBuf {
 
 struct TicketResult {
     int status = TPC_EBUSY;
+    tpc_track_params prm{};  // the parameter set the event is tracked with
+    uint64_t prm_version = 0;
     PinnedBuf buf;
     tpc_tracks view{};
 };
@@ -170,6 +174,7 @@ struct tpc_track_ctx {
     std::vector<tpc::PinnedBuf> pool;  // free pinned result buffers
     bool stop = false;
     uint64_t next_ticket = 1;
+    uint64_t prm_version = 0;  // bumped by every tpc_track_set_params (cfg.params under mu)
     std::atomic<int> direct_busy{0};
     bool trace = false;  // TPC_TRACE=1: one stderr line per served launch
     bool graphs = true;  // TPC_NO_GRAPH=1: launch the kernels one by one
@@ -406,7 +411,7 @@ int launch_graph(tpc_track_ctx* ctx, Slot& s, const Launch& L)
 
 // Enqueue the whole device pipeline of one launch on the slot's stream.
 int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const tpc_geometry* g,
-            float bz)
+            float bz, const tpc_track_params& P)
 {
     if (n_ev < 1 || n_ev > s.caps.e || n_ev > kMaxEventsPerLaunch)
         return fail(ctx, TPC_EINVAL, "n_ev out of range (1.." + std::to_string(s.caps.e) + ")");
@@ -481,7 +486,6 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.tan_half = tanf(g->half_angle_rad);
     L.z_max = g->z_max;
     L.kB = (float)(kKappa * (double)bz);
-    const tpc_track_params& P = ctx->cfg.params;
     L.sy2 = P.meas_sigma_y * P.meas_sigma_y;
     L.sz2 = P.meas_sigma_z * P.meas_sigma_z;
     L.slope_win_y = P.slope_win_y;
@@ -859,11 +863,11 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* 
             std::vector<int32_t> rh((size_t)R);
             int32_t count = 0;
             for (auto& o : order)
-                if (tl[o.second].chain_len >= ctx->cfg.params.min_chain) ++count;
+                if (tl[o.second].chain_len >= s.info.L.min_chain) ++count;
             put(&count, 4);
             for (auto& o : order) {
                 const TrackletHdr& H = tl[o.second];
-                if (H.chain_len < ctx->cfg.params.min_chain) continue;
+                if (H.chain_len < s.info.L.min_chain) continue;
                 tpc_dump_tracklet D;
                 std::memset(&D, 0, sizeof(D));
                 D.start_cid = o.first;
@@ -920,7 +924,8 @@ void worker(tpc_track_ctx* ctx, Slot* s)
                                       q.geom.n_sectors_phi == b0.geom.n_sectors_phi &&
                                       q.geom.split_z == b0.geom.split_z &&
                                       q.geom.half_angle_rad == b0.geom.half_angle_rad &&
-                                      q.geom.z_max == b0.geom.z_max && q.row_x == b0.row_x;
+                                      q.geom.z_max == b0.geom.z_max && q.row_x == b0.row_x &&
+                                      q.prm_version == b0.prm_version;
                     if (!same || sum + q.ev.n > s->caps.n) break;
                 }
                 sum += q.ev.n;
@@ -935,7 +940,7 @@ void worker(tpc_track_ctx* ctx, Slot* s)
         const auto t0 = std::chrono::steady_clock::now();
         std::vector<std::unique_ptr<TicketResult>> done(batch.size());
         for (auto& d : done) d = std::make_unique<TicketResult>();
-        int rc = enqueue(ctx, *s, (int)evs.size(), evs.data(), &g, batch.front().bz);
+        int rc = enqueue(ctx, *s, (int)evs.size(), evs.data(), &g, batch.front().bz, batch.front().prm);
         const auto t1 = std::chrono::steady_clock::now();
         if (rc == TPC_OK) rc = collect_to_tickets(ctx, *s, done);
         const auto t2 = std::chrono::steady_clock::now();
@@ -953,6 +958,8 @@ void worker(tpc_track_ctx* ctx, Slot* s)
         for (size_t i = 0; i < batch.size(); ++i) {
             auto it = ctx->results.find(batch[i].ticket);
             if (it == ctx->results.end()) continue;
+            done[i]->prm = it->second->prm;
+            done[i]->prm_version = it->second->prm_version;
             std::swap(*it->second, *done[i]);
         }
         if (ctx->trace) {
@@ -995,6 +1002,15 @@ void tpc_track_default_params(tpc_track_params* p)
     p->seed_var_q = 100.0f;
 }
 
+static bool params_ok(const tpc_track_params& P)
+{
+    return P.meas_sigma_y > 0 && P.meas_sigma_z > 0 && std::isfinite(P.meas_sigma_y) &&
+           std::isfinite(P.meas_sigma_z) && P.d_max >= 0 && P.chi2_hit > 0 && P.max_gap >= 1 &&
+           P.min_chain >= 2 && P.min_tracklet_hits >= 1 && P.min_track_hits >= 1 &&
+           P.sin_max > 0 && P.sin_max < 1 && P.seed_var_s > 0 && P.seed_var_t > 0 &&
+           P.seed_var_q > 0;
+}
+
 int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out)
 {
     if (!out) return TPC_EINVAL;
@@ -1005,12 +1021,7 @@ int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out)
         cfg->max_rows < 0 || cfg->max_rows > kMaxRows || cfg->max_events_per_launch < 0 ||
         cfg->max_events_per_launch > kMaxEventsPerLaunch)
         return TPC_EINVAL;
-    const tpc_track_params& P = cfg->params;
-    if (!(P.meas_sigma_y > 0) || !(P.meas_sigma_z > 0) || !(P.d_max >= 0) || !(P.chi2_hit > 0) ||
-        P.max_gap < 1 || P.min_chain < 2 || P.min_tracklet_hits < 1 || P.min_track_hits < 1 ||
-        !(P.sin_max > 0 && P.sin_max < 1) || !(P.seed_var_s > 0) || !(P.seed_var_t > 0) ||
-        !(P.seed_var_q > 0))
-        return TPC_EINVAL;
+    if (!params_ok(cfg->params)) return TPC_EINVAL;
     auto ctx = std::make_unique<tpc_track_ctx>();
     ctx->cfg = *cfg;
     const char* tr = std::getenv("TPC_TRACE");
@@ -1062,7 +1073,12 @@ int tpc_track_launch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev, const
     Slot& s = *ctx->slots[0];
     s.info.pending = false;  // results of an uncollected launch are dropped
     if (s.prof && s.prof_used > 60000) return fail(ctx, TPC_EINVAL, "profiling buffer full");
-    return enqueue(ctx, s, n_ev, ev, geom, bz);
+    tpc_track_params P;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        P = ctx->cfg.params;
+    }
+    return enqueue(ctx, s, n_ev, ev, geom, bz, P);
 }
 
 int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs)
@@ -1120,8 +1136,13 @@ int tpc_track_submit(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geome
     q.row_x.assign(geom->row_x, geom->row_x + geom->n_rows);
     q.geom = *geom;
     q.bz = bz;
+    q.prm = ctx->cfg.params;
+    q.prm_version = ctx->prm_version;
     q.t_submit = std::chrono::steady_clock::now();
-    ctx->results[q.ticket] = std::make_unique<TicketResult>();
+    auto R = std::make_unique<TicketResult>();
+    R->prm = q.prm;
+    R->prm_version = q.prm_version;
+    ctx->results[q.ticket] = std::move(R);
     *ticket = q.ticket;
     ctx->queue.push_back(std::move(q));
     ctx->cv_req.notify_one();
@@ -1154,6 +1175,39 @@ int tpc_track_release(tpc_track_ctx* ctx, uint64_t ticket)
     gone = std::move(it->second);
     ctx->results.erase(it);
     pool_put(ctx, gone->buf);
+    return TPC_OK;
+}
+
+int tpc_track_set_params(tpc_track_ctx* ctx, const tpc_track_params* p, uint64_t* first_ticket,
+                         uint64_t* version)
+{
+    if (!ctx || !p) return TPC_EINVAL;
+    if (!params_ok(*p)) return fail(ctx, TPC_EINVAL, "parameter out of range");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->cfg.params = *p;
+    ++ctx->prm_version;
+    if (first_ticket) *first_ticket = ctx->next_ticket;
+    if (version) *version = ctx->prm_version;
+    return TPC_OK;
+}
+
+int tpc_track_get_params(tpc_track_ctx* ctx, tpc_track_params* p, uint64_t* version)
+{
+    if (!ctx || !p) return TPC_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *p = ctx->cfg.params;
+    if (version) *version = ctx->prm_version;
+    return TPC_OK;
+}
+
+int tpc_track_ticket_params(tpc_track_ctx* ctx, uint64_t ticket, tpc_track_params* p, uint64_t* version)
+{
+    if (!ctx) return TPC_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->results.find(ticket);
+    if (it == ctx->results.end()) return fail(ctx, TPC_EINVAL, "unknown ticket");
+    if (p) *p = it->second->prm;
+    if (version) *version = it->second->prm_version;
     return TPC_OK;
 }
 
@@ -1235,6 +1289,11 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     cudaSetDevice(ctx->cfg.device);
     Slot& s = *ctx->slots[0];
     const Schedule start = ctx->sched;
+    tpc_track_params P;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        P = ctx->cfg.params;
+    }
     // median over reps launches (after one warm-up) of the summed device time
     // of the named kernels under schedule S
     auto time_kernels = [&](const Schedule& S, const std::vector<std::string>& names,
@@ -1248,7 +1307,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
             s.prof_used = 0;
             s.prof_marks.clear();
             s.info.pending = false;
-            rc = enqueue(ctx, s, n_ev, ev, geom, bz);
+            rc = enqueue(ctx, s, n_ev, ev, geom, bz, P);
             if (rc == TPC_OK) rc = launch_status(ctx, s);
             if (rc != TPC_OK || r == 0) continue;
             double sum = 0.0;

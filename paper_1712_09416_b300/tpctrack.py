@@ -26,7 +26,11 @@ EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "
             "tpc_track_set_profiling", "tpc_track_kernel_times",
             "tpc_track_get_schedule", "tpc_track_set_schedule", "tpc_track_autotune",
             "tpc_track_debug_dump", "tpc_track_last_error", "tpc_track_destroy",
-            "tpc_track_links_noalloc"]
+            "tpc_track_links_noalloc", "tpc_track_set_params", "tpc_track_get_params",
+            "tpc_track_ticket_params", "tpc_async_create", "tpc_async_start", "tpc_async_poll",
+            "tpc_async_get_stats", "tpc_async_destroy", "tpc_chi2_calib_create",
+            "tpc_chi2_calib_add", "tpc_chi2_calib_poll", "tpc_chi2_calib_stats",
+            "tpc_chi2_calib_destroy"]
 
 
 class TpcError(RuntimeError):
@@ -90,6 +94,23 @@ class tpc_dump_tracklet(C.Structure):
         [("x", C.c_float), ("param", C.c_float * 5), ("cov", C.c_float * 15), ("chi2", C.c_float)]
 
 
+class tpc_async_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("started", "finished", "refused", "queued", "running",
+                                         "unpolled")] + \
+        [("busy_ms", C.c_double), ("max_task_ms", C.c_double)]
+
+
+class tpc_chi2_fit(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("first_event", "last_event", "n_events",
+                                          "params_version")] + \
+        [("n_tracks", C.c_int64), ("n_kept", C.c_int64), ("n_iter", C.c_int32), ("pad", C.c_int32),
+         ("scale2", C.c_double)]
+
+
+tpc_async_init_fn = C.CFUNCTYPE(C.c_int, C.c_void_p)
+tpc_async_run_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p))
+tpc_async_drop_fn = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
 _lib = None
 
 
@@ -134,6 +155,25 @@ def lib():
                                               C.POINTER(tpc_track_params), P, P, P]
         L.tpc_track_default_params.argtypes = [C.POINTER(tpc_track_params)]
         L.tpc_track_default_params.restype = None
+        L.tpc_track_set_params.argtypes = [P, C.POINTER(tpc_track_params), C.POINTER(C.c_uint64),
+                                           C.POINTER(C.c_uint64)]
+        L.tpc_track_get_params.argtypes = [P, C.POINTER(tpc_track_params), C.POINTER(C.c_uint64)]
+        L.tpc_track_ticket_params.argtypes = [P, C.c_uint64, C.POINTER(tpc_track_params),
+                                              C.POINTER(C.c_uint64)]
+        L.tpc_async_create.argtypes = [tpc_async_init_fn, tpc_async_run_fn, tpc_async_drop_fn, P,
+                                       C.c_int, C.POINTER(P)]
+        L.tpc_async_start.argtypes = [P, P, C.POINTER(C.c_uint64)]
+        L.tpc_async_poll.argtypes = [P, C.c_int, C.POINTER(C.c_uint64), C.POINTER(P),
+                                     C.POINTER(C.c_int)]
+        L.tpc_async_get_stats.argtypes = [P, C.POINTER(tpc_async_stats)]
+        L.tpc_async_destroy.argtypes = [P]
+        L.tpc_async_destroy.restype = None
+        L.tpc_chi2_calib_create.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(P)]
+        L.tpc_chi2_calib_add.argtypes = [P, C.POINTER(tpc_tracks), C.c_uint64]
+        L.tpc_chi2_calib_poll.argtypes = [P, C.c_int, C.POINTER(tpc_chi2_fit)]
+        L.tpc_chi2_calib_stats.argtypes = [P, C.POINTER(tpc_async_stats)]
+        L.tpc_chi2_calib_destroy.argtypes = [P]
+        L.tpc_chi2_calib_destroy.restype = None
         _lib = L
     return _lib
 
@@ -318,6 +358,144 @@ def tpc_track_kernel_times(ctx) -> dict:
     n = C.c_int()
     _check(ctx, lib().tpc_track_kernel_times(ctx, arr, 64, C.byref(n)))
     return {arr[i].name.decode(): (arr[i].total_ms, int(arr[i].launches)) for i in range(n.value)}
+
+
+def tpc_track_set_params(ctx, params: tpc_track_params) -> tuple[int, int]:
+    """New parameter set from the next submitted event on; returns
+    (first ticket tracked with it, its version)."""
+    ft, ver = C.c_uint64(), C.c_uint64()
+    _check(ctx, lib().tpc_track_set_params(ctx, C.byref(params), C.byref(ft), C.byref(ver)))
+    return ft.value, ver.value
+
+
+def tpc_track_get_params(ctx) -> tuple[tpc_track_params, int]:
+    p, ver = tpc_track_params(), C.c_uint64()
+    _check(ctx, lib().tpc_track_get_params(ctx, C.byref(p), C.byref(ver)))
+    return p, ver.value
+
+
+def tpc_track_ticket_params(ctx, ticket: int) -> tuple[tpc_track_params, int]:
+    p, ver = tpc_track_params(), C.c_uint64()
+    _check(ctx, lib().tpc_track_ticket_params(ctx, ticket, C.byref(p), C.byref(ver)))
+    return p, ver.value
+
+
+def _stats_dict(s: tpc_async_stats) -> dict:
+    return {k: (float if k.endswith("_ms") else int)(getattr(s, k)) for k, _ in s._fields_}
+
+
+class AsyncRunner:
+    """A tpc_async runner whose jobs are Python callables (for tests and
+    host-side tools; the callables run on the runner's thread)."""
+
+    def __init__(self, max_unfinished: int = 1, init=None):
+        self._jobs: dict[int, object] = {}
+        self._results: dict[int, object] = {}
+        self._n = 0
+        self._init_py = init
+
+        def _init(_user):
+            return int(self._init_py()) if self._init_py else TPC_OK
+
+        def _run(_user, job, result):
+            k = int(job)
+            fn = self._jobs.pop(k)
+            try:
+                self._results[k] = fn()
+                rc = TPC_OK
+            except Exception as e:  # noqa: BLE001 - the job's failure becomes its status
+                self._results[k] = e
+                rc = TPC_EINVAL
+            result[0] = k
+            return rc
+
+        def _drop(_user, job, result):
+            if job:
+                self._jobs.pop(int(job), None)
+            if result:
+                self._results.pop(int(result), None)
+        self._cb = (tpc_async_init_fn(_init), tpc_async_run_fn(_run), tpc_async_drop_fn(_drop))
+        h = C.c_void_p()
+        rc = lib().tpc_async_create(*self._cb, None, max_unfinished, C.byref(h))
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_async_create")
+        self.handle = h
+
+    def start(self, fn) -> int | None:
+        """Queue fn (never waits); its task id, or None if the runner is full."""
+        self._n += 1
+        self._jobs[self._n] = fn
+        t = C.c_uint64()
+        rc = lib().tpc_async_start(self.handle, C.c_void_p(self._n), C.byref(t))
+        if rc == TPC_EBUSY:
+            del self._jobs[self._n]
+            return None
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_async_start")
+        return t.value
+
+    def poll(self, timeout_us: int = 0):
+        """(task id, status, value) of the oldest finished job, or None."""
+        t, r, st = C.c_uint64(), C.c_void_p(), C.c_int()
+        rc = lib().tpc_async_poll(self.handle, timeout_us, C.byref(t), C.byref(r), C.byref(st))
+        if rc == TPC_EBUSY:
+            return None
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_async_poll")
+        return t.value, st.value, self._results.pop(int(r.value), None)
+
+    def stats(self) -> dict:
+        s = tpc_async_stats()
+        lib().tpc_async_get_stats(self.handle, C.byref(s))
+        return _stats_dict(s)
+
+    def close(self):
+        if self.handle:
+            lib().tpc_async_destroy(self.handle)
+            self.handle = None
+
+
+class Chi2Calib:
+    """The built-in accumulate-then-fit side task (tpc_chi2_calib_*)."""
+
+    def __init__(self, every_n_events: int, trim: float = 3.0, max_unfinished: int = 2):
+        h = C.c_void_p()
+        rc = lib().tpc_chi2_calib_create(every_n_events, trim, max_unfinished, C.byref(h))
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_chi2_calib_create")
+        self.handle = h
+
+    def add(self, chi2: np.ndarray, ndf: np.ndarray, params_version: int = 0):
+        """Accumulate one event's tracks (chi2 float32, ndf int32)."""
+        c = np.ascontiguousarray(chi2, np.float32)
+        d = np.ascontiguousarray(ndf, np.int32)
+        t = tpc_tracks()
+        t.n_tracks = len(c)
+        t.chi2 = c.ctypes.data_as(C.POINTER(C.c_float))
+        t.ndf = d.ctypes.data_as(C.POINTER(C.c_int32))
+        rc = lib().tpc_chi2_calib_add(self.handle, C.byref(t), params_version)
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_chi2_calib_add")
+
+    def poll(self, timeout_us: int = 0) -> dict | None:
+        f = tpc_chi2_fit()
+        rc = lib().tpc_chi2_calib_poll(self.handle, timeout_us, C.byref(f))
+        if rc == TPC_EBUSY:
+            return None
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_chi2_calib_poll")
+        return {k: (float(getattr(f, k)) if k == "scale2" else int(getattr(f, k)))
+                for k, _ in f._fields_ if k != "pad"}
+
+    def stats(self) -> dict:
+        s = tpc_async_stats()
+        lib().tpc_chi2_calib_stats(self.handle, C.byref(s))
+        return _stats_dict(s)
+
+    def close(self):
+        if self.handle:
+            lib().tpc_chi2_calib_destroy(self.handle)
+            self.handle = None
 
 
 def _schedule_dict(s: tpc_track_schedule) -> dict:

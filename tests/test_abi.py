@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "tpctrack.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(tpc_track_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(tpc_\w+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +70,8 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
         pytest.skip("gcc not available")
     recs = [tpctrack.tpc_geometry, tpctrack.tpc_clusters, tpctrack.tpc_tracks,
             tpctrack.tpc_track_params, tpctrack.tpc_track_config, tpctrack.tpc_track_counters,
-            tpctrack.tpc_kernel_time, tpctrack.tpc_track_schedule, tpctrack.tpc_dump_tracklet]
+            tpctrack.tpc_kernel_time, tpctrack.tpc_track_schedule, tpctrack.tpc_dump_tracklet,
+            tpctrack.tpc_async_stats, tpctrack.tpc_chi2_fit]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tpctrack.h"', 'int main(void) {']
     for r in recs:
         n = r.__name__
