@@ -425,6 +425,33 @@ def batched_vs_sequential(tp, torch, synth, stream, n_events=64, reps=3):
                 tp.tpc_track_results(ctx_1, 1, copy=False)
                 n_tracks_s += tp.tpc_track_get_counters(ctx_1)["n_tracks"]
         t_seq = (time.perf_counter() - t0) / reps
+        # the same single-event launches spread over 4 streams (concurrent
+        # kernels of up to 4 events), every event's results collected
+        ctx_4 = tp.tpc_track_create(max(e.n for e in evs) + 65536, max_events_per_launch=1,
+                                    max_events_in_flight=4, cuda_stream=stream.cuda_stream)
+        tp.tpc_track_set_schedule(ctx_4, **{k: v for k, v in tp.tpc_track_get_schedule(ctx_1).items()
+                                            if k in ("bin_blocks_per_sm", "sort_threads",
+                                                     "nb_threads", "tl_blocks_per_sm")}, streams=4)
+
+        def pipelined():
+            n_tr = 0
+            for i, c in enumerate(cs):
+                tp.tpc_track_launch(ctx_4, [c], geom, bz)
+                if i >= 3:
+                    tp.tpc_track_results(ctx_4, 1, copy=False)
+                    n_tr += tp.tpc_track_get_counters(ctx_4)["n_tracks"]
+            for _ in range(3):
+                tp.tpc_track_results(ctx_4, 1, copy=False)
+                n_tr += tp.tpc_track_get_counters(ctx_4)["n_tracks"]
+            return n_tr
+        try:
+            pipelined()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                n_tracks_p = pipelined()
+            t_pipe = (time.perf_counter() - t0) / reps
+        finally:
+            tp.tpc_track_destroy(ctx_4)
     finally:
         tp.tpc_track_destroy(ctx_b)
         tp.tpc_track_destroy(ctx_1)
@@ -434,6 +461,8 @@ def batched_vs_sequential(tp, torch, synth, stream, n_events=64, reps=3):
             "batch_ms": t_batch * 1e3, "sequential_ms": t_seq * 1e3,
             "clusters_per_s_batch": n_all / t_batch, "clusters_per_s_sequential": n_all / t_seq,
             "speedup": t_seq / t_batch, "schedule": sched,
+            "streams4_ms": t_pipe * 1e3, "clusters_per_s_streams4": n_all / t_pipe,
+            "tracks_streams4": int(n_tracks_p),
             "timing": "host wall clock around launch + results, inputs resident on the device"}
 
 
@@ -508,7 +537,8 @@ def calib_loop(tp, ctx, ev, geom, bz, n_cl, n_events, every_n, inline, depth=4):
     from collections import deque
     cal = tp.Chi2Calib(every_n, 3.0, 2)
     lat, gaps, fits, q = [], [], [], deque()
-    sigma_of = {0: float(tp.tpc_track_get_params(ctx)[0].meas_sigma_y)}
+    p0, v0 = tp.tpc_track_get_params(ctx)
+    sigma_of = {v0: float(p0.meas_sigma_y)}
     added = 0
 
     def feed_back(f):
@@ -617,9 +647,13 @@ def run_ours(args):
     # are recorded on it (torch's default stream is the legacy stream 0, for
     # which the library would create a separate non-blocking stream)
     stream = torch.cuda.Stream()
-    ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, cuda_stream=stream.cuda_stream)
+    # four slots: the autotuner may spread consecutive steps over up to four
+    # streams, so that one event's kernels overlap the next one's
+    ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, max_events_in_flight=4,
+                              cuda_stream=stream.cuda_stream)
     # launch schedule picked by the autotuner on this workload (untimed)
     schedule = tp.tpc_track_autotune(ctx, [cls[0][0]], geom, bz, reps=3)
+    n_streams = schedule["streams"]
 
     def step(i):
         tp.tpc_track_launch(ctx, [cls[i % N_COPIES][0]], geom, bz)
@@ -642,10 +676,12 @@ def run_ours(args):
         e0.record(stream)
         for i in range(args.steps):
             step(i)  # the kernel sequence replays as one CUDA graph per step
+        tp.tpc_track_join(ctx)  # the stream waits for the steps on every slot
         e1.record(stream)
         barrier()
     ms_total = e0.elapsed_time(e1)
-    tp.tpc_track_results(ctx, 1, copy=False)  # status of the last step
+    for _ in range(n_streams):  # status of the last step of every slot
+        tp.tpc_track_results(ctx, 1, copy=False)
     # per-kernel device times: the same steps again, kernels launched one by
     # one with a CUDA event after each (outside the timed region)
     tp.tpc_track_set_profiling(ctx, True)
@@ -766,8 +802,10 @@ def run_ours(args):
                              f"({N_COPIES * 12 * n / 1e6:.0f} MB) > 126 MB L2; each step also "
                              "writes ~150 MB of intermediate arrays",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "launch": "one CUDA graph per step (13 kernels); kernel times from a "
-                                 "separate pass with kernels launched one by one",
+                       "launch": f"one CUDA graph per step (13 kernels); consecutive steps "
+                                 f"spread over {n_streams} stream(s) so that their kernels run "
+                                 "concurrently (autotuned); kernel times from a separate pass "
+                                 "with kernels launched one by one on one stream",
                        "schedule": schedule,
                        "tracks_per_event": counters["n_tracks"],
                        "tracklets_per_event": counters["n_tracklets"]},
@@ -834,7 +872,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-served", action="store_true")

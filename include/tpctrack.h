@@ -150,15 +150,31 @@ int tpc_track_event(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geomet
 int tpc_track_batch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
                     const tpc_geometry* geom, float bz_tesla, tpc_tracks* outs);
 
-/* Asynchronous form of tpc_track_batch: enqueue the device pipeline on the
- * context's stream and return.  With host inputs the copies are enqueued
- * too (the inputs must stay valid until tpc_track_results).  The tracks
- * stay in device memory until tpc_track_results, which waits, checks the
- * device status and copies them out.  A launch with results still pending
- * first discards them. */
+/* Asynchronous form of tpc_track_batch: enqueue the device pipeline and
+ * return.  With host inputs the copies are enqueued too (the inputs must
+ * stay valid until tpc_track_results).  The tracks stay in device memory
+ * until tpc_track_results, which waits for the oldest launch not yet
+ * collected, checks its device status and copies its tracks out.
+ * With the schedule's streams = 1 (the default) every launch runs on the
+ * context's stream and a launch first discards the results of a pending
+ * one.  With streams = K > 1, consecutive launches go to K slots in turn,
+ * each on a stream of its own, so that the kernels of up to K launches run
+ * concurrently (Sect. 4.2: several different kernels in parallel); each
+ * launch starts after the work enqueued on the context's stream before the
+ * call (inputs written there are seen), a launch discards the uncollected
+ * results of the launch K before it (same slot), and the context's stream
+ * does not wait for the launches until tpc_track_join.  While profiling is on
+ * (tpc_track_set_profiling), launches run one at a time on the context's
+ * stream.  tpc_track_batch drops every uncollected launch first. */
 int tpc_track_launch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
                      const tpc_geometry* geom, float bz_tesla);
 int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs);
+
+/* Make the context's stream wait for every launch enqueued so far (on all
+ * slots); never blocks the host.  Work the caller enqueues on the context's
+ * stream afterwards (a timing event, a copy of inputs into reused buffers)
+ * runs after those launches. */
+int tpc_track_join(tpc_track_ctx* ctx);
 
 /* Served form: queue one event.  Every slot (a device arena, all of them
  * allocated at creation within mem_budget) has a worker thread that takes
@@ -306,11 +322,15 @@ int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, in
  *   sort_threads       threads of a row-sort block (256 or 512)
  *   nb_threads         threads of a neighbour-finder block (64, 128 or 256)
  *   tl_blocks_per_sm   persistent constructor blocks per SM (1..tl_max_per_sm)
+ *   streams            slots that consecutive direct launches go to in turn,
+ *                      each on its own stream (1..max_streams, the context's
+ *                      max_events_in_flight; see tpc_track_launch)
  * tpc_track_set_schedule rejects other values with TPC_EINVAL and returns
  * TPC_EBUSY while the context serves submitted events. */
 typedef struct {
     int n_sm, tl_max_per_sm;
     int bin_blocks_per_sm, sort_threads, nb_threads, tl_blocks_per_sm;
+    int max_streams, streams;
 } tpc_track_schedule;
 int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out);
 int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);
@@ -319,7 +339,10 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);
  * tpc_track_batch) with each candidate value of every schedule field, reps
  * times each (1..50), times the kernel that the field shapes with CUDA
  * events, and keeps the fastest value per field (fields shape different
- * kernels, so they are tuned one after the other).  Writes the chosen
+ * kernels, so they are tuned one after the other).  Last it times rounds of
+ * 4K back-to-back launches spread over K = 1 .. min(4, max_streams) streams
+ * (from the context's stream to tpc_track_join) and takes the K with the
+ * shortest time per launch (a larger K must win by 2%).  Writes the chosen
  * schedule to *out (may be NULL) and makes it the context's schedule.  The
  * results of the tuning launches are discarded.  Same errors as
  * tpc_track_batch, TPC_EBUSY while serving submitted events. */

@@ -118,8 +118,15 @@ struct Slot {
     size_t prof_last = 0;
     Counters* cnt_host = nullptr;
     HostOut out;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // the stream of the slot's current launch
     bool own_stream = false;
+    // home: the slot's stream for served launches and single-stream direct
+    // launches (the context's stream for slot 0); pipe: its stream for
+    // direct launches spread over several slots (a stream of its own, also
+    // for slot 0)
+    cudaStream_t home = nullptr, pipe = nullptr;
+    bool own_pipe = false;
+    bool launched = false;  // done_ev has been recorded
     cudaEvent_t done_ev = nullptr;
     LaunchInfo info;
     std::vector<tpc_tracks> tracks;  // per event of the last results
@@ -179,6 +186,13 @@ struct tpc_track_ctx {
     bool trace = false;  // TPC_TRACE=1: one stderr line per served launch
     bool graphs = true;  // TPC_NO_GRAPH=1: launch the kernels one by one
     tpc::Schedule sched;
+    // direct launches: spread over `streams` slots in turn; the launches not
+    // yet collected, oldest first
+    int streams = 1;
+    int next_slot = 0;
+    int last_slot = 0;  // slot of the last collected launch
+    std::deque<int> direct;
+    cudaEvent_t fork_ev = nullptr;
 };
 
 namespace tpc {
@@ -309,7 +323,7 @@ int alloc_slot(tpc_track_ctx* ctx, Slot& s)
 
 void free_slot(Slot& s)
 {
-    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.home) cudaStreamSynchronize(s.home);
     if (s.dev) cudaFree(s.dev);
     for (int i = 0; i < 2; ++i) {
         if (s.desc_ring[i]) cudaFreeHost(s.desc_ring[i]);
@@ -324,7 +338,9 @@ void free_slot(Slot& s)
         if (p) cudaFreeHost(p);
     if (s.done_ev) cudaEventDestroy(s.done_ev);
     if (s.graph) cudaGraphExecDestroy(s.graph);
-    if (s.own_stream && s.stream) cudaStreamDestroy(s.stream);
+    if (s.pipe) cudaStreamSynchronize(s.pipe);
+    if (s.own_pipe && s.pipe) cudaStreamDestroy(s.pipe);
+    if (s.own_stream && s.home) cudaStreamDestroy(s.home);
     s = Slot();
 }
 
@@ -594,6 +610,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     CUDA_TRY(ctx, cudaGetLastError());
     CUDA_TRY(ctx, cudaMemcpyAsync(s.cnt_host, L.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s.stream));
     CUDA_TRY(ctx, cudaEventRecord(s.done_ev, s.stream));
+    s.launched = true;
     I.pending = true;
     return TPC_OK;
 }
@@ -903,6 +920,14 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* 
     return TPC_OK;
 }
 
+// Make st the slot's stream, ordered after the slot's previous launch.
+int use_stream(tpc_track_ctx* ctx, Slot& s, cudaStream_t st)
+{
+    if (s.stream != st && s.launched) CUDA_TRY(ctx, cudaStreamWaitEvent(st, s.done_ev, 0));
+    s.stream = st;
+    return TPC_OK;
+}
+
 // --------------------------------------------------------------------------
 // served form: one worker per slot pulls what fits into its next launch
 // --------------------------------------------------------------------------
@@ -1054,11 +1079,22 @@ int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out)
             } else {
                 rc = TPC_ECUDA;
             }
+            s->home = s->pipe = s->stream;
+            if (rc == TPC_OK && s->id == 0) {
+                if (cudaStreamCreateWithFlags(&s->pipe, cudaStreamNonBlocking) == cudaSuccess)
+                    s->own_pipe = true;
+                else
+                    rc = TPC_ECUDA;
+            }
         }
         if (rc != TPC_OK) {
             for (auto& t : ctx->slots) free_slot(*t);
             return rc;
         }
+    }
+    if (cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+        for (auto& t : ctx->slots) free_slot(*t);
+        return TPC_ECUDA;
     }
     *out = ctx.release();
     return TPC_OK;
@@ -1070,22 +1106,51 @@ int tpc_track_launch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev, const
     if (!ctx) return TPC_EINVAL;
     if (!ctx->workers.empty()) return fail(ctx, TPC_EBUSY, "context is serving submitted events");
     cudaSetDevice(ctx->cfg.device);
-    Slot& s = *ctx->slots[0];
-    s.info.pending = false;  // results of an uncollected launch are dropped
-    if (s.prof && s.prof_used > 60000) return fail(ctx, TPC_EINVAL, "profiling buffer full");
+    Slot& s0 = *ctx->slots[0];
+    if (s0.prof && s0.prof_used > 60000) return fail(ctx, TPC_EINVAL, "profiling buffer full");
+    // while profiling, launches run one at a time on the context's stream
+    const int K = s0.prof ? 1 : ctx->streams;
+    const int j = K == 1 ? 0 : ctx->next_slot % K;
+    ctx->next_slot = K == 1 ? 0 : (j + 1) % K;
+    Slot& s = *ctx->slots[j];
+    // results of this slot's uncollected launch are dropped
+    s.info.pending = false;
+    ctx->direct.erase(std::remove(ctx->direct.begin(), ctx->direct.end(), j), ctx->direct.end());
+    cudaStream_t st = K == 1 ? s.home : s.pipe;
+    if (int rc = use_stream(ctx, s, st)) return rc;
+    if (st != s0.home) {  // fork: after the caller's work on the context's stream
+        CUDA_TRY(ctx, cudaEventRecord(ctx->fork_ev, s0.home));
+        CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->fork_ev, 0));
+    }
     tpc_track_params P;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         P = ctx->cfg.params;
     }
-    return enqueue(ctx, s, n_ev, ev, geom, bz, P);
+    const int rc = enqueue(ctx, s, n_ev, ev, geom, bz, P);
+    if (rc == TPC_OK) ctx->direct.push_back(j);
+    return rc;
+}
+
+int tpc_track_join(tpc_track_ctx* ctx)
+{
+    if (!ctx) return TPC_EINVAL;
+    cudaSetDevice(ctx->cfg.device);
+    cudaStream_t home = ctx->slots[0]->home;
+    for (auto& s : ctx->slots)
+        if (s->launched && s->stream != home) CUDA_TRY(ctx, cudaStreamWaitEvent(home, s->done_ev, 0));
+    return TPC_OK;
 }
 
 int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs)
 {
     if (!ctx) return TPC_EINVAL;
     cudaSetDevice(ctx->cfg.device);
-    Slot& s = *ctx->slots[0];
+    if (ctx->direct.empty()) return fail(ctx, TPC_EINVAL, "no launch pending");
+    const int j = ctx->direct.front();
+    ctx->direct.pop_front();
+    ctx->last_slot = j;
+    Slot& s = *ctx->slots[j];
     const int n_ev = s.info.n_ev;
     int rc = collect(ctx, s);
     if (outs)
@@ -1096,6 +1161,10 @@ int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs)
 int tpc_track_batch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev, const tpc_geometry* geom,
                     float bz, tpc_tracks* outs)
 {
+    if (ctx && ctx->workers.empty()) {  // uncollected direct launches are dropped
+        for (int j : ctx->direct) ctx->slots[j]->info.pending = false;
+        ctx->direct.clear();
+    }
     int rc = tpc_track_launch(ctx, n_ev, ev, geom, bz);
     if (rc != TPC_OK) {
         if (outs && ctx)
@@ -1127,8 +1196,10 @@ int tpc_track_submit(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geome
                 cudaEventSynchronize(s->done_ev);
                 s->info.pending = false;
             }
+            use_stream(ctx, *s, s->home);
             ctx->workers.emplace_back(worker, ctx, s.get());
         }
+        ctx->direct.clear();
     }
     Request q;
     q.ticket = ctx->next_ticket++;
@@ -1214,8 +1285,12 @@ int tpc_track_ticket_params(tpc_track_ctx* ctx, uint64_t ticket, tpc_track_param
 int tpc_track_set_profiling(tpc_track_ctx* ctx, int on)
 {
     if (!ctx) return TPC_EINVAL;
+    if (!ctx->workers.empty()) return fail(ctx, TPC_EBUSY, "context is serving submitted events");
+    cudaSetDevice(ctx->cfg.device);
+    for (auto& t : ctx->slots)
+        if (t->stream) CUDA_TRY(ctx, cudaStreamSynchronize(t->stream));
     Slot& s = *ctx->slots[0];
-    if (s.stream) CUDA_TRY(ctx, cudaStreamSynchronize(s.stream));
+    if (int rc = use_stream(ctx, s, s.home)) return rc;
     s.prof = on != 0;
     s.prof_used = 0;
     s.prof_marks.clear();
@@ -1260,6 +1335,8 @@ int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out)
     out->sort_threads = S.sort_threads;
     out->nb_threads = S.nb_threads;
     out->tl_blocks_per_sm = S.tl_blocks_per_sm;
+    out->max_streams = (int)ctx->slots.size();
+    out->streams = ctx->streams;
     return TPC_OK;
 }
 
@@ -1271,8 +1348,11 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* q)
     if (q->bin_blocks_per_sm < 1 || q->bin_blocks_per_sm > 32 ||
         (q->sort_threads != 256 && q->sort_threads != 512) ||
         (q->nb_threads != 64 && q->nb_threads != 128 && q->nb_threads != 256) ||
-        q->tl_blocks_per_sm < 1 || q->tl_blocks_per_sm > S.tl_max_per_sm)
+        q->tl_blocks_per_sm < 1 || q->tl_blocks_per_sm > S.tl_max_per_sm || q->streams < 1 ||
+        q->streams > (int)ctx->slots.size())
         return fail(ctx, TPC_EINVAL, "schedule value out of range");
+    ctx->streams = q->streams;
+    ctx->next_slot = 0;
     ctx->sched.bin_blocks_per_sm = q->bin_blocks_per_sm;
     ctx->sched.sort_threads = q->sort_threads;
     ctx->sched.nb_threads = q->nb_threads;
@@ -1287,7 +1367,12 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     if (!ctx->workers.empty()) return fail(ctx, TPC_EBUSY, "context is serving submitted events");
     if (reps < 1 || reps > 50) return fail(ctx, TPC_EINVAL, "reps out of range (1..50)");
     cudaSetDevice(ctx->cfg.device);
+    for (auto& t : ctx->slots)
+        if (t->stream) CUDA_TRY(ctx, cudaStreamSynchronize(t->stream));
+    ctx->direct.clear();
+    for (auto& t : ctx->slots) t->info.pending = false;
     Slot& s = *ctx->slots[0];
+    if (int rc = use_stream(ctx, s, s.home)) return rc;
     const Schedule start = ctx->sched;
     tpc_track_params P;
     {
@@ -1360,24 +1445,74 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     if (!rc) rc = tune(&Schedule::bin_blocks_per_sm, {2, 4, 8, 16}, {"k_count", "k_scatter"});
     if (rc) return rc;
     ctx->sched = best;
-    s.info.done = false;  // the tuning launches' results are not offered
+    // streams: rounds of 4 launches per stream spread over K slots, timed on
+    // the context's stream from the first fork to the join; a larger K must
+    // win by 2% to be taken
+    const int kmax = std::min(4, (int)ctx->slots.size());
+    if (kmax > 1) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CUDA_TRY(ctx, cudaEventCreate(&e0));
+        CUDA_TRY(ctx, cudaEventCreate(&e1));
+        double best_per = 1e30;
+        int best_k = 1;
+        for (int K = 1; K <= kmax && rc == TPC_OK; ++K) {
+            ctx->streams = K;
+            ctx->next_slot = 0;
+            std::vector<double> t;
+            for (int r = 0; r <= reps && rc == TPC_OK; ++r) {
+                const int nl = 4 * K;
+                rc = cudaEventRecord(e0, s.home) == cudaSuccess ? TPC_OK : TPC_ECUDA;
+                for (int l = 0; l < nl && rc == TPC_OK; ++l) rc = tpc_track_launch(ctx, n_ev, ev, geom, bz);
+                if (rc == TPC_OK) rc = tpc_track_join(ctx);
+                if (rc == TPC_OK && cudaEventRecord(e1, s.home) != cudaSuccess) rc = TPC_ECUDA;
+                if (rc == TPC_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = TPC_ECUDA;
+                // each slot's last launch holds the status of its launches
+                while (rc == TPC_OK && !ctx->direct.empty()) {
+                    Slot& q = *ctx->slots[ctx->direct.front()];
+                    ctx->direct.pop_front();
+                    rc = launch_status(ctx, q);
+                }
+                float ms = 0.0f;
+                if (rc == TPC_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = TPC_ECUDA;
+                if (rc == TPC_OK && r > 0) t.push_back(ms / nl);
+            }
+            if (rc != TPC_OK) break;
+            std::sort(t.begin(), t.end());
+            const double per = t[t.size() / 2];
+            if (per < best_per * (K == 1 ? 1.0 : 0.98)) {
+                best_per = per;
+                best_k = K;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->direct.clear();
+        ctx->streams = best_k;
+        ctx->next_slot = 0;
+        if (rc != TPC_OK) {
+            cudaGetLastError();
+            ctx->streams = 1;
+            return rc == TPC_ECUDA ? fail(ctx, TPC_ECUDA, "autotune stream timing") : rc;
+        }
+    }
+    for (auto& t : ctx->slots) t->info.done = false;  // the tuning launches' results are not offered
     return out ? tpc_track_get_schedule(ctx, out) : TPC_OK;
 }
 
 int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c)
 {
     if (!ctx || !c) return TPC_EINVAL;
-    *c = ctx->slots[0]->info.counters;
+    *c = ctx->slots[ctx->last_slot]->info.counters;
     return TPC_OK;
 }
 
-void* tpc_track_stream(const tpc_track_ctx* ctx) { return ctx ? (void*)ctx->slots[0]->stream : nullptr; }
+void* tpc_track_stream(const tpc_track_ctx* ctx) { return ctx ? (void*)ctx->slots[0]->home : nullptr; }
 
 int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t cap, size_t* used)
 {
     if (!ctx) return TPC_EINVAL;
     cudaSetDevice(ctx->cfg.device);
-    return dump(ctx, *ctx->slots[0], stage, host_buf, cap, used);
+    return dump(ctx, *ctx->slots[ctx->last_slot], stage, host_buf, cap, used);
 }
 
 const char* tpc_track_last_error(const tpc_track_ctx* ctx)
@@ -1401,6 +1536,7 @@ void tpc_track_destroy(tpc_track_ctx* ctx)
     for (auto& t : ctx->workers) t.join();
     cudaSetDevice(ctx->cfg.device);
     for (auto& s : ctx->slots) free_slot(*s);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     for (auto& r : ctx->results)
         if (r.second->buf.p) cudaFreeHost(r.second->buf.p);
     for (auto& b : ctx->pool) cudaFreeHost(b.p);

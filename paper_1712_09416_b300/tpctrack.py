@@ -21,7 +21,7 @@ TPC_OK, TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ECAPACITY, TPC_ETIMEOUT, TPC_EBUS
 TPC_DUMP_LINKS, TPC_DUMP_CLEAN, TPC_DUMP_STARTS, TPC_DUMP_TRACKLETS, TPC_DUMP_WEIGHTS, TPC_DUMP_SORTED = 1, 2, 3, 4, 5, 6
 
 EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "tpc_track_batch",
-            "tpc_track_launch", "tpc_track_results", "tpc_track_submit", "tpc_track_poll",
+            "tpc_track_launch", "tpc_track_results", "tpc_track_join", "tpc_track_submit", "tpc_track_poll",
             "tpc_track_release", "tpc_track_get_counters", "tpc_track_stream",
             "tpc_track_set_profiling", "tpc_track_kernel_times",
             "tpc_track_get_schedule", "tpc_track_set_schedule", "tpc_track_autotune",
@@ -85,7 +85,8 @@ class tpc_kernel_time(C.Structure):
 
 class tpc_track_schedule(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("n_sm", "tl_max_per_sm", "bin_blocks_per_sm",
-                                       "sort_threads", "nb_threads", "tl_blocks_per_sm")]
+                                       "sort_threads", "nb_threads", "tl_blocks_per_sm",
+                                       "max_streams", "streams")]
 
 
 class tpc_dump_tracklet(C.Structure):
@@ -131,6 +132,7 @@ def lib():
         L.tpc_track_launch.argtypes = [P, C.c_int, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry),
                                        C.c_float]
         L.tpc_track_results.argtypes = [P, C.POINTER(tpc_tracks)]
+        L.tpc_track_join.argtypes = [P]
         L.tpc_track_submit.argtypes = [P, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry), C.c_float,
                                        C.POINTER(C.c_uint64)]
         L.tpc_track_poll.argtypes = [P, C.c_uint64, C.c_int, C.POINTER(tpc_tracks)]
@@ -315,6 +317,10 @@ def tpc_track_results(ctx, n_ev: int, *, copy: bool = True):
     outs = (tpc_tracks * n_ev)()
     _check(ctx, lib().tpc_track_results(ctx, outs))
     return [tracks_to_numpy(o) for o in outs] if copy else outs
+
+
+def tpc_track_join(ctx):
+    _check(ctx, lib().tpc_track_join(ctx))
 
 
 def tpc_track_submit(ctx, clusters: tpc_clusters, geom: tpc_geometry, bz: float) -> int:

@@ -245,6 +245,60 @@ def test_schedule_changes_speed_not_results(tp):
                 assert np.array_equal(getattr(a, f), getattr(b, f)), ("tuned", f)
 
 
+def test_launches_on_several_streams_give_the_same_tracks(tp):
+    """Direct launches spread over 3 streams (kernels of consecutive launches
+    run concurrently): results come back oldest first and equal those of one
+    stream; joining makes the context's stream wait for all of them; a launch
+    discards only its own slot's uncollected results; the autotuner keeps
+    the stream count in range."""
+    import torch
+    evs = synth.batch_events(n_events=7, seed0=4300)
+    with tp.Tracker(2_000_000) as t1:
+        ref = [t1.event(e) for e in evs]
+    stream = torch.cuda.Stream()
+    t = tp.Tracker(2_000_000, max_events_in_flight=3, cuda_stream=stream.cuda_stream)
+    try:
+        s0 = tp.tpc_track_get_schedule(t.ctx)
+        assert s0["max_streams"] == 3 and s0["streams"] == 1
+        with pytest.raises(tp.TpcError):
+            tp.tpc_track_set_schedule(t.ctx, **{**s0, "streams": 4})
+        tp.tpc_track_set_schedule(t.ctx, **{**s0, "streams": 3})
+        g, keep_x = tp.geometry_of(evs[0])
+        cs = [tp.clusters_of(e.y, e.z, e.row, e.sector) for e in evs]
+        bz = float(evs[0].bz)
+
+        def same(a, b, what):
+            for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+                assert np.array_equal(getattr(a, f), getattr(b, f)), (what, f)
+        # three in flight, collected oldest first while the next ones launch
+        got = []
+        for i, (c, _) in enumerate(cs):
+            tp.tpc_track_launch(t.ctx, [c], g, bz)
+            if i >= 2:
+                got += tp.tpc_track_results(t.ctx, 1)
+        got += tp.tpc_track_results(t.ctx, 1) + tp.tpc_track_results(t.ctx, 1)
+        for k, (a, b) in enumerate(zip(ref, got)):
+            same(a, b, k)
+        with pytest.raises(tp.TpcError):
+            tp.tpc_track_results(t.ctx, 1)  # nothing pending
+        # launches 0..3: launch 3 reuses slot 0 and drops launch 0's results
+        for c, _ in cs[:4]:
+            tp.tpc_track_launch(t.ctx, [c], g, bz)
+        tp.tpc_track_join(t.ctx)
+        done = torch.cuda.Event()
+        done.record(stream)
+        done.synchronize()  # after the join: every launch has finished
+        for k in (1, 2, 3):
+            same(ref[k], tp.tpc_track_results(t.ctx, 1)[0], ("after join", k))
+        # batch and single-event calls still work and drop nothing they need
+        same(ref[5], t.event(evs[5]), "event")
+        tuned = tp.tpc_track_autotune(t.ctx, [cs[6][0]], g, bz, reps=1)
+        assert 1 <= tuned["streams"] <= 3
+        same(ref[6], t.event(evs[6]), "tuned")
+    finally:
+        t.close()
+
+
 def test_served_mix_with_an_invalid_event_and_a_polling_thread(tp):
     """Tickets polled from another thread while events are submitted, up to
     four events per launch: every valid event's tracks equal a single call's,
