@@ -23,6 +23,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 TIE_CHI2_CUT, TIE_CHI2_PAIR, TIE_SIN, TIE_EDGE = 1, 2, 4, 8
+MTIE_CUT, MTIE_PAIR, MTIE_DX, MTIE_SIN = 16, 32, 64, 128
 
 
 def build(force: bool = False) -> str:
@@ -44,6 +45,8 @@ def lib():
         _lib.orc_transport_packed.restype = C.c_int
         _lib.orc_update_packed.restype = C.c_double
         _lib.orc_fit_fixed.restype = C.c_int
+        _lib.orc_rotate_packed.restype = C.c_int
+        _lib.orc_merge.restype = C.c_int
     return _lib
 
 
@@ -234,3 +237,105 @@ def unpack_cov(Ct) -> np.ndarray:
 
 def pack_cov(M) -> np.ndarray:
     return np.array([M[i, j] for i in range(5) for j in range(i + 1)], dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# M: sector track merger and global refit (rules M0-M5 in tpc_oracle.c)
+# --------------------------------------------------------------------------
+
+@dataclass
+class MergeParams:
+    """Merger parameters (the same defaults as the GPU library's)."""
+    chi2_cut: float = 30.0
+    dx_lo: float = -5.0
+    dx_hi: float = 30.0
+    tie_chi2: float = 0.5
+    tie_dx: float = 1e-3
+
+
+class OrcMergeConfig(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("chi2_cut", "dx_lo", "dx_hi", "tie_chi2", "tie_dx")]
+
+
+def rotate(d: float, x: float, p, Ct, *, bz: float = 0.5, sin_max: float = 0.99):
+    """M0 on one state.  Returns (rc, x1, p1, C1 packed, J 5x5)."""
+    xx = C.c_double(x)
+    p = np.array(p, dtype=np.float64)
+    Ct = np.array(Ct, dtype=np.float64)
+    J = np.zeros((5, 5))
+    rc = lib().orc_rotate_packed(C.c_double(d), C.c_double(bz), C.c_double(sin_max),
+                                 C.byref(xx), _ptr(p), _ptr(Ct), _ptr(J))
+    return rc, xx.value, p, Ct, J
+
+
+def merge_tracks(ev, o: dict, params: Params | None = None, mparams: MergeParams | None = None) -> dict:
+    """M1-M5 on the sector tracks o of event ev (from track_event).
+
+    Returns the per-track link arrays and the merged track list: every chain
+    head with a successful refit replaces its chain, the other tracks stay as
+    they are, in the order of the sector tracks (a merged track takes its
+    head's place); hits segment by segment, inner to outer."""
+    params = params or Params()
+    mparams = mparams or MergeParams()
+    R = len(ev.row_x)
+    cfg = make_config(params, n_rows=R, n_sectors_phi=ev.n_sectors_phi, split_z=ev.split_z,
+                      half_angle=ev.half_angle, z_max=ev.z_max, bz=ev.bz)
+    mc = OrcMergeConfig(mparams.chi2_cut, mparams.dx_lo, mparams.dx_hi, mparams.tie_chi2,
+                        mparams.tie_dx)
+    T = int(o["n_tracks"])
+    y = np.ascontiguousarray(ev.y, dtype=np.float32)
+    z = np.ascontiguousarray(ev.z, dtype=np.float32)
+    row = np.ascontiguousarray(ev.row, dtype=np.uint16)
+    row_x = np.ascontiguousarray(ev.row_x, dtype=np.float32)
+    sec = np.ascontiguousarray(o["k_sector"], dtype=np.int32)
+    tx = np.ascontiguousarray(o["k_x"], dtype=np.float64)
+    tp = np.ascontiguousarray(o["k_p"], dtype=np.float64)
+    tC = np.ascontiguousarray(o["k_C"], dtype=np.float64)
+    off = np.ascontiguousarray(o["k_hit_off"], dtype=np.int32)
+    cid = np.ascontiguousarray(o["k_hit_cid"], dtype=np.int32)
+    n1 = max(T, 1)
+    r = {"link_out": np.empty(n1, np.int32), "flags": np.empty(n1, np.int32),
+         "match_chi2": np.empty(n1), "chain_head": np.empty(n1, np.int32),
+         "m_x": np.zeros(n1), "m_p": np.zeros((n1, 5)), "m_C": np.zeros((n1, 15)),
+         "m_chi2": np.zeros(n1), "m_ndf": np.zeros(n1, np.int32), "m_ok": np.zeros(n1, np.int32),
+         "m_len": np.zeros(n1, np.int32)}
+    rc = lib().orc_merge(C.byref(cfg), C.byref(mc), _ptr(row_x), _ptr(y), _ptr(z), _ptr(row),
+                         C.c_int64(T), _ptr(sec), _ptr(tx), _ptr(tp), _ptr(tC), _ptr(off), _ptr(cid),
+                         *[_ptr(r[k]) for k in ("link_out", "flags", "match_chi2", "chain_head",
+                                                "m_x", "m_p", "m_C", "m_chi2", "m_ndf", "m_ok",
+                                                "m_len")])
+    if rc != 0:
+        raise RuntimeError(f"oracle merge returned {rc}")
+    r = {k: v[:T] for k, v in r.items()}
+    # the merged track list
+    out_sec, out_x, out_p, out_C, out_chi2, out_ndf, out_hits, out_src = [], [], [], [], [], [], [], []
+    for a in range(T):
+        h = r["chain_head"][a]
+        if h != a:
+            continue  # absorbed into an earlier head's chain
+        if r["m_ok"][a]:
+            segs, b = [], a
+            while b >= 0:
+                segs.append(b)
+                b = r["link_out"][b]
+            hits = np.concatenate([cid[off[g]:off[g + 1]] for g in segs])
+            out_x.append(r["m_x"][a]); out_p.append(r["m_p"][a]); out_C.append(r["m_C"][a])
+            out_chi2.append(r["m_chi2"][a]); out_ndf.append(r["m_ndf"][a])
+            out_src.append(segs)
+        else:
+            hits = cid[off[a]:off[a + 1]]
+            out_x.append(tx[a]); out_p.append(tp[a]); out_C.append(tC[a])
+            out_chi2.append(o["k_chi2"][a]); out_ndf.append(o["k_ndf"][a])
+            out_src.append([a])
+        out_sec.append(sec[a])
+        out_hits.append(hits)
+    hit_off = np.zeros(len(out_hits) + 1, np.int32)
+    hit_off[1:] = np.cumsum([len(h) for h in out_hits])
+    r.update({"n_tracks": len(out_hits), "k_sector": np.array(out_sec, np.int32),
+              "k_x": np.array(out_x, np.float64), "k_p": np.array(out_p, np.float64).reshape(-1, 5),
+              "k_C": np.array(out_C, np.float64).reshape(-1, 15),
+              "k_chi2": np.array(out_chi2, np.float64), "k_ndf": np.array(out_ndf, np.int32),
+              "k_hit_off": hit_off,
+              "k_hit_cid": np.concatenate(out_hits).astype(np.int32) if out_hits else np.zeros(0, np.int32),
+              "sources": out_src})
+    return r

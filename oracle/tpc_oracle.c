@@ -826,3 +826,365 @@ void orc_seed(double x0, double y0, double z0, double x1, double y1, double z1, 
 {
     seed_state(x0, y0, z0, x1, y1, z1, p);
 }
+
+/* ------------------------------------------------------------------------ */
+/* M: sector track merger and global refit                                    */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper places this step after the sector tracker (the tracker takes the
+ * clusters of all TPC links of an event, Sect. 2) but gives no rule, so every
+ * rule here is a reading:
+ *
+ *   M0 rotation of a state at x into a frame turned by d (d = alpha_to -
+ *      alpha_from): x' = x cos d + y sin d, y' = -x sin d + y cos d,
+ *      s' = s cos d - c sin d with c = sqrt(1 - s^2); the track must still
+ *      move outward, c' = c cos d + s sin d > 0, and |s'| < sin_max; z, t and
+ *      q/pT are unchanged.  The covariance is carried to the plane x' of the
+ *      new frame (a change of y slides the point along the track back onto
+ *      that plane): dy'/dy = c/c', dz'/dy = -t sin d / c', ds'/dy = -C_k sin d,
+ *      ds'/ds = c'/c, the rest the identity.
+ *   M1 outer state of a sector track: its state (at its innermost hit)
+ *      transported to the plane of its outermost hit.
+ *   M2 candidate pairs (a, b): b lies in a phi neighbour of a's sector in the
+ *      same z half (frames turned by -+ 2 half_angle; across phi = 0 only
+ *      when the sectors close the ring), or in a's phi sector in the other z
+ *      half (same frame).
+ *   M3 match of a pair: a's outer state turned into b's frame (M0), then
+ *      transported to the plane x_b of b's state; admissible iff the gap
+ *      x_b - x_a' lies in [dx_lo, dx_hi], M0 and the transport succeed, and
+ *      chi2 = r^T (C_a' + C_b)^-1 r <= chi2_cut with r = p_a' - p_b.
+ *   M4 links: a -> b iff b is the admissible partner of a with the least
+ *      chi2 (ties to the lower index) and a is that of b; a chain starts at a
+ *      track with an outgoing and no incoming link and follows the links.
+ *   M5 refit of a chain s_1 (innermost) .. s_m: s_m's outer state, covariance
+ *      reset to the seed covariance, updated with s_m's outermost hit; then
+ *      every other hit inward (each segment's hits by descending row; at a
+ *      change of segment the state is turned into the inner segment's frame
+ *      and transported to its outermost hit).  The result is the state at
+ *      s_1's innermost hit, chi2 the sum of the increments, ndf = 2 * hits - 5.
+ *      A chain whose refit fails (a transport or rotation fails) is not merged.
+ *
+ * Near-tie bits (for the parity tests) mark the tracks whose links could
+ * change under rounding: a chi2 within tie_chi2 of the cut or of the next
+ * candidate, a gap within tie_dx of the window, |s| within tie_sin of sin_max.
+ */
+
+typedef struct {
+    double chi2_cut, dx_lo, dx_hi;
+    double tie_chi2, tie_dx;
+} orc_merge_config;
+
+enum { ORC_MTIE_CUT = 16, ORC_MTIE_PAIR = 32, ORC_MTIE_DX = 64, ORC_MTIE_SIN = 128 };
+
+static void sandwich(const double J[5][5], double C[5][5])
+{
+    double T[5][5], N[5][5];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            double a = 0.0;
+            for (int k = 0; k < 5; ++k) a += J[i][k] * C[k][j];
+            T[i][j] = a;
+        }
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            double a = 0.0;
+            for (int k = 0; k < 5; ++k) a += T[i][k] * J[j][k];
+            N[i][j] = a;
+        }
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) C[i][j] = 0.5 * (N[i][j] + N[j][i]);
+}
+
+/* M0.  Returns 0, or -1 when the turned track would not move outward or
+ * |s'| >= sin_max (nothing is changed then). */
+int orc_rotate(double d, double bz, double sin_max, double tie, double* x, double* p,
+               double C[5][5], double J[5][5], int* flags)
+{
+    const double cd = cos(d), sd = sin(d);
+    const double s = p[2];
+    if (!(fabs(s) < 1.0)) return -1;
+    const double c = sqrt(1.0 - s * s);
+    const double s1 = s * cd - c * sd;
+    const double c1 = c * cd + s * sd;
+    if (flags && fabs(fabs(s1) - sin_max) <= tie) *flags |= ORC_MTIE_SIN;
+    if (!(c1 > 0.0) || !(fabs(s1) < sin_max)) return -1;
+    const double ck = -ORC_KAPPA * bz * p[4];
+    double Jr[5][5];
+    memset(Jr, 0, sizeof(Jr));
+    Jr[0][0] = c / c1;
+    Jr[1][0] = -p[3] * sd / c1;
+    Jr[1][1] = 1.0;
+    Jr[2][0] = -ck * sd;
+    Jr[2][2] = c1 / c;
+    Jr[3][3] = 1.0;
+    Jr[4][4] = 1.0;
+    const double x1 = *x * cd + p[0] * sd;
+    const double y1 = -*x * sd + p[0] * cd;
+    *x = x1;
+    p[0] = y1;
+    p[2] = s1;
+    if (C) sandwich(Jr, C);
+    if (J) memcpy(J, Jr, sizeof(Jr));
+    return 0;
+}
+
+/* M0 on a packed covariance (for the unit checks). */
+int orc_rotate_packed(double d, double bz, double sin_max, double* x, double* p, double* Ct,
+                      double* J)
+{
+    double C[5][5], Jr[5][5];
+    tri_to_cov(Ct, C);
+    const int rc = orc_rotate(d, bz, sin_max, 0.0, x, p, C, Jr, NULL);
+    if (rc == 0) {
+        cov_to_tri(C, Ct);
+        if (J) memcpy(J, Jr, sizeof(Jr));
+    }
+    return rc;
+}
+
+/* r^T S^-1 r by Cholesky; -1 if S is not positive definite. */
+static double chi2_5(const double r[5], double S[5][5])
+{
+    double L[5][5];
+    memset(L, 0, sizeof(L));
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double a = S[i][j];
+            for (int k = 0; k < j; ++k) a -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(a > 0.0)) return -1.0;
+                L[i][i] = sqrt(a);
+            } else {
+                L[i][j] = a / L[j][j];
+            }
+        }
+    double u[5], q = 0.0;
+    for (int i = 0; i < 5; ++i) {
+        double a = r[i];
+        for (int k = 0; k < i; ++k) a -= L[i][k] * u[k];
+        u[i] = a / L[i][i];
+        q += u[i] * u[i];
+    }
+    return q;
+}
+
+static double sector_alpha(const orc_config* cfg, int sec)
+{
+    const int k = sec % cfg->n_sectors_phi;
+    return (k + 0.5) * 2.0 * cfg->half_angle;
+}
+
+/* sectors whose tracks may continue a track of sector sa (M2); returns count */
+static int merge_partners(const orc_config* cfg, int sa, int out[3], double d[3])
+{
+    const int N = cfg->n_sectors_phi;
+    const int k = sa % N, half = sa / N;
+    const int ring = N * 2.0 * cfg->half_angle > 4.0 * acos(0.0) - 1e-9;  /* closes the ring */
+    int n = 0;
+    for (int dk = -1; dk <= 1; dk += 2) {
+        int kb = k + dk;
+        if (kb < 0 || kb >= N) {
+            if (!ring || N < 3) continue;
+            kb = (kb + N) % N;
+        }
+        out[n] = half * N + kb;
+        d[n] = dk * 2.0 * cfg->half_angle;
+        ++n;
+    }
+    if (cfg->split_z) {
+        out[n] = (1 - half) * N + k;
+        d[n] = 0.0;
+        ++n;
+    }
+    return n;
+}
+
+/*
+ * M1-M5 on the sector tracks of one event (arrays as produced by
+ * orc_track_event: sector, x, p[5], C[15], hit_off[T+1], hit_cid).
+ * Outputs per track: link_out (index of the continuing track or -1), flags
+ * (near-tie bits), match_chi2 (chi2 of its outgoing link), chain_head (the
+ * first track of its merged chain, itself if not merged); per chain head with
+ * m_ok = 1 the refit m_x, m_p[5], m_C[15], m_chi2, m_ndf and the chain's
+ * length m_len.  Returns 0, or -1 on bad input.
+ */
+int orc_merge(const orc_config* cfg, const orc_merge_config* mc, const float* row_x,
+              const float* yf, const float* zf, const uint16_t* row, int64_t T,
+              const int32_t* sector, const double* tx, const double* tp, const double* tC,
+              const int32_t* hit_off, const int32_t* hit_cid, int32_t* link_out, int32_t* flags,
+              double* match_chi2, int32_t* chain_head, double* m_x, double* m_p, double* m_C,
+              double* m_chi2, int32_t* m_ndf, int32_t* m_ok, int32_t* m_len)
+{
+    const int S = cfg->n_sectors_phi * (cfg->split_z ? 2 : 1);
+    const double vy = cfg->sigma_y * cfg->sigma_y, vz = cfg->sigma_z * cfg->sigma_z;
+    for (int64_t a = 0; a < T; ++a)
+        if (sector[a] < 0 || sector[a] >= S || hit_off[a + 1] <= hit_off[a]) return -1;
+    /* tracks grouped by sector (ascending index within a sector) */
+    int64_t* soff = calloc((size_t)S + 1, sizeof(int64_t));
+    int64_t* sidx = malloc(sizeof(int64_t) * (size_t)(T + 1));
+    int64_t* fill = calloc((size_t)S, sizeof(int64_t));
+    for (int64_t a = 0; a < T; ++a) soff[sector[a] + 1]++;
+    for (int s = 0; s < S; ++s) soff[s + 1] += soff[s];
+    for (int64_t a = 0; a < T; ++a) sidx[soff[sector[a]] + fill[sector[a]]++] = a;
+    /* M1 */
+    double* xo = malloc(sizeof(double) * (size_t)(T + 1));
+    double* po = malloc(sizeof(double) * 5 * (size_t)(T + 1));
+    double (*Co)[5][5] = malloc(sizeof(double[5][5]) * (size_t)(T + 1));
+    int* oko = malloc(sizeof(int) * (size_t)(T + 1));
+    for (int64_t a = 0; a < T; ++a) {
+        const int32_t last = hit_cid[hit_off[a + 1] - 1];
+        xo[a] = row_x[row[last]];
+        memcpy(po + 5 * a, tp + 5 * a, 5 * sizeof(double));
+        tri_to_cov(tC + 15 * a, Co[a]);
+        int fl = 0;
+        oko[a] = orc_transport(tx[a], xo[a], cfg->bz, cfg->sin_max, cfg->tie_sin, po + 5 * a,
+                               Co[a], NULL, &fl) == 0;
+        flags[a] = fl ? ORC_MTIE_SIN : 0;
+    }
+    /* M3: best partner per track on each side, with the runner-up for ties */
+    int64_t* best_b = malloc(sizeof(int64_t) * (size_t)(T + 1));
+    int64_t* best_a = malloc(sizeof(int64_t) * (size_t)(T + 1));
+    double* chi_b = malloc(sizeof(double) * (size_t)(T + 1));
+    double* chi_a = malloc(sizeof(double) * (size_t)(T + 1));
+    double* chi_b2 = malloc(sizeof(double) * (size_t)(T + 1));
+    double* chi_a2 = malloc(sizeof(double) * (size_t)(T + 1));
+    for (int64_t a = 0; a < T; ++a) {
+        best_b[a] = best_a[a] = -1;
+        chi_b[a] = chi_a[a] = chi_b2[a] = chi_a2[a] = INFINITY;
+    }
+    for (int64_t a = 0; a < T; ++a) {
+        if (!oko[a]) continue;
+        int ps[3];
+        double pd[3];
+        const int np = merge_partners(cfg, sector[a], ps, pd);
+        for (int q = 0; q < np; ++q) {
+            /* a's outer state in the frame of sector ps[q] (independent of b) */
+            double xr = xo[a], pr[5], Cr[5][5];
+            memcpy(pr, po + 5 * a, sizeof(pr));
+            memcpy(Cr, Co[a], sizeof(Cr));
+            int fr = 0;
+            const int rot_bad = pd[q] != 0.0 &&
+                orc_rotate(pd[q], cfg->bz, cfg->sin_max, cfg->tie_sin, &xr, pr, Cr, NULL, &fr);
+            if (fr) flags[a] |= ORC_MTIE_SIN;
+            if (rot_bad) continue;
+            for (int64_t k = soff[ps[q]]; k < soff[ps[q] + 1]; ++k) {
+                const int64_t b = sidx[k];
+                double x = xr, p[5], C[5][5];
+                memcpy(p, pr, sizeof(p));
+                memcpy(C, Cr, sizeof(C));
+                const double gap = tx[b] - x;
+                if (fabs(gap - mc->dx_lo) <= mc->tie_dx || fabs(gap - mc->dx_hi) <= mc->tie_dx) {
+                    flags[a] |= ORC_MTIE_DX;
+                    flags[b] |= ORC_MTIE_DX;
+                }
+                if (!(gap >= mc->dx_lo && gap <= mc->dx_hi)) continue;
+                int ft = 0;
+                const int bad = orc_transport(x, tx[b], cfg->bz, cfg->sin_max, cfg->tie_sin, p, C,
+                                              NULL, &ft);
+                if (ft) { flags[a] |= ORC_MTIE_SIN; flags[b] |= ORC_MTIE_SIN; }
+                if (bad) continue;
+                double r[5], Sm[5][5], Cb[5][5];
+                tri_to_cov(tC + 15 * b, Cb);
+                for (int i = 0; i < 5; ++i) {
+                    r[i] = p[i] - tp[5 * b + i];
+                    for (int j = 0; j < 5; ++j) Sm[i][j] = C[i][j] + Cb[i][j];
+                }
+                const double chi2 = chi2_5(r, Sm);
+                if (chi2 < 0.0) continue;
+                if (fabs(chi2 - mc->chi2_cut) <= mc->tie_chi2) {
+                    flags[a] |= ORC_MTIE_CUT;
+                    flags[b] |= ORC_MTIE_CUT;
+                }
+                if (!(chi2 <= mc->chi2_cut)) continue;
+                /* least chi2, ties to the lower index (candidates of b come in
+                 * ascending a, those of a in ascending b within a sector, and
+                 * sectors in the order above; compare indices explicitly) */
+                if (chi2 < chi_b[a] || (chi2 == chi_b[a] && b < best_b[a])) {
+                    chi_b2[a] = chi_b[a];
+                    chi_b[a] = chi2;
+                    best_b[a] = b;
+                } else if (chi2 < chi_b2[a]) {
+                    chi_b2[a] = chi2;
+                }
+                if (chi2 < chi_a[b] || (chi2 == chi_a[b] && a < best_a[b])) {
+                    chi_a2[b] = chi_a[b];
+                    chi_a[b] = chi2;
+                    best_a[b] = a;
+                } else if (chi2 < chi_a2[b]) {
+                    chi_a2[b] = chi2;
+                }
+            }
+        }
+    }
+    for (int64_t a = 0; a < T; ++a) {
+        if (chi_b2[a] - chi_b[a] <= mc->tie_chi2) flags[a] |= ORC_MTIE_PAIR;
+        if (chi_a2[a] - chi_a[a] <= mc->tie_chi2) flags[a] |= ORC_MTIE_PAIR;
+    }
+    /* M4 */
+    int64_t* link_in = malloc(sizeof(int64_t) * (size_t)(T + 1));
+    for (int64_t a = 0; a < T; ++a) link_in[a] = -1;
+    for (int64_t a = 0; a < T; ++a) {
+        link_out[a] = -1;
+        match_chi2[a] = 0.0;
+        chain_head[a] = (int32_t)a;
+        m_ok[a] = 0;
+        m_len[a] = 1;
+        const int64_t b = best_b[a];
+        if (b >= 0 && best_a[b] == a) {
+            link_out[a] = (int32_t)b;
+            match_chi2[a] = chi_b[a];
+        }
+    }
+    for (int64_t a = 0; a < T; ++a)
+        if (link_out[a] >= 0) link_in[link_out[a]] = a;
+    /* M5 */
+    int64_t* chain = malloc(sizeof(int64_t) * (size_t)(T + 1));
+    for (int64_t h = 0; h < T; ++h) {
+        if (link_in[h] >= 0 || link_out[h] < 0) continue;
+        int m = 0;
+        for (int64_t a = h; a >= 0 && m < T; a = link_out[a]) chain[m++] = a;
+        /* start: outer state of the outermost segment, seed covariance */
+        const int64_t so = chain[m - 1];
+        double x = xo[so], p[5], C[5][5];
+        memcpy(p, po + 5 * so, sizeof(p));
+        seed_cov(cfg, C, p[2]);
+        double chi2 = 0.0;
+        int n_upd = 0, ok = oko[so];
+        for (int g = m - 1; g >= 0 && ok; --g) {
+            const int64_t a = chain[g];
+            if (g < m - 1) {
+                const double d = sector_alpha(cfg, sector[a]) - sector_alpha(cfg, sector[chain[g + 1]]);
+                int fl = 0;
+                if (d != 0.0 && orc_rotate(d, cfg->bz, cfg->sin_max, cfg->tie_sin, &x, p, C, NULL, &fl)) ok = 0;
+                if (fl) flags[a] |= ORC_MTIE_SIN;
+            }
+            for (int32_t k = hit_off[a + 1] - 1; k >= hit_off[a] && ok; --k) {
+                const int32_t c = hit_cid[k];
+                const double xh = row_x[row[c]];
+                if (xh != x) {
+                    int ft = 0;
+                    if (orc_transport(x, xh, cfg->bz, cfg->sin_max, cfg->tie_sin, p, C, NULL, &ft)) ok = 0;
+                    if (ft) flags[a] |= ORC_MTIE_SIN;
+                    x = xh;
+                }
+                if (ok) {
+                    chi2 += orc_update(p, C, yf[c], zf[c], vy, vz);
+                    ++n_upd;
+                }
+            }
+        }
+        if (!ok) continue;
+        m_ok[h] = 1;
+        m_len[h] = m;
+        m_x[h] = x;
+        memcpy(m_p + 5 * h, p, sizeof(p));
+        cov_to_tri(C, m_C + 15 * h);
+        m_chi2[h] = chi2;
+        m_ndf[h] = 2 * n_upd - 5;
+        for (int g = 0; g < m; ++g) chain_head[chain[g]] = (int32_t)h;
+    }
+    free(soff); free(sidx); free(fill); free(xo); free(po); free(Co); free(oko);
+    free(best_b); free(best_a); free(chi_b); free(chi_a); free(chi_b2); free(chi_a2);
+    free(link_in); free(chain);
+    return 0;
+}
