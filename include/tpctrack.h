@@ -111,6 +111,25 @@ typedef struct {
     float seed_var_s;                  /* seed variance of the slope dy/dx (1); sin(phi) gets it x cos^6(phi) */
     float seed_var_t;                  /* seed variance of the slope dz/dx (1); tan(lambda) gets it x cos^2(phi) */
     float seed_var_q;                  /* seed variance of q/pT (100) */
+    /* Sector track merger and global refit (0 = off, the default).  With
+     * merge = 1 the tracks of neighbouring phi sectors (same z half) and of
+     * the two halves of one phi sector are joined where one continues the
+     * other, and each joined chain is refitted over all its hits:
+     *   - a track's state is carried to its outermost hit, turned into the
+     *     other sector's frame and carried to the other track's state;
+     *   - the pair is admissible if the gap between the two (along x of the
+     *     outer track's frame) lies in [merge_dx_lo, merge_dx_hi] cm and the
+     *     5-parameter chi2 of the two states is <= merge_chi2;
+     *   - tracks are linked when each is the other's admissible partner of
+     *     least chi2; a chain of up to 16 tracks is refitted from its
+     *     outermost hit inward (Kalman filter, frames turned between tracks).
+     * A merged track takes the place (and sector) of its innermost track;
+     * its state is at the innermost hit, ndf = 2 * hits - 5, and its hit list
+     * is the tracks' lists, innermost track first.  Tracks not merged are
+     * unchanged. */
+    int merge;
+    float merge_chi2;                  /* (30) */
+    float merge_dx_lo, merge_dx_hi;    /* (-5, 30) cm */
 } tpc_track_params;
 
 /* Context configuration. */
@@ -295,6 +314,8 @@ void tpc_chi2_calib_destroy(tpc_chi2_calib* c);
 typedef struct {
     int64_t n_clusters, n_rows_total, n_bins, n_links, n_starts, n_tracklets,
             n_valid_tracklets, n_tracklet_hits, n_tracks, n_track_hits, n_chain_hits;
+    int64_t n_merge_links, n_merge_chains;  /* merger: links, refitted chains (0 without merge) */
+    int64_t n_sector_tracks;                /* tracks before merging (= n_tracks without merge) */
 } tpc_track_counters;
 int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c);
 

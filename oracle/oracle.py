@@ -249,7 +249,7 @@ class MergeParams:
     chi2_cut: float = 30.0
     dx_lo: float = -5.0
     dx_hi: float = 30.0
-    tie_chi2: float = 0.5
+    tie_chi2: float = 1.0
     tie_dx: float = 1e-3
 
 

@@ -862,7 +862,8 @@ void orc_seed(double x0, double y0, double z0, double x1, double y1, double z1, 
  *      change of segment the state is turned into the inner segment's frame
  *      and transported to its outermost hit).  The result is the state at
  *      s_1's innermost hit, chi2 the sum of the increments, ndf = 2 * hits - 5.
- *      A chain whose refit fails (a transport or rotation fails) is not merged.
+ *      A chain whose refit fails (a transport or rotation fails), or of more
+ *      than 16 tracks, is not merged.
  *
  * Near-tie bits (for the parity tests) mark the tracks whose links could
  * change under rounding: a chi2 within tie_chi2 of the cut or of the next
@@ -1143,6 +1144,7 @@ int orc_merge(const orc_config* cfg, const orc_merge_config* mc, const float* ro
         if (link_in[h] >= 0 || link_out[h] < 0) continue;
         int m = 0;
         for (int64_t a = h; a >= 0 && m < T; a = link_out[a]) chain[m++] = a;
+        if (m > 16) continue;  /* chains of more than 16 tracks are left unmerged */
         /* start: outer state of the outermost segment, seed covariance */
         const int64_t so = chain[m - 1];
         double x = xo[so], p[5], C[5][5];

@@ -224,6 +224,7 @@ __global__ void k_sel_write(Launch L)
             L.k_chi2[j] = H.chi2;
             L.k_ndf[j] = H.ndf;
             L.k_hit_off[j] = off0;
+            L.k_gsec[j] = gs;
         }
         // owned rows from the bits k_sel_decide left (no weight reads here)
         const int* rowhit = L.tl_rowhit + (size_t)t * L.R;

@@ -77,7 +77,21 @@ struct Counters {
     int tl_next;          // work counter of the persistent constructor
     int n_chain_hits;     // hits on the chains of all start hits
     int n_big_rows;       // rows too large for the small row sort
-    int pad[13];
+    int n_mg_links;       // merger: links between sector tracks
+    int n_mg_chains;      // merger: refitted chains of two or more tracks
+    int n_mg_tracks;      // merger: tracks after merging
+    int pad[10];
+};
+
+// Merger scratch: a sector track's outer state, and the refit of a chain
+// stored at its first (innermost) track.
+struct MgState {
+    float x, p[5], C[15];
+    int ok;
+};
+struct MgFit {
+    float x, p[5], C[15], chi2;
+    int ndf, ok, nhits, pad;
 };
 
 // Everything a kernel needs, passed by value.
@@ -134,6 +148,19 @@ struct Launch {
     // outputs
     int* k_sector; float* k_x; float* k_param; float* k_cov; float* k_chi2; int* k_ndf;
     int* k_hit_off; int* k_hit_cid;
+    int* k_gsec;                // [t_cap] global sector of an output track
+    // sector track merger (run when merge != 0)
+    int merge, mg_ring;         // ring: the phi sectors close around the beam axis
+    float mg_chi2, mg_dx_lo, mg_dx_hi;
+    float mg_cd, mg_sd;         // cos, sin of the angle between neighbouring sectors
+    int n_mg_tiles;             // look-back tiles of the compaction (after the sectors')
+    MgState* mg_st;             // [t_cap]
+    MgFit* mg_fit;              // [t_cap]
+    unsigned long long* mg_key; // [t_cap] ~(chi2 bits << 32 | a) of b's best a, 0 = none
+    int* mg_best; int* mg_link; int* mg_in; int* mg_absorbed;  // [t_cap]
+    int* mg_oidx; int* mg_ohoff;    // [t_cap] output index / hit offset before a track
+    int* m_sector; float* m_x; float* m_param; float* m_cov; float* m_chi2; int* m_ndf;
+    int* m_hit_off; int* m_hit_cid; int* m_sec_trk_off; int* m_sec_hit_off;
     Counters* cnt;
 };
 
@@ -258,6 +285,8 @@ int constructor_occupancy();
 void launch_binning(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
 void launch_finder(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
 void launch_constructor(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
+void launch_merger(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
+constexpr int kMgTile = 1024;  // tracks per look-back tile of the merger's compaction
 void launch_selector(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);
 
 }  // namespace tpc

@@ -101,8 +101,15 @@ struct Slot {
     unsigned long long* tl_key;
     int *tl_nown, *tl_out, *tl_hitoff, *sec_trk_off, *sec_hit_off;
     unsigned* tl_own;
-    int *k_sector, *k_ndf, *k_hit_off, *k_hit_cid;
+    int *k_sector, *k_ndf, *k_hit_off, *k_hit_cid, *k_gsec;
     float *k_x, *k_param, *k_cov, *k_chi2;
+    // merger scratch and merged outputs
+    MgState* mg_st;
+    MgFit* mg_fit;
+    unsigned long long* mg_key;
+    int *mg_best, *mg_link, *mg_in, *mg_absorbed, *mg_oidx, *mg_ohoff;
+    int *m_sector, *m_ndf, *m_hit_off, *m_hit_cid, *m_sec_trk_off, *m_sec_hit_off;
+    float *m_x, *m_param, *m_cov, *m_chi2;
     // host side
     void* desc_ring[2] = {nullptr, nullptr};  // pinned mirrors of desc_dev, used in turn
     cudaEvent_t desc_done[2] = {nullptr, nullptr};
@@ -247,7 +254,8 @@ size_t layout(Slot& s, char* base)
     s.desc_bytes = sizeof(EventDesc) * k.e + sizeof(long long) * (k.e + 1) + sizeof(int) * k.s +
                    sizeof(float) * kMaxRows + 64;
     s.desc_dev = take(s.desc_bytes);
-    s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (k.rs * kCntPad + 2 * k.s + k.e) + 8 * (k.row_tiles + k.hit_tiles + k.s) + 4096;
+    s.zero_cap = align_up(sizeof(Counters), 256) + 4 * (k.rs * kCntPad + 2 * k.s + k.e) +
+                 8 * (k.row_tiles + k.hit_tiles + k.s + ((long long)k.t + kMgTile - 1) / kMgTile) + 4096;
     s.zero_dev = take(s.zero_cap);
     s.row_off = (int*)take(4 * (k.rs + 1));
     s.big_rows = (int*)take(4 * k.rs);
@@ -284,6 +292,26 @@ size_t layout(Slot& s, char* base)
     s.k_param = (float*)take(20 * (size_t)k.t);
     s.k_cov = (float*)take(60 * (size_t)k.t);
     s.k_chi2 = (float*)take(4 * (size_t)k.t);
+    s.k_gsec = (int*)take(4 * (size_t)k.t);
+    s.mg_st = (MgState*)take(sizeof(MgState) * (size_t)k.t);
+    s.mg_fit = (MgFit*)take(sizeof(MgFit) * (size_t)k.t);
+    s.mg_key = (unsigned long long*)take(8 * (size_t)k.t);
+    s.mg_best = (int*)take(4 * (size_t)k.t);
+    s.mg_link = (int*)take(4 * (size_t)k.t);
+    s.mg_in = (int*)take(4 * (size_t)k.t);
+    s.mg_absorbed = (int*)take(4 * (size_t)k.t);
+    s.mg_oidx = (int*)take(4 * (size_t)k.t);
+    s.mg_ohoff = (int*)take(4 * (size_t)k.t);
+    s.m_sector = (int*)take(4 * (size_t)k.t);
+    s.m_ndf = (int*)take(4 * (size_t)k.t);
+    s.m_hit_off = (int*)take(4 * ((size_t)k.t + 1));
+    s.m_hit_cid = (int*)take(4 * k.n);
+    s.m_sec_trk_off = (int*)take(4 * (k.s + 1));
+    s.m_sec_hit_off = (int*)take(4 * (k.s + 1));
+    s.m_x = (float*)take(4 * (size_t)k.t);
+    s.m_param = (float*)take(20 * (size_t)k.t);
+    s.m_cov = (float*)take(60 * (size_t)k.t);
+    s.m_chi2 = (float*)take(4 * (size_t)k.t);
     return align_up(off, 256);
 }
 
@@ -379,6 +407,7 @@ void launch_all(const Launch& L, const Schedule& S, cudaStream_t st, const Kerne
     launch_finder(L, S, st, hk);
     launch_constructor(L, S, st, hk);
     launch_selector(L, S, st, hk);
+    if (L.merge) launch_merger(L, S, st, hk);
 }
 
 // The kernel sequence as one CUDA graph launch.  The graph of the slot is
@@ -517,6 +546,17 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.min_chain = P.min_chain;
     L.min_tracklet_hits = P.min_tracklet_hits;
     L.min_track_hits = P.min_track_hits;
+    L.merge = P.merge ? 1 : 0;
+    L.mg_chi2 = P.merge_chi2;
+    L.mg_dx_lo = P.merge_dx_lo;
+    L.mg_dx_hi = P.merge_dx_hi;
+    {
+        const double d = 2.0 * (double)g->half_angle_rad;
+        L.mg_cd = (float)std::cos(d);
+        L.mg_sd = (float)std::sin(d);
+        L.mg_ring = g->n_sectors_phi * d > 2.0 * M_PI - 1e-6 ? 1 : 0;
+    }
+    L.n_mg_tiles = (int)(((long long)s.caps.t + kMgTile - 1) / kMgTile);
     L.ev = (EventDesc*)s.desc_dev;
     L.ev_off = (long long*)((char*)s.desc_dev + sizeof(EventDesc) * s.caps.e);
     L.sec_event = (int*)((char*)L.ev_off + sizeof(long long) * (s.caps.e + 1));
@@ -539,7 +579,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
         if (L.n_row_tiles < 1) L.n_row_tiles = 1;
         L.n_hit_tiles = (int)((n_total + kHitTile - 1) / kHitTile);
         if (L.n_hit_tiles < 1) L.n_hit_tiles = 1;
-        L.tile_state = (unsigned long long*)take(8 * ((size_t)L.n_row_tiles + L.n_hit_tiles + S));
+        L.tile_state = (unsigned long long*)take(8 * ((size_t)L.n_row_tiles + L.n_hit_tiles + S +
+                                                     (L.merge ? L.n_mg_tiles : 0)));
         zo = align_up(zo, 16);
         if (zo > s.zero_cap) return fail(ctx, TPC_EINVAL, "internal: zero region too small");
         CUDA_TRY(ctx, cudaMemsetAsync(s.zero_dev, 0, zo, s.stream));
@@ -579,6 +620,26 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.k_ndf = s.k_ndf;
     L.k_hit_off = s.k_hit_off;
     L.k_hit_cid = s.k_hit_cid;
+    L.k_gsec = s.k_gsec;
+    L.mg_st = s.mg_st;
+    L.mg_fit = s.mg_fit;
+    L.mg_key = s.mg_key;
+    L.mg_best = s.mg_best;
+    L.mg_link = s.mg_link;
+    L.mg_in = s.mg_in;
+    L.mg_absorbed = s.mg_absorbed;
+    L.mg_oidx = s.mg_oidx;
+    L.mg_ohoff = s.mg_ohoff;
+    L.m_sector = s.m_sector;
+    L.m_x = s.m_x;
+    L.m_param = s.m_param;
+    L.m_cov = s.m_cov;
+    L.m_chi2 = s.m_chi2;
+    L.m_ndf = s.m_ndf;
+    L.m_hit_off = s.m_hit_off;
+    L.m_hit_cid = s.m_hit_cid;
+    L.m_sec_trk_off = s.m_sec_trk_off;
+    L.m_sec_hit_off = s.m_sec_hit_off;
     // inputs
     CUDA_TRY(ctx, cudaMemcpyAsync(s.desc_dev, s.desc_host, s.desc_bytes, cudaMemcpyHostToDevice, s.stream));
     CUDA_TRY(ctx, cudaEventRecord(s.desc_done[s.desc_turn], s.stream));
@@ -654,7 +715,31 @@ void fill_counters(Slot& s)
     K.n_tracks = c.n_tracks;
     K.n_track_hits = c.n_track_hits;
     K.n_chain_hits = c.n_chain_hits;
+    K.n_sector_tracks = c.n_tracks;
+    if (I.L.merge) {
+        K.n_tracks = c.n_mg_tracks;
+        K.n_merge_links = c.n_mg_links;
+        K.n_merge_chains = c.n_mg_chains;
+    }
     I.done = true;
+}
+
+// The device arrays of a launch's final tracks: the selector's, or the
+// merger's when the launch merged.
+struct DevOut {
+    const int* sector;
+    const float *x, *param, *cov, *chi2;
+    const int *ndf, *hit_off, *hit_cid, *sec_trk_off, *sec_hit_off;
+    int nt, nh;
+};
+DevOut dev_out(const Slot& s)
+{
+    const Counters& c = *s.cnt_host;
+    if (s.info.L.merge)
+        return {s.m_sector, s.m_x, s.m_param, s.m_cov, s.m_chi2, s.m_ndf, s.m_hit_off, s.m_hit_cid,
+                s.m_sec_trk_off, s.m_sec_hit_off, c.n_mg_tracks, c.n_track_hits};
+    return {s.k_sector, s.k_x, s.k_param, s.k_cov, s.k_chi2, s.k_ndf, s.k_hit_off, s.k_hit_cid,
+            s.sec_trk_off, s.sec_hit_off, c.n_tracks, c.n_track_hits};
 }
 
 // Wait for the slot's launch, check the device status, copy the results.
@@ -663,21 +748,21 @@ int collect(tpc_track_ctx* ctx, Slot& s)
     LaunchInfo& I = s.info;
     s.tracks.assign(I.n_ev, tpc_tracks{});
     if (int rc = launch_status(ctx, s)) return rc;
-    const Counters& c = *s.cnt_host;
-    const int nt = c.n_tracks, nh = c.n_track_hits;
+    const DevOut D = dev_out(s);
+    const int nt = D.nt, nh = D.nh;
     cudaStream_t st = s.stream;
     if (nt > 0) {
-        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sector, s.k_sector, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.x, s.k_x, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.param, s.k_param, 20 * (size_t)nt, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.cov, s.k_cov, 60 * (size_t)nt, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.chi2, s.k_chi2, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.ndf, s.k_ndf, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.hit_off, s.k_hit_off, 4 * ((size_t)nt + 1), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sector, D.sector, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.x, D.x, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.param, D.param, 20 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.cov, D.cov, 60 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.chi2, D.chi2, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.ndf, D.ndf, 4 * (size_t)nt, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.hit_off, D.hit_off, 4 * ((size_t)nt + 1), cudaMemcpyDeviceToHost, st));
     }
     if (nh > 0)
-        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.hit_cid, s.k_hit_cid, 4 * (size_t)nh, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_trk_off, s.sec_trk_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(s.out.hit_cid, D.hit_cid, 4 * (size_t)nh, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_trk_off, D.sec_trk_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
     // split per event (sectors of an event are contiguous, so are its tracks)
     int32_t* eho = s.out.ev_hit_off;
@@ -753,11 +838,12 @@ int collect_to_tickets(tpc_track_ctx* ctx, Slot& s, std::vector<std::unique_ptr<
     LaunchInfo& I = s.info;
     if (int rc = launch_status(ctx, s, true)) return rc;
     const Counters& c = *s.cnt_host;
-    const int nt = c.n_tracks;
+    const DevOut D = dev_out(s);
+    const int nt = D.nt;
     cudaStream_t st = s.stream;
     std::vector<int> inv(I.n_ev, 0);
-    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_trk_off, s.sec_trk_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_hit_off, s.sec_hit_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_trk_off, D.sec_trk_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s.out.sec_hit_off, D.sec_hit_off, 4 * ((size_t)I.S + 1), cudaMemcpyDeviceToHost, st));
     if (c.n_invalid)
         CUDA_TRY(ctx, cudaMemcpyAsync(inv.data(), I.L.ev_invalid, 4 * (size_t)I.n_ev, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -787,16 +873,16 @@ int collect_to_tickets(tpc_track_ctx* ctx, Slot& s, std::vector<std::unique_ptr<
         if (!R.buf.p) return fail(ctx, TPC_ENOMEM, "pinned result buffer");
         char* b = R.buf.p;
         if (m > 0) {
-            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_sec, s.k_sector + t0, 4 * m, cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_x, s.k_x + t0, 4 * m, cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_par, s.k_param + 5 * (size_t)t0, 20 * m, cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_cov, s.k_cov + 15 * (size_t)t0, 60 * m, cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_chi, s.k_chi2 + t0, 4 * m, cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_ndf, s.k_ndf + t0, 4 * m, cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_ho, s.k_hit_off + t0, 4 * (m + 1), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_sec, D.sector + t0, 4 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_x, D.x + t0, 4 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_par, D.param + 5 * (size_t)t0, 20 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_cov, D.cov + 15 * (size_t)t0, 60 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_chi, D.chi2 + t0, 4 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_ndf, D.ndf + t0, 4 * m, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_ho, D.hit_off + t0, 4 * (m + 1), cudaMemcpyDeviceToHost, st));
         }
         if (mh > 0)
-            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_hc, s.k_hit_cid + h0, 4 * mh, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(b + o_hc, D.hit_cid + h0, 4 * mh, cudaMemcpyDeviceToHost, st));
         tpc_tracks& V = R.view;
         V.n_tracks = (int64_t)m;
         V.sector = (const int32_t*)(b + o_sec);
@@ -1025,6 +1111,10 @@ void tpc_track_default_params(tpc_track_params* p)
     p->seed_var_s = 1.0f;
     p->seed_var_t = 1.0f;
     p->seed_var_q = 100.0f;
+    p->merge = 0;
+    p->merge_chi2 = 30.0f;
+    p->merge_dx_lo = -5.0f;
+    p->merge_dx_hi = 30.0f;
 }
 
 static bool params_ok(const tpc_track_params& P)
@@ -1033,7 +1123,9 @@ static bool params_ok(const tpc_track_params& P)
            std::isfinite(P.meas_sigma_z) && P.d_max >= 0 && P.chi2_hit > 0 && P.max_gap >= 1 &&
            P.min_chain >= 2 && P.min_tracklet_hits >= 1 && P.min_track_hits >= 1 &&
            P.sin_max > 0 && P.sin_max < 1 && P.seed_var_s > 0 && P.seed_var_t > 0 &&
-           P.seed_var_q > 0;
+           P.seed_var_q > 0 && (P.merge == 0 || P.merge == 1) && P.merge_chi2 > 0 &&
+           std::isfinite(P.merge_chi2) && std::isfinite(P.merge_dx_lo) &&
+           std::isfinite(P.merge_dx_hi) && P.merge_dx_lo <= P.merge_dx_hi;
 }
 
 int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out)

@@ -63,7 +63,8 @@ class tpc_track_params(C.Structure):
                 ("chi2_hit", C.c_float), ("max_gap", C.c_int), ("min_chain", C.c_int),
                 ("min_tracklet_hits", C.c_int), ("min_track_hits", C.c_int),
                 ("sin_max", C.c_float), ("edge_margin", C.c_float), ("seed_var_s", C.c_float),
-                ("seed_var_t", C.c_float), ("seed_var_q", C.c_float)]
+                ("seed_var_t", C.c_float), ("seed_var_q", C.c_float), ("merge", C.c_int),
+                ("merge_chi2", C.c_float), ("merge_dx_lo", C.c_float), ("merge_dx_hi", C.c_float)]
 
 
 class tpc_track_config(C.Structure):
@@ -76,7 +77,8 @@ class tpc_track_config(C.Structure):
 class tpc_track_counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n_clusters", "n_rows_total", "n_bins", "n_links", "n_starts", "n_tracklets",
-        "n_valid_tracklets", "n_tracklet_hits", "n_tracks", "n_track_hits", "n_chain_hits")]
+        "n_valid_tracklets", "n_tracklet_hits", "n_tracks", "n_track_hits", "n_chain_hits",
+        "n_merge_links", "n_merge_chains", "n_sector_tracks")]
 
 
 class tpc_kernel_time(C.Structure):

@@ -1,0 +1,151 @@
+"""Sector track merger and global refit on the GPU against the oracle (M0-M5).
+
+The GPU merges its own sector tracks; the oracle merges its own.  Tracks are
+compared by hit set; a track is left out of the exact comparison when any of
+its source tracks carries a near-tie bit (tracker or merger) or holds a
+cluster of a flagged tracklet, since binary32 may decide those differently.
+Parameters of the compared tracks are held to the same bars as the sector
+tracks'.  Noiseless helices across phi boundaries (also across phi = 0) and
+the membrane come out as one track; batched and served launches give the
+same merged tracks as single events.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1712_09416_b300 import synth
+from tests import _parity
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid")
+
+
+@pytest.fixture(scope="module")
+def tp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1712_09416_b300 import build, tpctrack
+    build.build()
+    return tpctrack
+
+
+def merge_params(tp):
+    p = tp.tpc_track_default_params()
+    p.merge = 1
+    return p
+
+
+@pytest.fixture(scope="module")
+def mtrk(tp):
+    t = tp.Tracker(2_000_000, max_events_per_launch=4, params=merge_params(tp))
+    yield t
+    t.close()
+
+
+def merge_taint(o, m):
+    """Hits of every oracle output track with a flagged or tracker-tainted source."""
+    bad_hits = _parity.tainted_hits(o)
+    off, cid = o["k_hit_off"], o["k_hit_cid"]
+    taint = set(bad_hits)
+    for srcs in m["sources"]:
+        hs = [cid[off[g]:off[g + 1]] for g in srcs]
+        if any(m["flags"][g] for g in srcs) or any(set(h.tolist()) & bad_hits for h in hs):
+            for h in hs:
+                taint.update(h.tolist())
+    return taint
+
+
+def check_merged(tr, ev, orc, counters=None, max_diff_frac=2e-3):
+    o = orc.track_event(ev)
+    m = orc.merge_tracks(ev, o)
+    taint = merge_taint(o, m)
+    rep = _parity.compare_tracks(tr, m, taint)
+    n = max(1, rep["n_oracle"])
+    assert len(rep["missing"]) + len(rep["extra"]) <= max_diff_frac * n, \
+        (len(rep["missing"]), len(rep["extra"]), rep["missing"][:3], rep["extra"][:3])
+    assert rep["order_ok"]
+    _parity.check_param_bars(rep["param_scaled"], "merged tracks")
+    merged = sum(len(s) > 1 for s in m["sources"])
+    if counters is not None:
+        assert counters["n_sector_tracks"] == o["n_tracks"]
+        assert abs(counters["n_merge_chains"] - merged) <= max_diff_frac * n + 2
+        assert counters["n_tracks"] == tr.n_tracks
+    return o, m, rep
+
+
+def test_merged_tracks_match_the_oracle(tp, mtrk, orc):
+    ev = synth.batch_events(2, seed0=3000)[1]
+    tr = mtrk.event(ev)
+    o, m, rep = check_merged(tr, ev, orc, mtrk.counters())
+    assert sum(len(s) > 1 for s in m["sources"]) > 1000
+    assert rep["compared"] > 0.85 * rep["n_oracle"]  # the rest touch a near-tie
+
+
+def test_merge_off_gives_the_sector_tracks(tp, mtrk):
+    ev = synth.batch_events(2, seed0=3000)[0]
+    with tp.Tracker(2_000_000) as t:
+        plain = t.event(ev)
+        c = t.counters()
+    assert c["n_merge_links"] == 0 and c["n_sector_tracks"] == c["n_tracks"]
+    merged = mtrk.event(ev)
+    assert mtrk.counters()["n_sector_tracks"] == plain.n_tracks
+    assert merged.n_tracks <= plain.n_tracks
+    # every cluster of a sector track is in exactly one merged track
+    assert sorted(merged.hit_cid.tolist()) == sorted(plain.hit_cid.tolist())
+
+
+@pytest.mark.parametrize("q,pt,tanl,phi0,vz,split", [
+    (1.0, 0.5, 0.3, 17.0, 0.0, False), (1.0, 0.3, -0.4, 35.0, 0.0, False),
+    (-1.0, 2.0, -0.3, 50.0, 45.0, True)])
+def test_noiseless_helices_come_out_whole(tp, mtrk, q, pt, tanl, phi0, vz, split):
+    p = synth.Particles(q=np.array([q]), pt=np.array([pt]), tanl=np.array([tanl]),
+                        phi0=np.array([math.radians(phi0)]), vx=np.zeros(1), vy=np.zeros(1),
+                        vz=np.array([vz]))
+    ev = synth.make_event(np.random.default_rng(0), p, n_sectors_phi=18, split_z=split, sigma=0.0,
+                          noise_frac=0.0, dtype=np.float32, shuffle=False)
+    tr = mtrk.event(ev)
+    assert mtrk.counters()["n_sector_tracks"] >= 2
+    assert tr.n_tracks == 1
+    h0 = tr.hit_cid[0]
+    truth = np.array([ev.y[h0], ev.z[h0], ev.true_sinphi[h0], tanl, q / pt])
+    err = np.abs(tr.param[0] - truth) / np.maximum(np.abs(truth), 1.0)
+    assert err.max() < 2e-4, err  # binary32 coordinates and arithmetic
+    assert tr.ndf[0] == 2 * len(tr.hit_cid) - 5
+
+
+def test_batched_and_served_merges_equal_single_events(tp, mtrk):
+    evs = synth.batch_events(n_events=4, seed0=3300)
+    alone = [mtrk.event(e) for e in evs]
+    got = mtrk.batch(evs)
+    for k, (a, b) in enumerate(zip(alone, got)):
+        for f in FIELDS:
+            assert np.array_equal(getattr(a, f), getattr(b, f)), (k, f)
+    s = tp.Tracker(2_000_000, max_events_in_flight=2, max_events_per_launch=2)
+    try:
+        tp.tpc_track_set_params(s.ctx, merge_params(tp))
+        keep, tickets = [], []
+        for e in evs:
+            g, kx = tp.geometry_of(e)
+            c, k = tp.clusters_of(e.y, e.z, e.row, e.sector)
+            keep.append((g, kx, c, k))
+            tickets.append(tp.tpc_track_submit(s.ctx, c, g, float(e.bz)))
+        for k, (a, tk) in enumerate(zip(alone, tickets)):
+            b = tp.tpc_track_poll(s.ctx, tk, 60_000_000)
+            assert b is not None
+            for f in FIELDS:
+                assert np.array_equal(getattr(a, f), getattr(b, f)), ("served", k, f)
+            tp.tpc_track_release(s.ctx, tk)
+    finally:
+        s.close()
+
+
+def test_central_event_merge(tp, orc):
+    """The full central event merged on the GPU against the oracle."""
+    ev = synth.central_event(seed=2)
+    with tp.Tracker(2_000_000, params=merge_params(tp)) as t:
+        tr = t.event(ev)
+        c = t.counters()
+    o, m, rep = check_merged(tr, ev, orc, c)
+    assert c["n_merge_chains"] > 4000
