@@ -604,6 +604,60 @@ def async_section(tp, torch, host_ev, geom, bz, n_cl, n_events=600, every_n=100)
     return out
 
 
+def merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, base_ms, steps=200):
+    """The central event with the sector track merger on: step time (timed
+    like the headline, autotuned streams), the merger's kernels, and the
+    tracks per particle with and without merging."""
+    p = tp.tpc_track_default_params()
+    p.merge = 1
+    ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, max_events_in_flight=4,
+                              cuda_stream=stream.cuda_stream, params=p)
+    try:
+        sched = tp.tpc_track_autotune(ctx, [cls[0][0]], geom, bz, reps=2)
+        for i in range(4):
+            tp.tpc_track_launch(ctx, [cls[i % len(cls)][0]], geom, bz)
+            tp.tpc_track_results(ctx, 1, copy=False)
+        c = tp.tpc_track_get_counters(ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(steps):
+            tp.tpc_track_launch(ctx, [cls[i % len(cls)][0]], geom, bz)
+        tp.tpc_track_join(ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        for _ in range(sched["streams"]):
+            tp.tpc_track_results(ctx, 1, copy=False)
+        tp.tpc_track_set_profiling(ctx, True)
+        for i in range(20):
+            tp.tpc_track_launch(ctx, [cls[i % len(cls)][0]], geom, bz)
+            tp.tpc_track_results(ctx, 1, copy=False)
+        kt = tp.tpc_track_kernel_times(ctx)
+        tp.tpc_track_set_profiling(ctx, False)
+    finally:
+        tp.tpc_track_destroy(ctx)
+    mg = {k: v[0] / v[1] for k, v in kt.items() if k.startswith("k_mg_")}
+    whole = sum(v[0] / v[1] for v in kt.values())
+    perf = {}
+    for name, merge in (("without", 0), ("with", 1)):
+        q = tp.tpc_track_default_params()
+        q.merge = merge
+        with tp.Tracker(n + 65536, params=q) as t:
+            tr = t.event(ev)
+        perf[name] = synth.particle_performance(ev, tr.hit_off, tr.hit_cid)
+    return {"workload": "central event with the sector track merger (merge = 1)",
+            "ms_per_event": ms, "clusters_per_s": n / (ms * 1e-3),
+            "ms_per_event_without_merge": base_ms, "schedule": sched,
+            "sector_tracks": int(c["n_sector_tracks"]), "tracks": int(c["n_tracks"]),
+            "links": int(c["n_merge_links"]), "chains": int(c["n_merge_chains"]),
+            "merger_kernels_ms": mg, "merger_share_of_kernel_time": sum(mg.values()) / whole,
+            "particles": perf,
+            "timing": "CUDA events on the tracker stream over the steps (fork to join); "
+                      "kernel times from a separate pass, one stream"}
+
+
 def traffic_for(kernel: str, counters: dict):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current source of that kernel."""
@@ -780,6 +834,13 @@ def run_ours(args):
         except Exception as e:  # reported, the bench line still goes out
             pileup = {"error": repr(e)}
 
+    merged = None
+    if not args.no_merge and rank == 0:
+        try:
+            merged = merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, ms_step)
+        except Exception as e:  # reported, the bench line still goes out
+            merged = {"error": repr(e)}
+
     side_task = None
     if not args.no_served and rank == 0:
         try:
@@ -821,7 +882,7 @@ def run_ours(args):
             "kernels_ms": {k: v[0] / v[1] for k, v in ktimes.items()},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "cpu_baseline": cpu, "served": served, "batched": batched, "pileup": pileup,
-            "side_task": side_task,
+            "side_task": side_task, "merge": merged,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -878,6 +939,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pileup", action="store_true")
+    ap.add_argument("--no-merge", action="store_true", help="skip the sector track merger section")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-input runs (profiling)")
     ap.add_argument("--served-sweep", default="short", choices=["short", "full"],
                     help="event-stream sweep: 4 rates x <=300 events (short) or the 8 rates "

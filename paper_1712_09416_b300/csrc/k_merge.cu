@@ -23,9 +23,10 @@
 //      turned at each change of track); result at the innermost hit.
 //
 // Kernels: k_mg_outer (M1, one thread per track; also clears the scratch),
-// k_mg_match (M2-M3, one thread per track a over the tracks of its partner
-// sectors; b's best a by a 64-bit atomicMax of ~(chi2 bits << 32 | a)),
-// k_mg_link (M4), k_mg_refit (M5, one thread per chain), k_mg_scan (output
+// k_mg_match (M2-M3, one warp per track a, lanes over the tracks of its
+// partner sectors; b's best a by a 64-bit atomicMax of ~(chi2 bits << 32 | a)),
+// k_mg_link (M4), k_mg_gather (hit coordinates of linked tracks), k_mg_refit
+// (M5, one thread per chain), k_mg_scan (output
 // index and hit offset of every surviving track in the original order,
 // decoupled look-back over tiles of kMgTile tracks), k_mg_write (one warp per
 // output track).  Arithmetic is binary32.
@@ -145,12 +146,14 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_outer(Launch L)
     }
 }
 
-// M2-M3
+// M2-M3: one warp per track a, its lanes over the candidate tracks b
 __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
 {
     const int T = n_tracks(L);
     const int N = L.n_sectors_phi;
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T; a += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < T; a += warps) {
         const MgState& O = L.mg_st[a];
         int best = -1;
         float bchi = 0.0f;
@@ -158,6 +161,8 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
             const int gs = L.k_gsec[a];
             const int base = L.ev[L.sec_event[gs]].sec_base;
             const int ls = gs - base, k = ls % N, half = ls / N;
+            const float t_a = O.p[3], q_a = O.p[4], c33 = O.C[9], c43 = O.C[13], c44 = O.C[14];
+            const float cut_pre = L.mg_chi2 * 1.001f + 1e-3f;
             for (int q = 0; q < 3; ++q) {
                 int lb;
                 float sd = 0.0f;
@@ -173,6 +178,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
                     if (!L.split_z) continue;
                     lb = (1 - half) * N + k;
                 }
+                // a's outer state in b's frame (the same on every lane)
                 Fit r;
                 r.x = O.x;
 #pragma unroll
@@ -182,9 +188,24 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
                 if (q < 2 && !rotate(r, L.mg_cd, sd, L)) continue;
                 const int gb = base + lb;
                 const int b1 = L.sec_trk_off[gb + 1];
-                for (int b = L.sec_trk_off[gb]; b < b1; ++b) {
+                for (int b = L.sec_trk_off[gb] + lane; b < b1; b += 32) {
                     const float gap = L.k_x[b] - r.x;
                     if (!(gap >= L.mg_dx_lo && gap <= L.mg_dx_hi)) continue;
+                    // tan(lambda) and q/pT and their covariance block are left
+                    // as they are by transport and rotation, so their 2x2 chi2
+                    // bounds the 5x5 one from below: a pair over the cut there
+                    // (with a margin for rounding) is over it in full
+                    {
+                        const float dt = t_a - L.k_param[(size_t)b * 5 + 3];
+                        const float dq = q_a - L.k_param[(size_t)b * 5 + 4];
+                        const float s33 = c33 + L.k_cov[(size_t)b * 15 + 9];
+                        const float s43 = c43 + L.k_cov[(size_t)b * 15 + 13];
+                        const float s44 = c44 + L.k_cov[(size_t)b * 15 + 14];
+                        const float det = s33 * s44 - s43 * s43;
+                        if (det > 0.0f &&
+                            dt * dt * s44 - 2.0f * dt * dq * s43 + dq * dq * s33 > cut_pre * det)
+                            continue;
+                    }
                     Fit t = r;
                     if (!transport(t, L.k_x[b], L)) continue;
                     const float chi2 = match_chi2(t, L, b);
@@ -198,7 +219,17 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
                 }
             }
         }
-        L.mg_best[a] = best;
+        // least chi2 over the lanes, ties to the lower index
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oc = __shfl_xor_sync(0xffffffffu, bchi, o);
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+            if (ob >= 0 && (best < 0 || oc < bchi || (oc == bchi && ob < best))) {
+                bchi = oc;
+                best = ob;
+            }
+        }
+        if (lane == 0) L.mg_best[a] = best;
     }
 }
 
@@ -221,6 +252,24 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_link(Launch L)
     }
 }
 
+// (x, y, z) of every hit of a linked track, in the order of k_hit_cid, so that
+// the refit reads one float4 per hit instead of three dependent loads
+__global__ void k_mg_gather(Launch L)
+{
+    const int T = n_tracks(L);
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < T; j += warps) {
+        if (L.mg_link[j] < 0 && L.mg_in[j] < 0) continue;
+        const EventDesc ev = L.ev[L.sec_event[L.k_gsec[j]]];
+        const int k1 = L.k_hit_off[j + 1];
+        for (int k = L.k_hit_off[j] + lane; k < k1; k += 32) {
+            const int c = L.k_hit_cid[k];
+            L.mg_hxyz[k] = make_float4(L.xr[ev.row[c]], ev.y[c], ev.z[c], 0.0f);
+        }
+    }
+}
+
 // M5: one thread per chain head (a track with an outgoing and no incoming link)
 __global__ void __launch_bounds__(kMgThreads) k_mg_refit(Launch L)
 {
@@ -237,7 +286,6 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_refit(Launch L)
         if (m > kMaxChain) continue;  // too long: left unmerged
         const MgState& O = L.mg_st[so];
         if (!O.ok) continue;
-        const EventDesc ev = L.ev[L.sec_event[L.k_gsec[h]]];
         Fit f;
         f.x = O.x;
 #pragma unroll
@@ -248,29 +296,20 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_refit(Launch L)
         int a = so;
         for (;;) {
             const int k1 = L.k_hit_off[a], k0 = L.k_hit_off[a + 1] - 1;
-            int c = L.k_hit_cid[k0];
-            float hy = ev.y[c], hz = ev.z[c], hx = L.xr[ev.row[c]];
+            float4 hit = L.mg_hxyz[k0];
             for (int kk = k0; kk >= k1; --kk) {
-                // next hit's inputs before this hit's arithmetic
-                float ny = 0.0f, nz = 0.0f, nx = 0.0f;
-                if (kk > k1) {
-                    const int cn = L.k_hit_cid[kk - 1];
-                    ny = ev.y[cn];
-                    nz = ev.z[cn];
-                    nx = L.xr[ev.row[cn]];
-                }
-                if (hx != f.x && !transport(f, hx, L)) {
+                // the next hit's coordinates load during this hit's arithmetic
+                const float4 nxt = kk > k1 ? L.mg_hxyz[kk - 1] : hit;
+                if (hit.x != f.x && !transport(f, hit.x, L)) {
                     ok = false;
                     break;
                 }
-                chi2 += update(f, hy, hz, L);
-                hy = ny;
-                hz = nz;
-                hx = nx;
+                chi2 += update(f, hit.y, hit.z, L);
+                hit = nxt;
             }
             if (!ok || a == h) break;
             const int inner = L.mg_in[a];
-            const int ka = (L.k_gsec[inner] - ev.sec_base) % N, kp = (L.k_gsec[a] - ev.sec_base) % N;
+            const int ka = L.k_gsec[inner] % N, kp = L.k_gsec[a] % N;
             if (ka != kp) {  // turn into the inner track's frame
                 int dk = ka - kp;
                 if (dk > 1) dk -= N;  // neighbours across phi = 0
@@ -424,17 +463,22 @@ void launch_merger(const Launch& L, const Schedule& S, void* stream_, const Kern
     if (blocks < 1) blocks = 1;
     k_mg_outer<<<blocks, kMgThreads, 0, stream>>>(L);
     hook_after(hook, "k_mg_outer");
-    k_mg_match<<<blocks, kMgThreads, 0, stream>>>(L);
+    int mblocks = (L.t_cap + kMgThreads / 32 - 1) / (kMgThreads / 32);  // one warp per track
+    if (mblocks > S.n_sm * 16) mblocks = S.n_sm * 16;
+    if (mblocks < 1) mblocks = 1;
+    k_mg_match<<<mblocks, kMgThreads, 0, stream>>>(L);
     hook_after(hook, "k_mg_match");
     k_mg_link<<<blocks, kMgThreads, 0, stream>>>(L);
     hook_after(hook, "k_mg_link");
+    int wblocks = (L.t_cap + 7) / 8;  // one warp per track, 8 warps per block
+    if (wblocks > S.n_sm * 16) wblocks = S.n_sm * 16;
+    if (wblocks < 1) wblocks = 1;
+    k_mg_gather<<<wblocks, 256, 0, stream>>>(L);
+    hook_after(hook, "k_mg_gather");
     k_mg_refit<<<blocks, kMgThreads, 0, stream>>>(L);
     hook_after(hook, "k_mg_refit");
     k_mg_scan<<<L.n_mg_tiles, kScanThreads, 0, stream>>>(L);
     hook_after(hook, "k_mg_scan");
-    int wblocks = (L.t_cap + 7) / 8;
-    if (wblocks > S.n_sm * 16) wblocks = S.n_sm * 16;
-    if (wblocks < 1) wblocks = 1;
     k_mg_write<<<wblocks, 256, 0, stream>>>(L);
     hook_after(hook, "k_mg_write");
 }

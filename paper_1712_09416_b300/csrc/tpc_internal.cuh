@@ -159,6 +159,7 @@ struct Launch {
     unsigned long long* mg_key; // [t_cap] ~(chi2 bits << 32 | a) of b's best a, 0 = none
     int* mg_best; int* mg_link; int* mg_in; int* mg_absorbed;  // [t_cap]
     int* mg_oidx; int* mg_ohoff;    // [t_cap] output index / hit offset before a track
+    float4* mg_hxyz;            // [clusters] (x, y, z) of the hits of linked tracks, as k_hit_cid
     int* m_sector; float* m_x; float* m_param; float* m_cov; float* m_chi2; int* m_ndf;
     int* m_hit_off; int* m_hit_cid; int* m_sec_trk_off; int* m_sec_hit_off;
     Counters* cnt;

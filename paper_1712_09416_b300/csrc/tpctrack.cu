@@ -108,6 +108,7 @@ struct Slot {
     MgFit* mg_fit;
     unsigned long long* mg_key;
     int *mg_best, *mg_link, *mg_in, *mg_absorbed, *mg_oidx, *mg_ohoff;
+    float4* mg_hxyz;
     int *m_sector, *m_ndf, *m_hit_off, *m_hit_cid, *m_sec_trk_off, *m_sec_hit_off;
     float *m_x, *m_param, *m_cov, *m_chi2;
     // host side
@@ -302,6 +303,7 @@ size_t layout(Slot& s, char* base)
     s.mg_absorbed = (int*)take(4 * (size_t)k.t);
     s.mg_oidx = (int*)take(4 * (size_t)k.t);
     s.mg_ohoff = (int*)take(4 * (size_t)k.t);
+    s.mg_hxyz = (float4*)take(16 * k.n);
     s.m_sector = (int*)take(4 * (size_t)k.t);
     s.m_ndf = (int*)take(4 * (size_t)k.t);
     s.m_hit_off = (int*)take(4 * ((size_t)k.t + 1));
@@ -630,6 +632,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.mg_absorbed = s.mg_absorbed;
     L.mg_oidx = s.mg_oidx;
     L.mg_ohoff = s.mg_ohoff;
+    L.mg_hxyz = s.mg_hxyz;
     L.m_sector = s.m_sector;
     L.m_x = s.m_x;
     L.m_param = s.m_param;

@@ -354,3 +354,44 @@ def mc_performance(ev: Event, sector, hit_off, hit_cid, *, min_clusters: int = 3
     res["fake_rate"] = fakes / max(1, n_tr)
     res["clone_rate"] = int(np.sum(mc - 1)) / max(1, n_tr)
     return res
+
+
+def particle_performance(ev: Event, hit_off, hit_cid, *, min_clusters: int = 30,
+                         match_frac: float = 0.9) -> dict:
+    """Tracks against the generator's labels, per particle (all its sectors
+    together, unlike mc_performance).
+
+    A track matches particle P when at least match_frac of its hits carry P's
+    label.  A particle is reconstructable when it left at least min_clusters
+    clusters.  Returns the efficiency (reconstructable particles with a
+    matching track), the mean number of matching tracks per found particle
+    (1 when no particle is split into pieces) and the fake rate (tracks that
+    match no particle)."""
+    hit_off = np.asarray(hit_off, np.int64)
+    hit_cid = np.asarray(hit_cid, np.int64)
+    n_tr = len(hit_off) - 1
+    lab = ev.label.astype(np.int64)
+    n_part = int(lab.max()) + 1 if len(lab) else 0
+    counts = np.bincount(lab[lab >= 0], minlength=n_part)
+    reco = counts >= min_clusters
+    res = {"n_tracks": n_tr, "reconstructable": int(reco.sum())}
+    if n_tr <= 0 or n_part == 0:
+        res.update(efficiency=0.0, tracks_per_found_particle=0.0, fake_rate=0.0)
+        return res
+    nh = np.diff(hit_off)
+    tid = np.repeat(np.arange(n_tr), nh)
+    l = lab[hit_cid] + 1  # 0 = noise
+    key = tid * (n_part + 1) + l
+    k, c = np.unique(key, return_counts=True)
+    kt, kl = k // (n_part + 1), k % (n_part + 1)
+    order = np.lexsort((-c, kt))
+    first = np.ones(len(order), bool)
+    first[1:] = kt[order][1:] != kt[order][:-1]
+    best_t, best_l, best_c = kt[order][first], kl[order][first], c[order][first]
+    ok = (best_l > 0) & (best_c >= match_frac * nh[best_t])
+    per_part = np.bincount(best_l[ok] - 1, minlength=n_part)
+    found = reco & (per_part > 0)
+    res["efficiency"] = float(found.sum() / max(1, reco.sum()))
+    res["tracks_per_found_particle"] = float(per_part[found].sum() / max(1, found.sum()))
+    res["fake_rate"] = float(1.0 - ok.sum() / n_tr)
+    return res
