@@ -604,7 +604,7 @@ def async_section(tp, torch, host_ev, geom, bz, n_cl, n_events=600, every_n=100)
     return out
 
 
-def merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, base_ms, steps=200):
+def merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, base_ms, steps=200, tune=True):
     """The central event with the sector track merger on: step time (timed
     like the headline, autotuned streams), the merger's kernels, and the
     tracks per particle with and without merging."""
@@ -613,7 +613,8 @@ def merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, base_ms, steps
     ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, max_events_in_flight=4,
                               cuda_stream=stream.cuda_stream, params=p)
     try:
-        sched = tp.tpc_track_autotune(ctx, [cls[0][0]], geom, bz, reps=2)
+        sched = tp.tpc_track_autotune(ctx, [cls[0][0]], geom, bz, reps=2) if tune else \
+            tp.tpc_track_get_schedule(ctx)
         for i in range(4):
             tp.tpc_track_launch(ctx, [cls[i % len(cls)][0]], geom, bz)
             tp.tpc_track_results(ctx, 1, copy=False)
@@ -669,8 +670,11 @@ def traffic_for(kernel: str, counters: dict):
     e = d.get(kernel)
     if not e:
         return None
-    src = os.path.join(ROOT, "paper_1712_09416_b300", "csrc", e["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    srcs = e["source"] if isinstance(e["source"], list) else [e["source"]]
+    hs = hashlib.sha256()
+    for f in srcs:
+        hs.update(open(os.path.join(ROOT, "paper_1712_09416_b300", "csrc", f), "rb").read())
+    h = hs.hexdigest()[:16]
     if h != e["source_sha"]:
         return None
     return e["dram_bytes_per_cluster"] * counters["n_clusters"]
@@ -706,7 +710,10 @@ def run_ours(args):
     ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, max_events_in_flight=4,
                               cuda_stream=stream.cuda_stream)
     # launch schedule picked by the autotuner on this workload (untimed)
-    schedule = tp.tpc_track_autotune(ctx, [cls[0][0]], geom, bz, reps=3)
+    if args.no_autotune:
+        schedule = tp.tpc_track_get_schedule(ctx)
+    else:
+        schedule = tp.tpc_track_autotune(ctx, [cls[0][0]], geom, bz, reps=3)
     n_streams = schedule["streams"]
 
     def step(i):
@@ -837,7 +844,8 @@ def run_ours(args):
     merged = None
     if not args.no_merge and rank == 0:
         try:
-            merged = merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, ms_step)
+            merged = merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, ms_step,
+                                   steps=max(20, min(200, args.steps)), tune=not args.no_autotune)
         except Exception as e:  # reported, the bench line still goes out
             merged = {"error": repr(e)}
 
@@ -940,6 +948,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pileup", action="store_true")
     ap.add_argument("--no-merge", action="store_true", help="skip the sector track merger section")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default schedule, one stream (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-input runs (profiling)")
     ap.add_argument("--served-sweep", default="short", choices=["short", "full"],
                     help="event-stream sweep: 4 rates x <=300 events (short) or the 8 rates "
