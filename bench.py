@@ -15,8 +15,8 @@ launch stream) for the roofline of the dominant kernel, served (continuous
 batching) versus one-event-at-a-time latency under Poisson arrivals, SM
 clocks during the timed region, and the CPU oracle on a bounded sample.
 
---impl reference times the CPU oracle (the reference of this build) on the
-same workload and metric, each step a bounded sample of sectors.
+--impl reference times the CPU oracle (the plain FP64 statement of the
+method) on the same workload and metric, each step a bounded sample of sectors.
 Multi-GPU (torchrun): independent replicas, one event stream per GPU, no
 collective on the data path; value = clusters of all ranks / slowest rank.
 """
