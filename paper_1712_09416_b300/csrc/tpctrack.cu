@@ -1541,18 +1541,24 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     if (rc) return rc;
     ctx->sched = best;
     // streams: rounds of 4 launches per stream spread over K slots, timed on
-    // the context's stream from the first fork to the join; a larger K must
+    // the context's stream from the first fork to the join, each K with the
+    // constructor block counts above (concurrent launches share the SMs, so
+    // the best count alone need not be the best together); a larger K must
     // win by 2% to be taken
     const int kmax = std::min(4, (int)ctx->slots.size());
     if (kmax > 1) {
+        const Schedule tuned = ctx->sched;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         CUDA_TRY(ctx, cudaEventCreate(&e0));
         CUDA_TRY(ctx, cudaEventCreate(&e1));
         double best_per = 1e30;
-        int best_k = 1;
-        for (int K = 1; K <= kmax && rc == TPC_OK; ++K) {
+        int best_k = 1, best_tl = tuned.tl_blocks_per_sm;
+        for (int K = 1; K <= kmax && rc == TPC_OK; ++K)
+        for (int tlv : (K == 1 ? std::vector<int>{tuned.tl_blocks_per_sm} : tl)) {
+            if (rc != TPC_OK) break;
             ctx->streams = K;
             ctx->next_slot = 0;
+            ctx->sched.tl_blocks_per_sm = tlv;
             std::vector<double> t;
             for (int r = 0; r <= reps && rc == TPC_OK; ++r) {
                 const int nl = 4 * K;
@@ -1574,11 +1580,13 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
             if (rc != TPC_OK) break;
             std::sort(t.begin(), t.end());
             const double per = t[t.size() / 2];
-            if (per < best_per * (K == 1 ? 1.0 : 0.98)) {
+            if (per < best_per * (K > best_k ? 0.98 : 1.0)) {
                 best_per = per;
                 best_k = K;
+                best_tl = tlv;
             }
         }
+        ctx->sched.tl_blocks_per_sm = best_tl;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         ctx->direct.clear();
@@ -1587,6 +1595,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
         if (rc != TPC_OK) {
             cudaGetLastError();
             ctx->streams = 1;
+            ctx->sched = tuned;
             return rc == TPC_ECUDA ? fail(ctx, TPC_ECUDA, "autotune stream timing") : rc;
         }
     }

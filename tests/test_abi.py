@@ -58,6 +58,16 @@ def test_create_rejects_bad_config_before_touching_the_device(lib):
     cfg.params.chi2_hit = -1.0
     assert lib.tpc_track_create(ctypes.byref(cfg), ctypes.byref(ctx)) == tpctrack.TPC_EINVAL
     assert lib.tpc_track_create(None, ctypes.byref(ctx)) == tpctrack.TPC_EINVAL
+    # merger parameters: merge is 0 or 1, a positive cut, an ordered gap window
+    cfg.params = tpctrack.tpc_track_default_params()
+    assert cfg.params.merge == 0 and cfg.params.merge_chi2 == 30.0
+    assert cfg.params.merge_dx_lo == -5.0 and cfg.params.merge_dx_hi == 30.0
+    for field, value in (("merge", 2), ("merge_chi2", 0.0), ("merge_dx_lo", 31.0),
+                         ("merge_chi2", float("nan"))):
+        cfg.params = tpctrack.tpc_track_default_params()
+        setattr(cfg.params, field, value)
+        assert lib.tpc_track_create(ctypes.byref(cfg), ctypes.byref(ctx)) == tpctrack.TPC_EINVAL, field
+        assert not ctx.value
 
 
 def test_struct_layouts_match_the_header(lib, tmp_path):

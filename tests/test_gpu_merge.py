@@ -149,3 +149,26 @@ def test_central_event_merge(tp, orc):
         c = t.counters()
     o, m, rep = check_merged(tr, ev, orc, c)
     assert c["n_merge_chains"] > 4000
+
+
+def test_empty_tiny_and_one_sector_events_with_merging(tp, mtrk, orc):
+    """No clusters, a few noise clusters, a one-wedge event (no partner
+    sectors): merging leaves the sector tracks as they are."""
+    g, kx = tp.geometry_of(synth.batch_events(1, seed0=3000)[0])
+    for n in (0, 1, 7):
+        rng = np.random.default_rng(n)
+        y = rng.uniform(-10, 10, n).astype(np.float32)
+        z = rng.uniform(-100, 100, n).astype(np.float32)
+        row = rng.integers(0, 159, n).astype(np.uint16)
+        sec = rng.integers(0, 36, n).astype(np.uint16)
+        c, keep = tp.clusters_of(y, z, row, sec)
+        tr = tp.tpc_track_event(mtrk.ctx, c, g, 0.5)
+        assert tr.n_tracks == 0 and mtrk.counters()["n_merge_links"] == 0
+    ev = synth.one_sector_event(seed=1)
+    tr = mtrk.event(ev)
+    c = mtrk.counters()
+    assert c["n_merge_links"] == 0 and c["n_tracks"] == c["n_sector_tracks"] == tr.n_tracks
+    with tp.Tracker(200_000) as t:
+        plain = t.event(ev)
+    for f in FIELDS:
+        assert np.array_equal(getattr(tr, f), getattr(plain, f)), f
