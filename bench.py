@@ -498,6 +498,23 @@ def pileup_section(tp, torch, synth, stream, reps=3, n_served=4):
                           "timing": "host wall clock around launch + results, device inputs"}
         out["tracks"] = int(tr.n_tracks)
         out["mc"] = synth.mc_performance(ev, tr.sector, tr.hit_off, tr.hit_cid)
+        out["particles"] = synth.particle_performance(ev, tr.hit_off, tr.hit_cid)
+        # the same launch with the sector track merger
+        p = tp.tpc_track_default_params()
+        p.merge = 1
+        tp.tpc_track_set_params(ctx, p)
+        tp.tpc_track_launch(ctx, [c], geom, bz)
+        tp.tpc_track_results(ctx, 1, copy=False)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            tp.tpc_track_launch(ctx, [c], geom, bz)
+            outs = tp.tpc_track_results(ctx, 1, copy=False)
+        dt = (time.perf_counter() - t0) / reps
+        tr = tp.tracks_to_numpy(outs[0])
+        cm = tp.tpc_track_get_counters(ctx)
+        out["merged"] = {"ms": dt * 1e3, "clusters_per_s": ev.n / dt, "tracks": int(tr.n_tracks),
+                         "chains": int(cm["n_merge_chains"]),
+                         "particles": synth.particle_performance(ev, tr.hit_off, tr.hit_cid)}
     finally:
         tp.tpc_track_destroy(ctx)
     pinned = [torch.from_numpy(ev.y).pin_memory(), torch.from_numpy(ev.z).pin_memory(),
