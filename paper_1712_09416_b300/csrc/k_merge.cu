@@ -23,8 +23,9 @@
 //      turned at each change of track); result at the innermost hit.
 //
 // Kernels: k_mg_outer (M1, one thread per track; also clears the scratch),
-// k_mg_match (M2-M3, one warp per track a, lanes over the tracks of its
-// partner sectors; b's best a by a 64-bit atomicMax of ~(chi2 bits << 32 | a)),
+// k_mg_sortx (each sector's tracks ordered by x), k_mg_match (M2-M3, one
+// warp per track a, lanes over the tracks of its partner sectors whose x lies
+// in the gap window; b's best a by a 64-bit atomicMax of ~(chi2 bits << 32 | a)),
 // k_mg_link (M4), k_mg_gather (hit coordinates of linked tracks), k_mg_refit
 // (M5, one thread per chain), k_mg_scan (output
 // index and hit offset of every surviving track in the original order,
@@ -146,6 +147,75 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_outer(Launch L)
     }
 }
 
+// The tracks of each sector ordered by x (bitonic sort in shared memory, one
+// block per sector; a sector holds at most kMaxSectorTracks tracks), so that
+// the matcher scans only the tracks whose x can lie in the gap window.
+constexpr int kSortXThreads = 512;
+__global__ void __launch_bounds__(kSortXThreads) k_mg_sortx(Launch L)
+{
+    extern __shared__ float sx[];                   // [kMaxSectorTracks]
+    int* si = reinterpret_cast<int*>(sx + kMaxSectorTracks);  // [kMaxSectorTracks]
+    const int g = blockIdx.x;
+    // a sector over kMaxSectorTracks fails the launch (selector); stay in bounds
+    const int t0 = L.sec_trk_off[g], m = min(L.sec_trk_off[g + 1] - t0, kMaxSectorTracks);
+    if (m <= 0) return;
+    int p2 = 1;
+    while (p2 < m) p2 <<= 1;
+    for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+        sx[i] = i < m ? L.k_x[t0 + i] : __int_as_float(0x7f800000);  // +inf pads
+        si[i] = i < m ? t0 + i : 0x7fffffff;
+    }
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const float a = sx[i], b = sx[l];
+                    const int ia = si[i], ib = si[l];
+                    const bool gt = a > b || (a == b && ia > ib);
+                    if (gt == up) {
+                        sx[i] = b;
+                        sx[l] = a;
+                        si[i] = ib;
+                        si[l] = ia;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        L.mg_xs[t0 + i] = sx[i];
+        L.mg_xi[t0 + i] = si[i];
+    }
+}
+
+// First position in xs[0, n) whose value is >= v (xs ascending), by the
+// whole warp (same arguments on every lane): each round probes 32 evenly
+// spaced positions at once and keeps the bracket the ballot points to.
+__device__ __forceinline__ int warp_lower_bound(const float* xs, int n, float v)
+{
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n;  // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) >> 5;
+        const int p = lo + lane * step;
+        const bool valid = p < hi;
+        const unsigned below = __ballot_sync(0xffffffffu, valid && xs[p] < v);
+        const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+        const int c = __popc(below);  // probes below v come first
+        const int nlo = c > 0 ? lo + (c - 1) * step + 1 : lo;
+        const int nhi = c < (int)nvalid ? lo + c * step : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const int p = lo + lane;
+    const unsigned below = __ballot_sync(0xffffffffu, p < hi && xs[p] < v);
+    return lo + __popc(below);
+}
+
 // M2-M3: one warp per track a, its lanes over the candidate tracks b
 __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
 {
@@ -186,9 +256,16 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
 #pragma unroll
                 for (int i = 0; i < 15; ++i) r.C[i] = O.C[i];
                 if (q < 2 && !rotate(r, L.mg_cd, sd, L)) continue;
+                // the tracks of sector gb with x in the gap window (widened by
+                // 0.01 cm against rounding; the exact test follows)
                 const int gb = base + lb;
-                const int b1 = L.sec_trk_off[gb + 1];
-                for (int b = L.sec_trk_off[gb] + lane; b < b1; b += 32) {
+                const int s0 = L.sec_trk_off[gb];
+                const int ns = min(L.sec_trk_off[gb + 1] - s0, kMaxSectorTracks);
+                const float* xs = L.mg_xs + s0;
+                const int k0 = warp_lower_bound(xs, ns, r.x + L.mg_dx_lo - 0.01f);
+                const int k1 = warp_lower_bound(xs, ns, r.x + L.mg_dx_hi + 0.01f);
+                for (int kk = k0 + lane; kk < k1; kk += 32) {
+                    const int b = L.mg_xi[s0 + kk];
                     const float gap = L.k_x[b] - r.x;
                     if (!(gap >= L.mg_dx_lo && gap <= L.mg_dx_hi)) continue;
                     // tan(lambda) and q/pT and their covariance block are left
@@ -455,6 +532,13 @@ __global__ void k_mg_write(Launch L)
 
 }  // namespace
 
+constexpr size_t kSortXSmem = kMaxSectorTracks * (sizeof(float) + sizeof(int));
+
+void prepare_merger()
+{
+    cudaFuncSetAttribute(k_mg_sortx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortXSmem);
+}
+
 void launch_merger(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -463,6 +547,8 @@ void launch_merger(const Launch& L, const Schedule& S, void* stream_, const Kern
     if (blocks < 1) blocks = 1;
     k_mg_outer<<<blocks, kMgThreads, 0, stream>>>(L);
     hook_after(hook, "k_mg_outer");
+    k_mg_sortx<<<L.S, kSortXThreads, kSortXSmem, stream>>>(L);
+    hook_after(hook, "k_mg_sortx");
     int mblocks = (L.t_cap + kMgThreads / 32 - 1) / (kMgThreads / 32);  // one warp per track
     if (mblocks > S.n_sm * 16) mblocks = S.n_sm * 16;
     if (mblocks < 1) mblocks = 1;

@@ -160,6 +160,7 @@ struct Launch {
     int* mg_best; int* mg_link; int* mg_in; int* mg_absorbed;  // [t_cap]
     int* mg_oidx; int* mg_ohoff;    // [t_cap] output index / hit offset before a track
     float4* mg_hxyz;            // [clusters] (x, y, z) of the hits of linked tracks, as k_hit_cid
+    float* mg_xs; int* mg_xi;   // [t_cap] each sector's tracks by ascending x: x, track index
     int* m_sector; float* m_x; float* m_param; float* m_cov; float* m_chi2; int* m_ndf;
     int* m_hit_off; int* m_hit_cid; int* m_sec_trk_off; int* m_sec_hit_off;
     Counters* cnt;
@@ -280,6 +281,7 @@ struct Schedule {
 void prepare_kernels(Schedule* s);
 void prepare_binning();
 void prepare_selector();
+void prepare_merger();
 int constructor_occupancy();
 
 // host-side launchers (one translation unit each)

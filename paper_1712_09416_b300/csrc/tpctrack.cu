@@ -109,6 +109,8 @@ struct Slot {
     unsigned long long* mg_key;
     int *mg_best, *mg_link, *mg_in, *mg_absorbed, *mg_oidx, *mg_ohoff;
     float4* mg_hxyz;
+    float* mg_xs;
+    int* mg_xi;
     int *m_sector, *m_ndf, *m_hit_off, *m_hit_cid, *m_sec_trk_off, *m_sec_hit_off;
     float *m_x, *m_param, *m_cov, *m_chi2;
     // host side
@@ -304,6 +306,8 @@ size_t layout(Slot& s, char* base)
     s.mg_oidx = (int*)take(4 * (size_t)k.t);
     s.mg_ohoff = (int*)take(4 * (size_t)k.t);
     s.mg_hxyz = (float4*)take(16 * k.n);
+    s.mg_xs = (float*)take(4 * (size_t)k.t);
+    s.mg_xi = (int*)take(4 * (size_t)k.t);
     s.m_sector = (int*)take(4 * (size_t)k.t);
     s.m_ndf = (int*)take(4 * (size_t)k.t);
     s.m_hit_off = (int*)take(4 * ((size_t)k.t + 1));
@@ -633,6 +637,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.mg_oidx = s.mg_oidx;
     L.mg_ohoff = s.mg_ohoff;
     L.mg_hxyz = s.mg_hxyz;
+    L.mg_xs = s.mg_xs;
+    L.mg_xi = s.mg_xi;
     L.m_sector = s.m_sector;
     L.m_x = s.m_x;
     L.m_param = s.m_param;
@@ -800,6 +806,7 @@ void prepare_kernels(Schedule* s)
         s->n_sm = n_sm;
     prepare_binning();
     prepare_selector();
+    prepare_merger();
     s->tl_max_per_sm = constructor_occupancy();
     s->tl_blocks_per_sm = s->tl_max_per_sm;
 }
