@@ -621,10 +621,46 @@ def async_section(tp, torch, host_ev, geom, bz, n_cl, n_events=600, every_n=100)
     return out
 
 
+def merge_oracle_baseline(ev) -> dict:
+    """The oracle's merger (M1-M5) on the event, on one host core: the
+    sector tracks come from 36 per-sector oracle calls on all cores
+    (untimed), gathered into one track list in the sector order."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import oracle
+    oracle.build()
+    import numpy as np
+    parts = [ev.select_sectors([s]) for s in range(36)]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
+        outs = list(pool.map(oracle.track_event, parts))
+    o = {"n_tracks": 0}
+    keys = ("k_sector", "k_x", "k_p", "k_C", "k_chi2", "k_ndf")
+    acc = {k: [] for k in keys}
+    hits, lens = [], []
+    for s, (sub, r) in enumerate(zip(parts, outs)):
+        parent = sub.info["parent_index"]
+        acc["k_sector"].append(np.full(r["n_tracks"], s, np.int32))
+        for k in keys[1:]:
+            acc[k].append(r[k])
+        hits.append(parent[r["k_hit_cid"]].astype(np.int32))
+        lens.append(np.diff(r["k_hit_off"]))
+    for k in keys:
+        o[k] = np.concatenate(acc[k])
+    o["n_tracks"] = len(o["k_sector"])
+    o["k_hit_cid"] = np.concatenate(hits)
+    o["k_hit_off"] = np.concatenate([[0], np.cumsum(np.concatenate(lens))]).astype(np.int32)
+    t0 = time.perf_counter()
+    m = oracle.merge_tracks(ev, o)
+    dt = time.perf_counter() - t0
+    return {"value": ev.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the merger alone on the central event's {o['n_tracks']} oracle sector "
+                      f"tracks -> {m['n_tracks']} tracks, {dt:.1f} s on one core"}
+
+
 def merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, base_ms, steps=200, tune=True):
     """The central event with the sector track merger on: step time (timed
     like the headline, autotuned streams), the merger's kernels, and the
     tracks per particle with and without merging."""
+    import numpy as np
     p = tp.tpc_track_default_params()
     p.merge = 1
     ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, max_events_in_flight=4,
@@ -665,7 +701,28 @@ def merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, base_ms, steps
         with tp.Tracker(n + 65536, params=q) as t:
             tr = t.event(ev)
         perf[name] = synth.particle_performance(ev, tr.hit_off, tr.hit_cid)
+    # hits of the merged tracks (those spanning more than one sector): the
+    # refit reads one 16-byte (x, y, z) record per hit, the gather writes it
+    nh = np.diff(tr.hit_off)
+    tid = np.repeat(np.arange(tr.n_tracks), nh)
+    sec = ev.sector[tr.hit_cid].astype(np.int64)
+    spans = np.zeros(tr.n_tracks, bool)
+    if len(sec):
+        first = np.repeat(sec[tr.hit_off[:-1]], nh)
+        np.logical_or.at(spans, tid, sec != first)
+    merged_hits = int(nh[spans].sum())
+    peak, _ = peaks()
+    b_refit = 16 * merged_hits + 2 * 88 * int(c["n_merge_chains"])
+    roof = {"k_mg_refit": {"bytes": b_refit, "ms": mg.get("k_mg_refit"),
+                           "frac_of_hbm": b_refit / (mg["k_mg_refit"] * 1e-3) / 1e9 / peak,
+                           "bound": "latency: one serial Kalman chain per merged track"},
+            "k_mg_match": {"bytes": 88 * int(c["n_sector_tracks"]),
+                           "ms": mg.get("k_mg_match"),
+                           "bound": "latency and ALU: candidate tests from L2 (tracks of one "
+                                    "sector ~40 kB)"}}
     return {"workload": "central event with the sector track merger (merge = 1)",
+            "roofline": roof, "merged_track_hits": merged_hits,
+            "cpu_baseline": merge_oracle_baseline(ev),
             "ms_per_event": ms, "clusters_per_s": n / (ms * 1e-3),
             "ms_per_event_without_merge": base_ms, "schedule": sched,
             "sector_tracks": int(c["n_sector_tracks"]), "tracks": int(c["n_tracks"]),
