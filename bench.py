@@ -616,8 +616,31 @@ def async_section(tp, torch, host_ev, geom, bz, n_cl, n_events=600, every_n=100)
             calib_loop(tp, ctx, host_ev, geom, bz, n_cl, 2 * every_n, every_n, mode == "inline")
             out[mode] = calib_loop(tp, ctx, host_ev, geom, bz, n_cl, n_events, every_n,
                                    mode == "inline")
+            if mode == "async":  # one event's tracks, for the fit timings below
+                tk = tp.tpc_track_submit(ctx, host_ev, geom, bz)
+                tr = tp.tpc_track_poll(ctx, tk, 60_000_000)
+                tp.tpc_track_release(ctx, tk)
         finally:
             tp.tpc_track_destroy(ctx)
+    # the fit alone on the tracks of every_n events: the library's (on its
+    # side thread) and the oracle's statement of it, on one core each
+    import numpy as np
+    from oracle.calib import chi2_scale_fit
+    chi2 = np.tile(tr.chi2, every_n)
+    ndf = np.tile(tr.ndf, every_n)
+    cal = tp.Chi2Calib(1, 3.0, 1)
+    try:
+        cal.add(chi2, ndf, 0)
+        f = cal.poll(-1)
+        native_ms = cal.stats()["max_task_ms"]
+    finally:
+        cal.close()
+    t0 = time.perf_counter()
+    o = chi2_scale_fit(chi2.astype(np.float64), ndf)
+    oracle_ms = (time.perf_counter() - t0) * 1e3
+    out["fit"] = {"tracks": int(len(chi2)), "native_ms": native_ms, "oracle_ms": oracle_ms,
+                  "same_result": bool(abs(f["scale2"] - o["scale2"]) <= 1e-12 * abs(o["scale2"])
+                                      and f["n_kept"] == o["n_kept"])}
     return out
 
 
