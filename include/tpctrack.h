@@ -360,8 +360,9 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);
  * tpc_track_batch) with each candidate value of every schedule field, reps
  * times each (1..50), times the kernel that the field shapes with CUDA
  * events, and keeps the fastest value per field (fields shape different
- * kernels, so they are tuned one after the other).  Last it times rounds of
- * 4K back-to-back launches spread over K = 1 .. min(4, max_streams) streams
+ * kernels, so they are tuned one after the other).  Last it times rounds
+ * (at least 5) of 8K back-to-back launches spread over K = 1 .. min(4,
+ * max_streams) streams
  * (from the context's stream to tpc_track_join), for K > 1 with each of the
  * constructor block counts tried before (launches running together share the
  * SMs), and takes the pair with the shortest time per launch (a larger K

@@ -1547,7 +1547,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     if (!rc) rc = tune(&Schedule::bin_blocks_per_sm, {2, 4, 8, 16}, {"k_count", "k_scatter"});
     if (rc) return rc;
     ctx->sched = best;
-    // streams: rounds of 4 launches per stream spread over K slots, timed on
+    // streams: rounds of 8 launches per stream spread over K slots, timed on
     // the context's stream from the first fork to the join, each K with the
     // constructor block counts above (concurrent launches share the SMs, so
     // the best count alone need not be the best together); a larger K must
@@ -1567,8 +1567,8 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
             ctx->next_slot = 0;
             ctx->sched.tl_blocks_per_sm = tlv;
             std::vector<double> t;
-            for (int r = 0; r <= reps && rc == TPC_OK; ++r) {
-                const int nl = 4 * K;
+            for (int r = 0; r <= std::max(reps, 5) && rc == TPC_OK; ++r) {
+                const int nl = 8 * K;
                 rc = cudaEventRecord(e0, s.home) == cudaSuccess ? TPC_OK : TPC_ECUDA;
                 for (int l = 0; l < nl && rc == TPC_OK; ++l) rc = tpc_track_launch(ctx, n_ev, ev, geom, bz);
                 if (rc == TPC_OK) rc = tpc_track_join(ctx);
