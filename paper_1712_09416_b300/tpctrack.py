@@ -525,6 +525,24 @@ def tpc_track_set_schedule(ctx, **fields):
     _check(ctx, lib().tpc_track_set_schedule(ctx, C.byref(s)))
 
 
+def save_schedule(ctx, path: str):
+    """Write the context's schedule (for instance the autotuner's choice) as JSON."""
+    import json
+    with open(path, "w") as f:
+        json.dump(tpc_track_get_schedule(ctx), f, indent=1)
+
+
+def load_schedule(ctx, path: str) -> dict:
+    """Apply a schedule written by save_schedule (the device fields n_sm,
+    tl_max_per_sm and max_streams are read-only and ignored); returns it."""
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    tpc_track_set_schedule(ctx, **{k: v for k, v in d.items()
+                                   if k not in ("n_sm", "tl_max_per_sm", "max_streams")})
+    return tpc_track_get_schedule(ctx)
+
+
 def tpc_track_autotune(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz: float,
                        reps: int = 3) -> dict:
     arr = (tpc_clusters * len(clusters))(*clusters)

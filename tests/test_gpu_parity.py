@@ -409,6 +409,31 @@ def test_too_many_clusters_for_the_context(tp):
         t.close()
 
 
+def test_memory_budget_too_small_is_refused_before_allocating(tp):
+    """A context whose arenas exceed mem_budget is refused with TPC_ENOMEM
+    before any device allocation; the device stays usable."""
+    with pytest.raises(tp.TpcError) as ei:
+        tp.tpc_track_create(2_000_000, mem_budget=64 << 20)
+    assert ei.value.code == tp.TPC_ENOMEM
+    with tp.Tracker(200_000) as t:
+        assert t.event(synth.one_sector_event(seed=1, n_tracks=20)).n_tracks > 0
+
+
+def test_tuned_schedule_saved_and_loaded(tp, tmp_path):
+    ev = synth.one_sector_event(seed=1)
+    with tp.Tracker(200_000, max_events_in_flight=2) as a:
+        g, kx = tp.geometry_of(ev)
+        c, k = tp.clusters_of(ev.y, ev.z, ev.row, ev.sector)
+        tuned = tp.tpc_track_autotune(a.ctx, [c], g, float(ev.bz), reps=1)
+        tp.save_schedule(a.ctx, str(tmp_path / "s.json"))
+        ref = a.event(ev)
+    with tp.Tracker(200_000, max_events_in_flight=2) as b:
+        assert tp.load_schedule(b.ctx, str(tmp_path / "s.json")) == tuned
+        got = b.event(ev)
+    for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+        assert np.array_equal(getattr(ref, f), getattr(got, f)), f
+
+
 def test_served_results_equal_alone(tp):
     evs = synth.batch_events(n_events=8, seed0=3100)
     t = tp.Tracker(2_000_000, max_events_in_flight=2)
