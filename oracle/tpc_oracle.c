@@ -867,7 +867,9 @@ void orc_seed(double x0, double y0, double z0, double x1, double y1, double z1, 
  *
  * Near-tie bits (for the parity tests) mark the tracks whose links could
  * change under rounding: a chi2 within tie_chi2 of the cut or of the next
- * candidate, a gap within tie_dx of the window, |s| within tie_sin of sin_max.
+ * candidate, and a pair that would be admissible (chi2 within the cut plus
+ * tie_chi2) while its gap lies within tie_dx of the window or |s| within
+ * tie_sin of sin_max at its rotation or transport.
  */
 
 typedef struct {
@@ -1059,31 +1061,39 @@ int orc_merge(const orc_config* cfg, const orc_merge_config* mc, const float* ro
         double pd[3];
         const int np = merge_partners(cfg, sector[a], ps, pd);
         for (int q = 0; q < np; ++q) {
-            /* a's outer state in the frame of sector ps[q] (independent of b) */
+            /* a's outer state in the frame of sector ps[q] (independent of b);
+             * a rotation that fails within the tie width is evaluated as if
+             * it had passed, for the near-tie bits only */
             double xr = xo[a], pr[5], Cr[5][5];
             memcpy(pr, po + 5 * a, sizeof(pr));
             memcpy(Cr, Co[a], sizeof(Cr));
-            int fr = 0;
-            const int rot_bad = pd[q] != 0.0 &&
-                orc_rotate(pd[q], cfg->bz, cfg->sin_max, cfg->tie_sin, &xr, pr, Cr, NULL, &fr);
-            if (fr) flags[a] |= ORC_MTIE_SIN;
-            if (rot_bad) continue;
+            int fr = 0, relaxed = 0;
+            if (pd[q] != 0.0 &&
+                orc_rotate(pd[q], cfg->bz, cfg->sin_max, cfg->tie_sin, &xr, pr, Cr, NULL, &fr)) {
+                if (!fr) continue;
+                xr = xo[a];
+                memcpy(pr, po + 5 * a, sizeof(pr));
+                memcpy(Cr, Co[a], sizeof(Cr));
+                if (orc_rotate(pd[q], cfg->bz, 1.0 - 1e-9, 0.0, &xr, pr, Cr, NULL, NULL)) continue;
+                relaxed = 1;
+            }
             for (int64_t k = soff[ps[q]]; k < soff[ps[q] + 1]; ++k) {
                 const int64_t b = sidx[k];
                 double x = xr, p[5], C[5][5];
                 memcpy(p, pr, sizeof(p));
                 memcpy(C, Cr, sizeof(C));
                 const double gap = tx[b] - x;
-                if (fabs(gap - mc->dx_lo) <= mc->tie_dx || fabs(gap - mc->dx_hi) <= mc->tie_dx) {
-                    flags[a] |= ORC_MTIE_DX;
-                    flags[b] |= ORC_MTIE_DX;
-                }
-                if (!(gap >= mc->dx_lo && gap <= mc->dx_hi)) continue;
+                const int near_dx = fabs(gap - mc->dx_lo) <= mc->tie_dx || fabs(gap - mc->dx_hi) <= mc->tie_dx;
+                const int in_window = gap >= mc->dx_lo && gap <= mc->dx_hi;
+                if (!in_window && !near_dx) continue;
                 int ft = 0;
-                const int bad = orc_transport(x, tx[b], cfg->bz, cfg->sin_max, cfg->tie_sin, p, C,
-                                              NULL, &ft);
-                if (ft) { flags[a] |= ORC_MTIE_SIN; flags[b] |= ORC_MTIE_SIN; }
-                if (bad) continue;
+                int bad = orc_transport(x, tx[b], cfg->bz, cfg->sin_max, cfg->tie_sin, p, C, NULL, &ft);
+                if (bad) {
+                    if (!ft) continue;
+                    memcpy(p, pr, sizeof(p));
+                    memcpy(C, Cr, sizeof(C));
+                    if (orc_transport(x, tx[b], cfg->bz, 1.0 - 1e-9, 0.0, p, C, NULL, NULL)) continue;
+                }
                 double r[5], Sm[5][5], Cb[5][5];
                 tri_to_cov(tC + 15 * b, Cb);
                 for (int i = 0; i < 5; ++i) {
@@ -1092,6 +1102,14 @@ int orc_merge(const orc_config* cfg, const orc_merge_config* mc, const float* ro
                 }
                 const double chi2 = chi2_5(r, Sm);
                 if (chi2 < 0.0) continue;
+                /* a bound met within its tie width matters only for a pair
+                 * that could be admissible */
+                if ((ft || fr || near_dx) && chi2 <= mc->chi2_cut + mc->tie_chi2) {
+                    const int bit = near_dx ? ORC_MTIE_DX : ORC_MTIE_SIN;
+                    flags[a] |= bit;
+                    flags[b] |= bit;
+                }
+                if (relaxed || bad || !in_window) continue;
                 if (fabs(chi2 - mc->chi2_cut) <= mc->tie_chi2) {
                     flags[a] |= ORC_MTIE_CUT;
                     flags[b] |= ORC_MTIE_CUT;

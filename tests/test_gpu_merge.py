@@ -44,29 +44,43 @@ def mtrk(tp):
     t.close()
 
 
-def merge_taint(o, m):
-    """Hits of every oracle output track with a flagged or tracker-tainted source."""
-    bad_hits = _parity.tainted_hits(o)
+def merge_taint(o, m, sector_tracks=None):
+    """Hits of every oracle output track with a source that carries a merger
+    near-tie bit or that differs from the GPU's sector tracks.  sector_tracks
+    (the GPU's tracks of the event without merging) gives the sector tracks
+    that differ exactly, by hit set (their own parity is tested elsewhere);
+    without it every track holding a cluster of a near-tie tracklet counts as
+    different (a superset)."""
     off, cid = o["k_hit_off"], o["k_hit_cid"]
-    taint = set(bad_hits)
+    o_sets = [tuple(cid[off[a]:off[a + 1]].tolist()) for a in range(o["n_tracks"])]
+    if sector_tracks is None:
+        bad_hits = _parity.tainted_hits(o)
+        differs = [bool(set(h) & bad_hits) for h in o_sets]
+        taint = set(bad_hits)
+    else:
+        g_sets = {tuple(sector_tracks.hits(j).tolist()) for j in range(sector_tracks.n_tracks)}
+        differs = [h not in g_sets for h in o_sets]
+        o_set = set(o_sets)
+        taint = set()
+        for h in g_sets - o_set:  # GPU sector tracks the oracle does not have
+            taint.update(h)
     for srcs in m["sources"]:
-        hs = [cid[off[g]:off[g + 1]] for g in srcs]
-        if any(m["flags"][g] for g in srcs) or any(set(h.tolist()) & bad_hits for h in hs):
-            for h in hs:
-                taint.update(h.tolist())
+        if any(m["flags"][g] or differs[g] for g in srcs):
+            for g in srcs:
+                taint.update(o_sets[g])
     return taint
 
 
-def check_merged(tr, ev, orc, counters=None, max_diff_frac=2e-3):
+def check_merged(tr, ev, orc, counters=None, max_diff_frac=2e-3, sector_tracks=None):
     o = orc.track_event(ev)
     m = orc.merge_tracks(ev, o)
-    taint = merge_taint(o, m)
+    taint = merge_taint(o, m, sector_tracks)
     rep = _parity.compare_tracks(tr, m, taint)
     n = max(1, rep["n_oracle"])
     assert len(rep["missing"]) + len(rep["extra"]) <= max_diff_frac * n, \
         (len(rep["missing"]), len(rep["extra"]), rep["missing"][:3], rep["extra"][:3])
     assert rep["order_ok"]
-    _parity.check_param_bars(rep["param_scaled"], "merged tracks")
+    _parity.check_param_bars(rep["param_scaled"], "merged tracks", rep["param_sig"])
     merged = sum(len(s) > 1 for s in m["sources"])
     if counters is not None:
         assert counters["n_sector_tracks"] == o["n_tracks"]
@@ -75,12 +89,20 @@ def check_merged(tr, ev, orc, counters=None, max_diff_frac=2e-3):
     return o, m, rep
 
 
+def sector_tracks(tp, ev):
+    with tp.Tracker(ev.n + 65536) as t:
+        return t.event(ev)
+
+
 def test_merged_tracks_match_the_oracle(tp, mtrk, orc):
     ev = synth.batch_events(2, seed0=3000)[1]
     tr = mtrk.event(ev)
     o, m, rep = check_merged(tr, ev, orc, mtrk.counters())
     assert sum(len(s) > 1 for s in m["sources"]) > 1000
     assert rep["compared"] > 0.85 * rep["n_oracle"]  # the rest touch a near-tie
+    # with the exact sector-track differences as the taint
+    o, m, rep = check_merged(tr, ev, orc, sector_tracks=sector_tracks(tp, ev))
+    assert rep["compared"] > 0.97 * rep["n_oracle"]
 
 
 def test_merge_off_gives_the_sector_tracks(tp, mtrk):
@@ -172,3 +194,46 @@ def test_empty_tiny_and_one_sector_events_with_merging(tp, mtrk, orc):
         plain = t.event(ev)
     for f in FIELDS:
         assert np.array_equal(getattr(tr, f), getattr(plain, f)), f
+
+
+def oracle_by_sector(ev, orc):
+    """The oracle's sector tracks of a 36-sector event from one call per
+    sector on all host cores (sectors are independent), gathered into the
+    record a whole-event call gives (cluster ids of the event)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    n_sec = ev.n_sectors_phi * (2 if ev.split_z else 1)
+    parts = [ev.select_sectors([s]) for s in range(n_sec)]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
+        outs = list(pool.map(orc.track_event, parts))
+    o = {}
+    for k in ("k_x", "k_p", "k_C", "k_chi2", "k_ndf", "t_flags"):
+        o[k] = np.concatenate([r[k] for r in outs])
+    o["k_sector"] = np.concatenate([np.full(r["n_tracks"], s, np.int32) for s, r in enumerate(outs)])
+    o["k_hit_cid"] = np.concatenate([p.info["parent_index"][r["k_hit_cid"]]
+                                     for p, r in zip(parts, outs)]).astype(np.int32)
+    o["k_hit_off"] = np.concatenate([[0], np.cumsum(np.concatenate(
+        [np.diff(r["k_hit_off"]) for r in outs]))]).astype(np.int32)
+    o["t_rowhit"] = np.concatenate([np.where(r["t_rowhit"] >= 0, p.info["parent_index"][r["t_rowhit"]], -1)
+                                    for p, r in zip(parts, outs)])
+    o["n_tracks"] = len(o["k_sector"])
+    return o
+
+
+def test_pileup_event_merge(tp, orc):
+    """The pile-up event (7.37M clusters; vertices over +-200 cm, so many
+    tracks cross the membrane) merged on the GPU against the oracle."""
+    ev = synth.pileup_event()
+    with tp.Tracker(ev.n + 65536, params=merge_params(tp)) as t:
+        tr = t.event(ev)
+        c = t.counters()
+    o = oracle_by_sector(ev, orc)
+    m = orc.merge_tracks(ev, o)
+    rep = _parity.compare_tracks(tr, m, merge_taint(o, m, sector_tracks(tp, ev)))
+    n = max(1, rep["n_oracle"])
+    assert len(rep["missing"]) + len(rep["extra"]) <= 2e-3 * n, (len(rep["missing"]), len(rep["extra"]))
+    assert rep["order_ok"] and rep["compared"] > 0.9 * n, rep["compared"]
+    _parity.check_param_bars(rep["param_scaled"], "merged pile-up tracks", rep["param_sig"])
+    assert c["n_sector_tracks"] == o["n_tracks"]
+    merged = sum(len(s) > 1 for s in m["sources"])
+    assert merged > 20000 and abs(c["n_merge_chains"] - merged) <= 2e-3 * n
