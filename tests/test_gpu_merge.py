@@ -163,14 +163,29 @@ def test_batched_and_served_merges_equal_single_events(tp, mtrk):
         s.close()
 
 
+def check_sector_tracks(st, o, what):
+    """The GPU's sector tracks of a whole event against the oracle's: hit sets
+    of the tracks sharing no cluster with a near-tie tracklet, order,
+    parameters (the merger's inputs, compared at full size)."""
+    rep = _parity.compare_tracks(st, o, _parity.tainted_hits(o))
+    n = max(1, rep["n_oracle"])
+    assert len(rep["missing"]) + len(rep["extra"]) <= 1e-3 * n, \
+        (what, len(rep["missing"]), len(rep["extra"]))
+    assert rep["order_ok"] and "meta_mismatch" not in rep
+    _parity.check_param_bars(rep["param_scaled"], what, rep["param_sig"])
+
+
 def test_central_event_merge(tp, orc):
-    """The full central event merged on the GPU against the oracle."""
+    """The full central event merged on the GPU against the oracle (and its
+    sector tracks, whole, against the oracle's)."""
     ev = synth.central_event(seed=2)
     with tp.Tracker(2_000_000, params=merge_params(tp)) as t:
         tr = t.event(ev)
         c = t.counters()
-    o, m, rep = check_merged(tr, ev, orc, c)
+    st = sector_tracks(tp, ev)
+    o, m, rep = check_merged(tr, ev, orc, c, sector_tracks=st)
     assert c["n_merge_chains"] > 4000
+    check_sector_tracks(st, o, "central-event sector tracks")
 
 
 def test_empty_tiny_and_one_sector_events_with_merging(tp, mtrk, orc):
@@ -222,14 +237,17 @@ def oracle_by_sector(ev, orc):
 
 def test_pileup_event_merge(tp, orc):
     """The pile-up event (7.37M clusters; vertices over +-200 cm, so many
-    tracks cross the membrane) merged on the GPU against the oracle."""
+    tracks cross the membrane) merged on the GPU against the oracle, and its
+    sector tracks, whole, against the oracle's."""
     ev = synth.pileup_event()
     with tp.Tracker(ev.n + 65536, params=merge_params(tp)) as t:
         tr = t.event(ev)
         c = t.counters()
     o = oracle_by_sector(ev, orc)
     m = orc.merge_tracks(ev, o)
-    rep = _parity.compare_tracks(tr, m, merge_taint(o, m, sector_tracks(tp, ev)))
+    st = sector_tracks(tp, ev)
+    check_sector_tracks(st, o, "pile-up sector tracks")
+    rep = _parity.compare_tracks(tr, m, merge_taint(o, m, st))
     n = max(1, rep["n_oracle"])
     assert len(rep["missing"]) + len(rep["extra"]) <= 2e-3 * n, (len(rep["missing"]), len(rep["extra"]))
     assert rep["order_ok"] and rep["compared"] > 0.9 * n, rep["compared"]
