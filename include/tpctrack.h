@@ -316,6 +316,8 @@ typedef struct {
             n_valid_tracklets, n_tracklet_hits, n_tracks, n_track_hits, n_chain_hits;
     int64_t n_merge_links, n_merge_chains;  /* merger: links, refitted chains (0 without merge) */
     int64_t n_sector_tracks;                /* tracks before merging (= n_tracks without merge) */
+    int64_t max_row_hits;       /* high-water marks: clusters of the fullest (sector, row) of the */
+    int64_t max_sector_tracks;  /* launch and tracks of its fullest sector (each limited to 4096) */
 } tpc_track_counters;
 int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c);
 

@@ -180,12 +180,14 @@ __global__ void __launch_bounds__(kScanThreads) k_rowscan(Launch L)
     const int g0 = tile * kScanTile + threadIdx.x * kScanItems;
     unsigned long long loc[kScanItems];
     unsigned long long sum = 0;
+    int cmax = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int g = g0 + k;
         unsigned long long v = 0;
         if (g < L.RS) {
             const int c = L.row_cnt[g * kCntPad];
+            cmax = max(cmax, c);
             RowGrid G = make_grid(L, g, c);
             L.grid[g] = G;
             v = pack2((unsigned)c, (unsigned)(G.ny * G.nz + 1));
@@ -193,6 +195,9 @@ __global__ void __launch_bounds__(kScanThreads) k_rowscan(Launch L)
         loc[k] = sum;
         sum += v;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    if ((threadIdx.x & 31) == 0 && cmax > 0) atomicMax(&L.cnt->max_row_hits, cmax);
     unsigned long long total;
     const unsigned long long excl = block_excl_scan(sum, &total);
     if (threadIdx.x < 32) {

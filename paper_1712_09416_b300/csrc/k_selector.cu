@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
     }
     __syncthreads();
     int m = m_s;
+    if (threadIdx.x == 0 && m > 0) atomicMax(&L.cnt->max_sector_tracks, m);
     if (m > kMaxSectorTracks) {
         if (threadIdx.x == 0) atomicExch(&L.cnt->ovf_sector, 1);
         m = kMaxSectorTracks;

@@ -80,7 +80,9 @@ struct Counters {
     int n_mg_links;       // merger: links between sector tracks
     int n_mg_chains;      // merger: refitted chains of two or more tracks
     int n_mg_tracks;      // merger: tracks after merging
-    int pad[10];
+    int max_row_hits;     // high-water marks: hits of the fullest (sector, row)
+    int max_sector_tracks;  // ... and emitted tracks of the fullest sector
+    int pad[8];
 };
 
 // Merger scratch: a sector track's outer state, and the refit of a chain

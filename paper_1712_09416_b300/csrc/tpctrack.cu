@@ -725,6 +725,8 @@ void fill_counters(Slot& s)
     K.n_track_hits = c.n_track_hits;
     K.n_chain_hits = c.n_chain_hits;
     K.n_sector_tracks = c.n_tracks;
+    K.max_row_hits = c.max_row_hits;
+    K.max_sector_tracks = c.max_sector_tracks;
     if (I.L.merge) {
         K.n_tracks = c.n_mg_tracks;
         K.n_merge_links = c.n_mg_links;

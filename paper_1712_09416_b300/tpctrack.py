@@ -78,7 +78,7 @@ class tpc_track_counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n_clusters", "n_rows_total", "n_bins", "n_links", "n_starts", "n_tracklets",
         "n_valid_tracklets", "n_tracklet_hits", "n_tracks", "n_track_hits", "n_chain_hits",
-        "n_merge_links", "n_merge_chains", "n_sector_tracks")]
+        "n_merge_links", "n_merge_chains", "n_sector_tracks", "max_row_hits", "max_sector_tracks")]
 
 
 class tpc_kernel_time(C.Structure):

@@ -434,6 +434,19 @@ def test_tuned_schedule_saved_and_loaded(tp, tmp_path):
         assert np.array_equal(getattr(ref, f), getattr(got, f)), f
 
 
+def test_high_water_marks(tp):
+    """The counters' fullest (sector, row) and fullest sector: the first a
+    count of the inputs, the second a count of the emitted tracks."""
+    ev = synth.batch_events(2, seed0=3000)[1]
+    with tp.Tracker(2_000_000) as t:
+        tr = t.event(ev)
+        c = t.counters()
+    R = len(ev.row_x)
+    assert c["max_row_hits"] == np.bincount(ev.sector.astype(np.int64) * R + ev.row).max()
+    assert c["max_sector_tracks"] == np.bincount(tr.sector).max()
+    assert c["max_row_hits"] <= 4096 and c["max_sector_tracks"] <= 4096
+
+
 def test_served_results_equal_alone(tp):
     evs = synth.batch_events(n_events=8, seed0=3100)
     t = tp.Tracker(2_000_000, max_events_in_flight=2)
