@@ -974,7 +974,9 @@ def run_ours(args):
                                  "with kernels launched one by one on one stream",
                        "schedule": schedule,
                        "tracks_per_event": counters["n_tracks"],
-                       "tracklets_per_event": counters["n_tracklets"]},
+                       "tracklets_per_event": counters["n_tracklets"],
+                       "fullest_row_hits": counters["max_row_hits"],
+                       "fullest_sector_tracks": counters["max_sector_tracks"]},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                          "traffic": traffic_for(dom, counters),
