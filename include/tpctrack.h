@@ -363,12 +363,12 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);
  * times each (1..50), times the kernel that the field shapes with CUDA
  * events, and keeps the fastest value per field (fields shape different
  * kernels, so they are tuned one after the other).  Last it times rounds
- * (at least 5) of 8K back-to-back launches spread over K = 1 .. min(4,
+ * (at least 7) of 8K back-to-back launches spread over K = 1 .. min(4,
  * max_streams) streams
  * (from the context's stream to tpc_track_join), for K > 1 with each of the
  * constructor block counts tried before (launches running together share the
  * SMs), and takes the pair with the shortest time per launch (a larger K
- * must win by 2%).  Writes the chosen
+ * must win by 1%).  Writes the chosen
  * schedule to *out (may be NULL) and makes it the context's schedule.  The
  * results of the tuning launches are discarded.  Same errors as
  * tpc_track_batch, TPC_EBUSY while serving submitted events. */

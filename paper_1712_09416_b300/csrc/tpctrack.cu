@@ -1553,7 +1553,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     // the context's stream from the first fork to the join, each K with the
     // constructor block counts above (concurrent launches share the SMs, so
     // the best count alone need not be the best together); a larger K must
-    // win by 2% to be taken
+    // win by 1% to be taken
     const int kmax = std::min(4, (int)ctx->slots.size());
     if (kmax > 1) {
         const Schedule tuned = ctx->sched;
@@ -1569,7 +1569,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
             ctx->next_slot = 0;
             ctx->sched.tl_blocks_per_sm = tlv;
             std::vector<double> t;
-            for (int r = 0; r <= std::max(reps, 5) && rc == TPC_OK; ++r) {
+            for (int r = 0; r <= std::max(reps, 7) && rc == TPC_OK; ++r) {
                 const int nl = 8 * K;
                 rc = cudaEventRecord(e0, s.home) == cudaSuccess ? TPC_OK : TPC_ECUDA;
                 for (int l = 0; l < nl && rc == TPC_OK; ++l) rc = tpc_track_launch(ctx, n_ev, ev, geom, bz);
@@ -1589,7 +1589,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
             if (rc != TPC_OK) break;
             std::sort(t.begin(), t.end());
             const double per = t[t.size() / 2];
-            if (per < best_per * (K > best_k ? 0.98 : 1.0)) {
+            if (per < best_per * (K > best_k ? 0.99 : 1.0)) {
                 best_per = per;
                 best_k = K;
                 best_tl = tlv;
