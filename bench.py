@@ -840,6 +840,29 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     for _ in range(n_streams):  # status of the last step of every slot
         tp.tpc_track_results(ctx, 1, copy=False)
+    # the same steps on 1..max streams with the tuned grid shapes (outside the
+    # timed region): what running consecutive events' kernels together buys
+    streams_sweep = {}
+    if rank == 0 and not args.no_autotune:
+        for k in range(1, schedule["max_streams"] + 1):
+            tp.tpc_track_set_schedule(ctx, **{**schedule, "streams": k})
+            for i in range(2 * k):
+                step(i)
+            tp.tpc_track_join(ctx)
+            torch.cuda.synchronize()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            n_sw = min(args.steps, 200)
+            for i in range(n_sw):
+                step(i)
+            tp.tpc_track_join(ctx)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            for _ in range(k):
+                tp.tpc_track_results(ctx, 1, copy=False)
+            streams_sweep[k] = s0.elapsed_time(s1) / n_sw
+        tp.tpc_track_set_schedule(ctx, **schedule)
     # per-kernel device times: the same steps again, kernels launched one by
     # one with a CUDA event after each (outside the timed region)
     tp.tpc_track_set_profiling(ctx, True)
@@ -990,6 +1013,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "cpu_baseline": cpu, "served": served, "batched": batched, "pileup": pileup,
             "side_task": side_task, "merge": merged,
+            "streams_ms_per_event": streams_sweep,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
