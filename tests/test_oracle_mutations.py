@@ -1,0 +1,125 @@
+"""The oracle's merger pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (a dropped
+minus sign, a rotation turned the wrong way, a Jacobian entry lost), builds
+it with gcc under a temporary directory, and checks that the pin written for
+that part of the merger fails on the mutant while it passes on the oracle.
+Nothing here touches the GPU or the package.
+"""
+import ctypes as C
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1712_09416_b300 import synth
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                   "tpc_oracle.c")
+
+MUTATIONS = {
+    "rotation turned the wrong way": ("    const double s1 = s * cd - c * sd;\n    const double c1 = c * cd + s * sd;",
+                                      "    const double s1 = s * cd + c * sd;\n    const double c1 = c * cd - s * sd;"),
+    "sign of ds'/dy": ("    Jr[2][0] = -ck * sd;", "    Jr[2][0] = ck * sd;"),
+    "dz'/dy dropped": ("    Jr[1][0] = -p[3] * sd / c1;", "    Jr[1][0] = 0.0;"),
+    "refit turns the frame backwards": (
+        "                const double d = sector_alpha(cfg, sector[a]) - sector_alpha(cfg, sector[chain[g + 1]]);",
+        "                const double d = sector_alpha(cfg, sector[chain[g + 1]]) - sector_alpha(cfg, sector[a]);"),
+}
+
+
+@pytest.fixture
+def mutant(orc, tmp_path, monkeypatch):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+
+    def build(name):
+        old, new = MUTATIONS[name]
+        src = open(SRC).read()
+        assert src.count(old) == 1, name
+        p = tmp_path / "mutant.c"
+        p.write_text(src.replace(old, new))
+        so = tmp_path / "libmutant.so"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                        str(so), str(p), "-lm"], check=True)
+        lib = C.CDLL(str(so))
+        for f in ("orc_track_event", "orc_transport_packed", "orc_fit_fixed", "orc_rotate_packed",
+                  "orc_merge"):
+            getattr(lib, f).restype = C.c_int
+        lib.orc_update_packed.restype = C.c_double
+        monkeypatch.setattr(orc, "_lib", lib)
+        return orc
+    return build
+
+
+def closed_form_ok(orc):
+    """The rotation pin: truth in sector A turned into B and carried to a row
+    of B lands on the generator's crossing there."""
+    p0 = synth.Particles(q=np.array([1.0]), pt=np.array([0.5]), tanl=np.array([0.3]),
+                         phi0=np.array([math.radians(17.0)]), vx=np.zeros(1), vy=np.zeros(1),
+                         vz=np.zeros(1))
+    ev = synth.make_event(np.random.default_rng(0), p0, n_sectors_phi=18, split_z=False, sigma=0.0,
+                          noise_frac=0.0, dtype=np.float64, shuffle=False)
+    (sa, sb) = sorted(set(ev.sector.tolist()))
+    if (sb - sa) % 18 != 1:
+        sa, sb = sb, sa
+    ma = np.nonzero(ev.sector == sa)[0]
+    mb = np.nonzero(ev.sector == sb)[0]
+    i, j = ma[np.argmax(ev.row[ma])], mb[np.argmin(ev.row[mb])]
+    xr = ev.row_x.astype(np.float64)
+    p = np.array([ev.y[i], ev.z[i], ev.true_sinphi[i], 0.3, 2.0])
+    rc, x1, p1, _, _ = orc.rotate(math.radians(20.0), xr[ev.row[i]], p, np.zeros(15))
+    if rc:
+        return False
+    rc, p2, _, _ = orc.transport(x1, xr[ev.row[j]], p1, np.zeros(15))
+    return rc == 0 and abs(p2[0] - ev.y[j]) < 1e-9 and abs(p2[2] - ev.true_sinphi[j]) < 1e-11
+
+
+def jacobian_ok(orc):
+    """The Jacobian pin: analytic against central differences."""
+    x0, X, d = 150.0, 170.0, math.radians(20.0)
+    p0 = np.array([3.0, 20.0, 0.2, 0.4, 1.5])
+    rc, x1, p1, _, Jr = orc.rotate(d, x0, p0, np.zeros(15))
+    rc, p2, _, Jt = orc.transport(x1, X, p1, np.zeros(15))
+    J = Jt @ Jr
+
+    def f(p):
+        _, x1, p1, _, _ = orc.rotate(d, x0, p, np.zeros(15))
+        return orc.transport(x1, X, p1, np.zeros(15))[1]
+    for k in range(5):
+        h = 1e-6 * max(1.0, abs(p0[k]))
+        e = np.zeros(5)
+        e[k] = h
+        if not np.allclose((f(p0 + e) - f(p0 - e)) / (2 * h), J[:, k], rtol=1e-6, atol=1e-7):
+            return False
+    return True
+
+
+def merged_truth_ok(orc):
+    """The merger pin: a noiseless helix across a phi boundary comes out as
+    one track with the generator's state."""
+    p0 = synth.Particles(q=np.array([1.0]), pt=np.array([0.5]), tanl=np.array([0.3]),
+                         phi0=np.array([math.radians(17.0)]), vx=np.zeros(1), vy=np.zeros(1),
+                         vz=np.zeros(1))
+    ev = synth.make_event(np.random.default_rng(0), p0, n_sectors_phi=18, split_z=False, sigma=0.0,
+                          noise_frac=0.0, dtype=np.float64, shuffle=False)
+    o = orc.track_event(ev)
+    m = orc.merge_tracks(ev, o)
+    if m["n_tracks"] != 1:
+        return False
+    h0 = m["k_hit_cid"][0]
+    truth = np.array([ev.y[h0], ev.z[h0], ev.true_sinphi[h0], 0.3, 2.0])
+    return bool((np.abs(m["k_p"][0] - truth) / np.maximum(np.abs(truth), 1.0)).max() < 2e-5)
+
+
+PINS = {"rotation turned the wrong way": closed_form_ok, "sign of ds'/dy": jacobian_ok,
+        "dz'/dy dropped": jacobian_ok, "refit turns the frame backwards": merged_truth_ok}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pin_catches_the_mistake(orc, mutant, name):
+    assert PINS[name](orc), "the pin must pass on the oracle itself"
+    assert not PINS[name](mutant(name)), f"the pin missed: {name}"
