@@ -1,10 +1,11 @@
-"""The oracle's merger pins catch plausible mistakes.
+"""The oracle's pins catch plausible mistakes.
 
 Each case plants one mistake in a copy of the oracle's C source (a dropped
-minus sign, a rotation turned the wrong way, a Jacobian entry lost), builds
-it with gcc under a temporary directory, and checks that the pin written for
-that part of the merger fails on the mutant while it passes on the oracle.
-Nothing here touches the GPU or the package.
+minus sign, a rotation turned the wrong way, a Jacobian entry lost, a wrong
+prior, a path length without the arc), builds it with gcc under a temporary
+directory, and checks that the pin written for that part of the oracle
+(merger, transport, update, seed) fails on the mutant while it passes on the
+oracle.  Nothing here touches the GPU or the package.
 """
 import ctypes as C
 import math
@@ -28,6 +29,16 @@ MUTATIONS = {
     "refit turns the frame backwards": (
         "                const double d = sector_alpha(cfg, sector[a]) - sector_alpha(cfg, sector[chain[g + 1]]);",
         "                const double d = sector_alpha(cfg, sector[chain[g + 1]]) - sector_alpha(cfg, sector[a]);"),
+    # the sector tracker's transport, update and seed (pins in test_oracle_transport/_fit)
+    "transport: q/pT column of dy lost": (
+        "    Jl[0][4] = -kB * dx * dx * (cc + (s0 + s1) * s1 / c1) / (cc * cc);", "    Jl[0][4] = 0.0;"),
+    "update: sign of the off-diagonal gain": (
+        "    const double I00 = S11 / det, I01 = -S01 / det, I11 = S00 / det;",
+        "    const double I00 = S11 / det, I01 = S01 / det, I11 = S00 / det;"),
+    "seed: sin(phi) variance with cos^4": (
+        "    C[2][2] = cfg->seed_var_s * c2 * c2 * c2;", "    C[2][2] = cfg->seed_var_s * c2 * c2;"),
+    "transport: path length without the arc": (
+        "    double dS = (h > 0.0) ? ch * asin(h) / h : ch;", "    double dS = ch;"),
 }
 
 
@@ -115,8 +126,43 @@ def merged_truth_ok(orc):
     return bool((np.abs(m["k_p"][0] - truth) / np.maximum(np.abs(truth), 1.0)).max() < 2e-5)
 
 
+def passes(test, *args):
+    """Run one of the existing pin tests; True if it passes."""
+    try:
+        test(*args)
+        return True
+    except AssertionError:
+        return False
+
+
+def transport_jacobian_ok(orc):
+    from tests import test_oracle_transport as t
+    return all(passes(t.test_jacobian_matches_finite_differences, orc, seed) for seed in range(12))
+
+
+def update_ok(orc):
+    from tests import test_oracle_transport as t
+    return all(passes(t.test_update_equals_information_form, orc, seed) for seed in range(8))
+
+
+def prior_ok(orc):
+    from tests import test_oracle_fit as t
+    return all(passes(t.test_zero_field_line_equals_batch_least_squares, orc, s0, tt)
+               for s0, tt in ((0.0, 0.0), (0.25, 0.5), (-0.4, -0.9), (0.6, 0.1)))
+
+
+def crossings_ok(orc):
+    from tests import test_oracle_transport as t
+    return passes(t.test_transport_matches_closed_form_crossings, orc, 1.0, 0.35, 0.4,
+                  math.radians(10.0))
+
+
 PINS = {"rotation turned the wrong way": closed_form_ok, "sign of ds'/dy": jacobian_ok,
-        "dz'/dy dropped": jacobian_ok, "refit turns the frame backwards": merged_truth_ok}
+        "dz'/dy dropped": jacobian_ok, "refit turns the frame backwards": merged_truth_ok,
+        "transport: q/pT column of dy lost": transport_jacobian_ok,
+        "update: sign of the off-diagonal gain": update_ok,
+        "seed: sin(phi) variance with cos^4": prior_ok,
+        "transport: path length without the arc": crossings_ok}
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
