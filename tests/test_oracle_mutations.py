@@ -169,3 +169,37 @@ PINS = {"rotation turned the wrong way": closed_form_ok, "sign of ds'/dy": jacob
 def test_pin_catches_the_mistake(orc, mutant, name):
     assert PINS[name](orc), "the pin must pass on the oracle itself"
     assert not PINS[name](mutant(name)), f"the pin missed: {name}"
+
+
+CALIB = os.path.join(os.path.dirname(SRC), "calib.py")
+CALIB_MUTATIONS = {
+    "mean of the ratios instead of the ratio of the sums": ("    s2 = c.sum() / d.sum()\n    keep",
+                                                           "    s2 = (c / d).mean()\n    keep"),
+    "trim against the ratio, not ratio x ndf": ("        nxt = c <= trim * s2 * d", "        nxt = c <= trim * s2"),
+    "stop after the first round": ("        if same:\n            break", "        break"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CALIB_MUTATIONS))
+def test_fit_pins_catch_the_mistake(tmp_path, name):
+    """The chi^2 scale fit's pins (known scale, outliers, brute force) fail on a
+    copy of oracle/calib.py with one planted mistake."""
+    import importlib.util
+    from tests import test_async_calib as t
+    old, new = CALIB_MUTATIONS[name]
+    src = open(CALIB).read()
+    assert src.count(old) == 1, name
+    p = tmp_path / "calib_mutant.py"
+    p.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("calib_mutant", p)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    pins = (t.test_recovers_a_known_scale, t.test_gross_outliers_are_trimmed,
+            t.test_kept_set_is_the_largest_self_consistent_one)
+    assert all(passes(f) for f in pins), "the pins must pass on the oracle itself"
+    orig = t.chi2_scale_fit
+    try:
+        t.chi2_scale_fit = mod.chi2_scale_fit
+        assert not all(passes(f) for f in pins), f"the pins missed: {name}"
+    finally:
+        t.chi2_scale_fit = orig
