@@ -295,6 +295,15 @@ def test_launches_on_several_streams_give_the_same_tracks(tp):
         tuned = tp.tpc_track_autotune(t.ctx, [cs[6][0]], g, bz, reps=1)
         assert 1 <= tuned["streams"] <= 3
         same(ref[6], t.event(evs[6]), "tuned")
+        # launches left in flight on several streams, then the served form on
+        # the same context: every slot moves back to its own stream in order
+        tp.tpc_track_set_schedule(t.ctx, **{**tuned, "streams": 3})
+        for c, _ in cs[:3]:
+            tp.tpc_track_launch(t.ctx, [c], g, bz)
+        tks = [tp.tpc_track_submit(t.ctx, c, g, bz) for c, _ in cs]
+        for k, tk in enumerate(tks):
+            same(ref[k], tp.tpc_track_poll(t.ctx, tk, 60_000_000), ("served after launches", k))
+            tp.tpc_track_release(t.ctx, tk)
     finally:
         t.close()
 
