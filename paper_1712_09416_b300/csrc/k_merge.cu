@@ -187,8 +187,14 @@ __global__ void __launch_bounds__(kSortXThreads) k_mg_sortx(Launch L)
         }
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int b = si[i];
         L.mg_xs[t0 + i] = sx[i];
-        L.mg_xi[t0 + i] = si[i];
+        L.mg_xi[t0 + i] = b;
+        // the matcher's first tests read one 32-byte record per candidate
+        L.mg_pre[2 * (t0 + i)] = make_float4(sx[i], L.k_param[(size_t)b * 5 + 3],
+                                             L.k_param[(size_t)b * 5 + 4], L.k_cov[(size_t)b * 15 + 9]);
+        L.mg_pre[2 * (t0 + i) + 1] = make_float4(L.k_cov[(size_t)b * 15 + 13], L.k_cov[(size_t)b * 15 + 14],
+                                                 __int_as_float(b), 0.0f);
     }
 }
 
@@ -265,19 +271,20 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
                 const int k0 = warp_lower_bound(xs, ns, r.x + L.mg_dx_lo - 0.01f);
                 const int k1 = warp_lower_bound(xs, ns, r.x + L.mg_dx_hi + 0.01f);
                 for (int kk = k0 + lane; kk < k1; kk += 32) {
-                    const int b = L.mg_xi[s0 + kk];
-                    const float gap = L.k_x[b] - r.x;
+                    const float4 pa = L.mg_pre[2 * (s0 + kk)], pb = L.mg_pre[2 * (s0 + kk) + 1];
+                    const int b = __float_as_int(pb.z);
+                    const float gap = pa.x - r.x;
                     if (!(gap >= L.mg_dx_lo && gap <= L.mg_dx_hi)) continue;
                     // tan(lambda) and q/pT and their covariance block are left
                     // as they are by transport and rotation, so their 2x2 chi2
                     // bounds the 5x5 one from below: a pair over the cut there
                     // (with a margin for rounding) is over it in full
                     {
-                        const float dt = t_a - L.k_param[(size_t)b * 5 + 3];
-                        const float dq = q_a - L.k_param[(size_t)b * 5 + 4];
-                        const float s33 = c33 + L.k_cov[(size_t)b * 15 + 9];
-                        const float s43 = c43 + L.k_cov[(size_t)b * 15 + 13];
-                        const float s44 = c44 + L.k_cov[(size_t)b * 15 + 14];
+                        const float dt = t_a - pa.y;
+                        const float dq = q_a - pa.z;
+                        const float s33 = c33 + pa.w;
+                        const float s43 = c43 + pb.x;
+                        const float s44 = c44 + pb.y;
                         const float det = s33 * s44 - s43 * s43;
                         if (det > 0.0f &&
                             dt * dt * s44 - 2.0f * dt * dq * s43 + dq * dq * s33 > cut_pre * det)

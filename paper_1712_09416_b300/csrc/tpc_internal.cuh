@@ -163,6 +163,7 @@ struct Launch {
     int* mg_oidx; int* mg_ohoff;    // [t_cap] output index / hit offset before a track
     float4* mg_hxyz;            // [clusters] (x, y, z) of the hits of linked tracks, as k_hit_cid
     float* mg_xs; int* mg_xi;   // [t_cap] each sector's tracks by ascending x: x, track index
+    float4* mg_pre;             // [2 t_cap] the same order: (x, t, q/pT, C33), (C43, C44, index, 0)
     int* m_sector; float* m_x; float* m_param; float* m_cov; float* m_chi2; int* m_ndf;
     int* m_hit_off; int* m_hit_cid; int* m_sec_trk_off; int* m_sec_hit_off;
     Counters* cnt;

@@ -111,6 +111,7 @@ struct Slot {
     float4* mg_hxyz;
     float* mg_xs;
     int* mg_xi;
+    float4* mg_pre;
     int *m_sector, *m_ndf, *m_hit_off, *m_hit_cid, *m_sec_trk_off, *m_sec_hit_off;
     float *m_x, *m_param, *m_cov, *m_chi2;
     // host side
@@ -308,6 +309,7 @@ size_t layout(Slot& s, char* base)
     s.mg_hxyz = (float4*)take(16 * k.n);
     s.mg_xs = (float*)take(4 * (size_t)k.t);
     s.mg_xi = (int*)take(4 * (size_t)k.t);
+    s.mg_pre = (float4*)take(32 * (size_t)k.t);
     s.m_sector = (int*)take(4 * (size_t)k.t);
     s.m_ndf = (int*)take(4 * (size_t)k.t);
     s.m_hit_off = (int*)take(4 * ((size_t)k.t + 1));
@@ -639,6 +641,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.mg_hxyz = s.mg_hxyz;
     L.mg_xs = s.mg_xs;
     L.mg_xi = s.mg_xi;
+    L.mg_pre = s.mg_pre;
     L.m_sector = s.m_sector;
     L.m_x = s.m_x;
     L.m_param = s.m_param;
