@@ -121,7 +121,7 @@ typedef struct {
      *     outer track's frame) lies in [merge_dx_lo, merge_dx_hi] cm and the
      *     5-parameter chi2 of the two states is <= merge_chi2;
      *   - tracks are linked when each is the other's admissible partner of
-     *     least chi2; a chain of up to 16 tracks is refitted from its
+     *     least chi2; a chain (of any length) is refitted from its
      *     outermost hit inward (Kalman filter, frames turned between tracks).
      * A merged track takes the place (and sector) of its innermost track;
      * its state is at the innermost hit, ndf = 2 * hits - 5, and its hit list
@@ -396,6 +396,13 @@ typedef struct {
 } tpc_dump_tracklet;
 int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t cap,
                          size_t* used);
+
+/* The same dump for event `event` (0 .. n_ev - 1) of the last completed
+ * launch, so that each event of a batch can be compared stage by stage; cids,
+ * rows and sectors are those of that event.  TPC_EINVAL for an event index
+ * outside the launch. */
+int tpc_track_debug_dump_event(tpc_track_ctx* ctx, int stage, int event, void* host_buf,
+                               size_t cap, size_t* used);
 
 /* Neighbour links of one event without any allocation (this entry point has
  * no counterpart in the paper; it serves callers that cannot allocate device

@@ -22,7 +22,8 @@ _SRC = os.path.join(_HERE, "tpc_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
-TIE_CHI2_CUT, TIE_CHI2_PAIR, TIE_SIN, TIE_EDGE = 1, 2, 4, 8
+TIE_CHI2_CUT, TIE_CHI2_PAIR, TIE_SIN, TIE_EDGE, TIE_CHAIN = 1, 2, 4, 8, 512
+C2_TIE_PAIR, C2_TIE_CUT, C2_TIE_WIN = 1, 2, 4
 MTIE_CUT, MTIE_PAIR, MTIE_DX, MTIE_SIN = 16, 32, 64, 128
 
 
@@ -53,7 +54,8 @@ def lib():
 class OrcConfig(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "half_angle", "z_max", "bz", "sigma_y", "sigma_z", "chi2_hit", "sin_max", "edge_margin",
-        "seed_var_s", "seed_var_t", "seed_var_q", "tie_chi2", "tie_sin", "tie_edge")] + \
+        "seed_var_s", "seed_var_t", "seed_var_q", "tie_chi2", "tie_sin", "tie_edge", "tie_d",
+        "tie_win")] + \
         [(n, C.c_float) for n in ("slope_win_y", "slope_win_z", "d_max", "pad0")] + \
         [(n, C.c_int32) for n in ("n_rows", "n_sectors_phi", "split_z", "max_gap", "min_chain",
                                   "min_tracklet_hits", "min_track_hits", "pad1")]
@@ -63,7 +65,8 @@ _P = C.c_void_p
 
 
 class OrcResult(C.Structure):
-    _fields_ = [("up", _P), ("dn", _P), ("up64", _P), ("dn64", _P), ("up_c", _P), ("dn_c", _P),
+    _fields_ = [("up", _P), ("dn", _P), ("c2_tie", _P), ("up32", _P), ("dn32", _P),
+                ("up_c", _P), ("dn_c", _P),
                 ("cap_tracklets", C.c_int64),
                 ("t_start", _P), ("t_sector", _P), ("t_chain_len", _P), ("t_valid", _P),
                 ("t_nhits", _P), ("t_first_row", _P), ("t_last_row", _P), ("t_flags", _P),
@@ -72,7 +75,8 @@ class OrcResult(C.Structure):
                 ("k_tracklet", _P), ("k_sector", _P), ("k_ndf", _P), ("k_x", _P), ("k_p", _P),
                 ("k_C", _P), ("k_chi2", _P), ("k_hit_off", _P), ("k_hit_cid", _P),
                 ("n_tracklets", C.c_int64), ("n_tracks", C.c_int64), ("n_track_hits", C.c_int64),
-                ("n_links", C.c_int64), ("n_link_flips64", C.c_int64), ("n_starts", C.c_int64)]
+                ("n_links", C.c_int64), ("n_link_flips32", C.c_int64), ("n_c2_ties", C.c_int64),
+                ("n_starts", C.c_int64)]
 
 
 @dataclass
@@ -96,6 +100,8 @@ class Params:
     tie_chi2: float = 0.05
     tie_sin: float = 1e-4
     tie_edge: float = 1e-3
+    tie_d: float = 1e-4
+    tie_win: float = 2e-5
 
 
 def make_config(params: Params, *, n_rows: int, n_sectors_phi: int, split_z: int,
@@ -106,6 +112,7 @@ def make_config(params: Params, *, n_rows: int, n_sectors_phi: int, split_z: int
     c.chi2_hit, c.sin_max, c.edge_margin = params.chi2_hit, params.sin_max, params.edge_margin
     c.seed_var_s, c.seed_var_t, c.seed_var_q = params.seed_var_s, params.seed_var_t, params.seed_var_q
     c.tie_chi2, c.tie_sin, c.tie_edge = params.tie_chi2, params.tie_sin, params.tie_edge
+    c.tie_d, c.tie_win = params.tie_d, params.tie_win
     c.slope_win_y, c.slope_win_z, c.d_max = params.slope_win_y, params.slope_win_z, params.d_max
     c.n_rows, c.n_sectors_phi, c.split_z = n_rows, n_sectors_phi, int(split_z)
     c.max_gap, c.min_chain = params.max_gap, params.min_chain
@@ -118,8 +125,12 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
 
-def track_event(ev, params: Params | None = None, *, shadow64: bool = True) -> dict:
-    """Run C2-C8 on one event; returns every stage's arrays as numpy (cids)."""
+def track_event(ev, params: Params | None = None, *, shadow32: bool = False) -> dict:
+    """Run C2-C8 on one event; returns every stage's arrays as numpy (cids).
+
+    ``up``/``dn`` are the binary64 neighbour decision and ``c2_tie`` its
+    near-tie bits per hit; with shadow32 the binary32 restatement of the same
+    rule is returned too (``up32``/``dn32``, diagnostic only)."""
     params = params or Params()
     n = int(ev.n)
     R = len(ev.row_x)
@@ -134,8 +145,9 @@ def track_event(ev, params: Params | None = None, *, shadow64: bool = True) -> d
     cap_k = cap_t
     o = {
         "up": np.empty(n, np.int32), "dn": np.empty(n, np.int32),
-        "up64": np.empty(n, np.int32) if shadow64 else None,
-        "dn64": np.empty(n, np.int32) if shadow64 else None,
+        "c2_tie": np.empty(n, np.int32),
+        "up32": np.empty(n, np.int32) if shadow32 else None,
+        "dn32": np.empty(n, np.int32) if shadow32 else None,
         "up_c": np.empty(n, np.int32), "dn_c": np.empty(n, np.int32),
         "t_start": np.empty(cap_t, np.int32), "t_sector": np.empty(cap_t, np.int32),
         "t_chain_len": np.empty(cap_t, np.int32), "t_valid": np.empty(cap_t, np.int32),
@@ -161,7 +173,8 @@ def track_event(ev, params: Params | None = None, *, shadow64: bool = True) -> d
         raise RuntimeError(f"oracle returned {rc}")
     nt, nk, nh = res.n_tracklets, res.n_tracks, res.n_track_hits
     out = {"status": rc, "n_tracklets": nt, "n_tracks": nk, "n_track_hits": nh,
-           "n_links": res.n_links, "n_link_flips64": res.n_link_flips64,
+           "n_links": res.n_links, "n_link_flips32": res.n_link_flips32,
+           "n_c2_ties": res.n_c2_ties,
            "n_starts": res.n_starts}
     for k, a in o.items():
         if a is None:

@@ -28,11 +28,15 @@
  *             a track keeps its owned hits.
  *   C9        iterated backward refit on a fixed hit set (tests only).
  *
- * Floating point: every fit quantity is binary64.  The neighbour decision of
- * C2 (an argmin whose result is an integer link) is taken in binary32, the
- * precision of the GPU tracker, with each operation rounded on its own (this
- * file is compiled with -ffp-contract=off); a binary64 shadow of the same rule
- * is evaluated alongside and its disagreements are counted.
+ * Floating point: everything is binary64, the neighbour decision of C2
+ * included (slopes are plain quotients of binary64 differences).  Where that
+ * decision could go the other way under a small rounding of D or of a window
+ * test, the hit carries near-tie bits (ORC_C2_TIE_*): the best and the
+ * second-best pair within tie_d, the best D within tie_d of D_MAX, or a
+ * candidate within tie_win cm of a window edge.  A binary32 restatement of
+ * the same rule (one rounding per operation; this file is compiled with
+ * -ffp-contract=off) can be evaluated alongside as a diagnostic; it feeds
+ * nothing downstream.
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,6 +61,8 @@ typedef struct {
     double tie_chi2;    /* near-tie width on chi2 decisions */
     double tie_sin;     /* near-tie width on |s| vs sin_max */
     double tie_edge;    /* near-tie width (cm) on the edge stops */
+    double tie_d;       /* near-tie width on the C2 kink score D */
+    double tie_win;     /* near-tie width (cm) on the C2 slope windows */
     float slope_win_y, slope_win_z, d_max, pad0;
     int32_t n_rows, n_sectors_phi, split_z;
     int32_t max_gap, min_chain, min_tracklet_hits, min_track_hits;
@@ -65,10 +71,11 @@ typedef struct {
 
 typedef struct {
     /* links by cid, -1 = none; all [n] */
-    int32_t* up;     /* C2, binary32 decision */
+    int32_t* up;     /* C2, binary64 decision */
     int32_t* dn;
-    int32_t* up64;   /* C2, binary64 shadow */
-    int32_t* dn64;
+    int32_t* c2_tie; /* C2 near-tie bits per hit (ORC_C2_TIE_*) */
+    int32_t* up32;   /* C2, binary32 restatement (diagnostic, may be NULL) */
+    int32_t* dn32;
     int32_t* up_c;   /* C3 */
     int32_t* dn_c;
     /* tracklets (one per chain of >= min_chain hits), capacity cap_tracklets */
@@ -102,7 +109,7 @@ typedef struct {
     int32_t* k_hit_cid;   /* [n] */
     /* counters (out) */
     int64_t n_tracklets, n_tracks, n_track_hits;
-    int64_t n_links, n_link_flips64, n_starts;
+    int64_t n_links, n_link_flips32, n_c2_ties, n_starts;
 } orc_result;
 
 enum {
@@ -110,6 +117,13 @@ enum {
     ORC_TIE_CHI2_PAIR = 2,  /* second-best chi2 within tie_chi2 of the best */
     ORC_TIE_SIN = 4,        /* |s| within tie_sin of sin_max at a transport */
     ORC_TIE_EDGE = 8,       /* |y| or |z| within tie_edge of the stop bound */
+    ORC_TIE_CHAIN = 512,    /* a chain hit lies outside the chi2 acceptance */
+};
+
+enum {
+    ORC_C2_TIE_PAIR = 1,    /* second-best pair within tie_d of the best D */
+    ORC_C2_TIE_CUT = 2,     /* best D within tie_d of D_MAX */
+    ORC_C2_TIE_WIN = 4,     /* a candidate within tie_win cm of a window edge */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -283,12 +297,74 @@ static int row_list(const hits_t* H, int sec, int r, const int32_t** out)
 /*
  * Hit h on row r (1 <= r <= R-2).  Candidate c on row r+-1 is admissible iff
  * |y_c - y_h| <= SY |x_c - x_h| and |z_c - z_h| <= SZ |x_c - x_h|.  Slopes
- * sy_u = (y_u - y_h)/(x_u - x_h), sy_d = (y_h - y_d)/(x_h - x_d), likewise z,
- * each taken as the coordinate difference times the rounded reciprocal of the
- * row spacing; score D = (sy_u - sy_d)^2 + (sz_u - sz_d)^2.  The admissible
- * pair (d, u) with the least D wins, exact ties going to the lower cid(u) and
- * then the lower cid(d); the links are set iff D <= D_MAX.  Binary32, one
- * rounding per operation.
+ * sy_u = (y_u - y_h)/(x_u - x_h), sy_d = (y_h - y_d)/(x_h - x_d), likewise z;
+ * score D = (sy_u - sy_d)^2 + (sz_u - sz_d)^2, the straight-line kink.  The
+ * admissible pair (d, u) with the least D wins, exact ties going to the lower
+ * cid(u) and then the lower cid(d); the links are set iff D <= D_MAX.
+ * Binary64 throughout.  *tie receives the near-tie bits of the decision:
+ * ORC_C2_TIE_PAIR when the best D is at most D_MAX + tie_d and another
+ * admissible pair lies within tie_d of it, ORC_C2_TIE_CUT when the best D
+ * lies within tie_d of D_MAX, ORC_C2_TIE_WIN when a candidate lies within
+ * tie_win cm of the edge of its slope window (inside the window widened by
+ * tie_win and outside the window narrowed by it, in y or in z).
+ */
+static void best_pair_f64(const hits_t* H, const orc_config* cfg, int sec, int r, int32_t h,
+                          int32_t* up, int32_t* dn, int32_t* tie)
+{
+    const int32_t *lu, *ld;
+    const int nu = row_list(H, sec, r + 1, &lu);
+    const int nd = row_list(H, sec, r - 1, &ld);
+    const double xh = H->xr[r], xu = H->xr[r + 1], xd = H->xr[r - 1];
+    const double wyu = cfg->slope_win_y * fabs(xu - xh), wzu = cfg->slope_win_z * fabs(xu - xh);
+    const double wyd = cfg->slope_win_y * fabs(xd - xh), wzd = cfg->slope_win_z * fabs(xd - xh);
+    const double tw = cfg->tie_win, dmax = cfg->d_max;
+    int flags = 0;
+    /* window edges: a candidate inside the widened window but not inside the
+     * narrowed one sits within tie_win of an edge */
+    for (int a = 0; a < nu + nd; ++a) {
+        const int32_t c = a < nu ? lu[a] : ld[a - nu];
+        const double wy = a < nu ? wyu : wyd, wz = a < nu ? wzu : wzd;
+        const double ay = fabs(H->y[c] - H->y[h]), az = fabs(H->z[c] - H->z[h]);
+        if (ay <= wy + tw && az <= wz + tw && (ay > wy - tw || az > wz - tw))
+            flags |= ORC_C2_TIE_WIN;
+    }
+    double bestD = 0.0, second = INFINITY;
+    int32_t bu = -1, bd = -1;
+    for (int a = 0; a < nu; ++a) {
+        const int32_t u = lu[a];
+        if (!(fabs(H->y[u] - H->y[h]) <= wyu) || !(fabs(H->z[u] - H->z[h]) <= wzu)) continue;
+        const double syu = (H->y[u] - H->y[h]) / (xu - xh);
+        const double szu = (H->z[u] - H->z[h]) / (xu - xh);
+        for (int b = 0; b < nd; ++b) {
+            const int32_t d = ld[b];
+            if (!(fabs(H->y[d] - H->y[h]) <= wyd) || !(fabs(H->z[d] - H->z[h]) <= wzd)) continue;
+            const double syd = (H->y[h] - H->y[d]) / (xh - xd);
+            const double szd = (H->z[h] - H->z[d]) / (xh - xd);
+            const double D = (syu - syd) * (syu - syd) + (szu - szd) * (szu - szd);
+            if (bu < 0 || D < bestD || (D == bestD && (u < bu || (u == bu && d < bd)))) {
+                if (bu >= 0) second = bestD;
+                bestD = D;
+                bu = u;
+                bd = d;
+            } else if (D < second) {
+                second = D;
+            }
+        }
+    }
+    if (bu >= 0 && bestD <= dmax + cfg->tie_d && second - bestD <= cfg->tie_d)
+        flags |= ORC_C2_TIE_PAIR;
+    if (bu >= 0 && fabs(bestD - dmax) <= cfg->tie_d) flags |= ORC_C2_TIE_CUT;
+    *tie = flags;
+    if (bu >= 0 && bestD <= dmax) { *up = bu; *dn = bd; }
+    else { *up = -1; *dn = -1; }
+}
+
+/*
+ * Diagnostic only: the same rule restated in binary32 (differences rounded,
+ * slopes as differences times the rounded reciprocal of the row spacing,
+ * one rounding per operation).  Its links are compared with the binary64
+ * decision to show that they differ only at hits with near-tie bits; no
+ * later step uses them.
  */
 static void best_pair_f32(const hits_t* H, const orc_config* cfg, int sec, int r, int32_t h,
                           int32_t* up, int32_t* dn)
@@ -316,44 +392,14 @@ static void best_pair_f32(const hits_t* H, const orc_config* cfg, int sec, int r
             const float ey = syu - syd, ez = szu - szd;
             const float ey2 = ey * ey, ez2 = ez * ez;
             const float D = ey2 + ez2;
-            int better = 0;
-            if (bu < 0 || D < bestD) better = 1;
-            else if (D == bestD && (u < bu || (u == bu && d < bd))) better = 1;
-            if (better) { bestD = D; bu = u; bd = d; }
-        }
-    }
-    if (bu >= 0 && bestD <= cfg->d_max) { *up = bu; *dn = bd; }
-    else { *up = -1; *dn = -1; }
-}
-
-/* the same rule in binary64 (shadow, for counting binary32 decision flips) */
-static void best_pair_f64(const hits_t* H, const orc_config* cfg, int sec, int r, int32_t h,
-                          int32_t* up, int32_t* dn)
-{
-    const int32_t *lu, *ld;
-    const int nu = row_list(H, sec, r + 1, &lu);
-    const int nd = row_list(H, sec, r - 1, &ld);
-    const double xh = H->xr[r], xu = H->xr[r + 1], xd = H->xr[r - 1];
-    const double SY = cfg->slope_win_y, SZ = cfg->slope_win_z;
-    double bestD = 0.0;
-    int32_t bu = -1, bd = -1;
-    for (int a = 0; a < nu; ++a) {
-        const int32_t u = lu[a];
-        if (!(fabs(H->y[u] - H->y[h]) <= SY * fabs(xu - xh))) continue;
-        if (!(fabs(H->z[u] - H->z[h]) <= SZ * fabs(xu - xh))) continue;
-        const double syu = (H->y[u] - H->y[h]) / (xu - xh), szu = (H->z[u] - H->z[h]) / (xu - xh);
-        for (int b = 0; b < nd; ++b) {
-            const int32_t d = ld[b];
-            if (!(fabs(H->y[d] - H->y[h]) <= SY * fabs(xd - xh))) continue;
-            if (!(fabs(H->z[d] - H->z[h]) <= SZ * fabs(xd - xh))) continue;
-            const double syd = (H->y[h] - H->y[d]) / (xh - xd), szd = (H->z[h] - H->z[d]) / (xh - xd);
-            const double D = (syu - syd) * (syu - syd) + (szu - szd) * (szu - szd);
             if (bu < 0 || D < bestD || (D == bestD && (u < bu || (u == bu && d < bd)))) {
-                bestD = D; bu = u; bd = d;
+                bestD = D;
+                bu = u;
+                bd = d;
             }
         }
     }
-    if (bu >= 0 && bestD <= (double)cfg->d_max) { *up = bu; *dn = bd; }
+    if (bu >= 0 && bestD <= cfg->d_max) { *up = bu; *dn = bd; }
     else { *up = -1; *dn = -1; }
 }
 
@@ -442,6 +488,14 @@ static int32_t search_row(const hits_t* H, const orc_config* cfg, int sec, int r
 }
 
 /*
+ * Near-tie bits (T->flags): a chi2 decision within tie_chi2 of the cut or of
+ * the runner-up, |s| within tie_sin of sin_max at a transport, |y| or |z|
+ * within tie_edge of a stop bound, and ORC_TIE_CHAIN when a chain hit is
+ * updated (without a test, as the chain prescribes) with a chi2 increment
+ * above chi2_hit: such a chain is not one helix (the cellular automaton
+ * joined two particles), the fit is pulled far outside its own covariance,
+ * and its later decisions depend on the precision of the arithmetic.
+ *
  * Chain h[0..k] on consecutive rows of sector sec (k + 1 >= min_chain).
  * Seed at x of h0: (y, z) of h0, tan(phi) and dz/dx from the chord h0 -> hk,
  * s = tan(phi)/sqrt(1 + tan^2 phi), t = (dz/dx) cos(phi), q/pT = 0, C = seed.
@@ -485,7 +539,8 @@ static void build_tracklet(const hits_t* H, const orc_config* cfg, int sec,
             break;
         }
         x = H->xr[r];
-        orc_update(p, C, H->y[chain[i]], H->z[chain[i]], vy, vz);
+        if (orc_update(p, C, H->y[chain[i]], H->z[chain[i]], vy, vz) > cfg->chi2_hit)
+            flags |= ORC_TIE_CHAIN;
         fwd[r] = chain[i];
         last = r;
         memcpy(pL, p, sizeof(pL));
@@ -631,17 +686,20 @@ int orc_track_event(const orc_config* cfg, const float* row_x, int64_t n, const 
 
     /* C2 */
     res->n_links = 0;
-    res->n_link_flips64 = 0;
+    res->n_link_flips32 = 0;
+    res->n_c2_ties = 0;
     for (int64_t i = 0; i < n; ++i) {
         res->up[i] = res->dn[i] = -1;
-        if (res->up64) res->up64[i] = res->dn64[i] = -1;
+        res->c2_tie[i] = 0;
+        if (res->up32) res->up32[i] = res->dn32[i] = -1;
         const int r = row[i];
         if (r < 1 || r > R - 2) continue;
-        best_pair_f32(&H, cfg, sector[i], r, (int32_t)i, &res->up[i], &res->dn[i]);
+        best_pair_f64(&H, cfg, sector[i], r, (int32_t)i, &res->up[i], &res->dn[i], &res->c2_tie[i]);
         if (res->up[i] >= 0) res->n_links++;
-        if (res->up64) {
-            best_pair_f64(&H, cfg, sector[i], r, (int32_t)i, &res->up64[i], &res->dn64[i]);
-            if (res->up64[i] != res->up[i] || res->dn64[i] != res->dn[i]) res->n_link_flips64++;
+        if (res->c2_tie[i]) res->n_c2_ties++;
+        if (res->up32) {
+            best_pair_f32(&H, cfg, sector[i], r, (int32_t)i, &res->up32[i], &res->dn32[i]);
+            if (res->up32[i] != res->up[i] || res->dn32[i] != res->dn[i]) res->n_link_flips32++;
         }
     }
     /* C3: mutual links only */
@@ -862,8 +920,10 @@ void orc_seed(double x0, double y0, double z0, double x1, double y1, double z1, 
  *      change of segment the state is turned into the inner segment's frame
  *      and transported to its outermost hit).  The result is the state at
  *      s_1's innermost hit, chi2 the sum of the increments, ndf = 2 * hits - 5.
- *      A chain whose refit fails (a transport or rotation fails), or of more
- *      than 16 tracks, is not merged.
+ *      A chain whose refit fails (a transport or rotation fails) is not
+ *      merged; chains of any length are refitted (every track has at most
+ *      one incoming and one outgoing link, so a chain from a head without an
+ *      incoming link ends).
  *
  * Near-tie bits (for the parity tests) mark the tracks whose links could
  * change under rounding: a chi2 within tie_chi2 of the cut or of the next
@@ -1162,7 +1222,6 @@ int orc_merge(const orc_config* cfg, const orc_merge_config* mc, const float* ro
         if (link_in[h] >= 0 || link_out[h] < 0) continue;
         int m = 0;
         for (int64_t a = h; a >= 0 && m < T; a = link_out[a]) chain[m++] = a;
-        if (m > 16) continue;  /* chains of more than 16 tracks are left unmerged */
         /* start: outer state of the outermost segment, seed covariance */
         const int64_t so = chain[m - 1];
         double x = xo[so], p[5], C[5][5];

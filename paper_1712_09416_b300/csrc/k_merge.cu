@@ -18,7 +18,7 @@
 //      [dx_lo, dx_hi] and r^T (C_a' + C_b)^-1 r <= chi2 cut.
 //   M4 link a -> b iff each is the other's admissible partner of least chi2
 //      (ties to the lower index).
-//   M5 refit of a chain (<= 16 tracks): the outermost track's outer state,
+//   M5 refit of a chain (any length): the outermost track's outer state,
 //      covariance reset to the seed covariance, every hit inward (frames
 //      turned at each change of track); result at the innermost hit.
 //
@@ -41,7 +41,6 @@ namespace tpc {
 namespace {
 
 constexpr int kMgThreads = 128;
-constexpr int kMaxChain = 16;
 constexpr int kScanThreads = 256;
 constexpr int kScanPer = kMgTile / kScanThreads;
 
@@ -361,13 +360,15 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_refit(Launch L)
     const int N = L.n_sectors_phi;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < T; h += gridDim.x * blockDim.x) {
         if (L.mg_in[h] >= 0 || L.mg_link[h] < 0) continue;
+        // every track has at most one incoming and one outgoing link, so the
+        // chain from a head ends within T steps (the bound only guards reads)
         int so = h, m = 1, nh = L.k_hit_off[h + 1] - L.k_hit_off[h];
-        while (L.mg_link[so] >= 0 && m <= kMaxChain) {
+        while (L.mg_link[so] >= 0 && m <= T) {
             so = L.mg_link[so];
             nh += L.k_hit_off[so + 1] - L.k_hit_off[so];
             ++m;
         }
-        if (m > kMaxChain) continue;  // too long: left unmerged
+        if (m > T) continue;
         const MgState& O = L.mg_st[so];
         if (!O.ok) continue;
         Fit f;

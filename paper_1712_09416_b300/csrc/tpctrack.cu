@@ -926,22 +926,31 @@ int collect_to_tickets(tpc_track_ctx* ctx, Slot& s, std::vector<std::unique_ptr<
 // --------------------------------------------------------------------------
 // debug dumps (event 0 of the last completed launch)
 // --------------------------------------------------------------------------
-int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* used)
+int dump(tpc_track_ctx* ctx, Slot& s, int stage, int event, void* buf, size_t cap, size_t* used)
 {
     LaunchInfo& I = s.info;
     if (!I.done) return fail(ctx, TPC_EINVAL, "no completed launch to dump");
+    if (event < 0 || event >= I.n_ev) return fail(ctx, TPC_EINVAL, "no such event in the last launch");
     const int R = I.R;
-    const int RS0 = I.ev_n_sec[0] * R;  // rows of event 0 (sectors first in the layout)
-    const long long n0 = I.ev_n[0];
-    std::vector<int> row_off(RS0 + 1);
-    CUDA_TRY(ctx, cudaMemcpy(row_off.data(), s.row_off, 4 * (RS0 + 1), cudaMemcpyDeviceToHost));
-    const int nh = row_off[RS0];  // sorted hits of event 0
+    // an event's sectors are consecutive in the launch's (sector, row) list,
+    // and so are its sorted hits
+    const int RSb = I.ev_sec_base[event] * R;
+    const int RSe = RSb + I.ev_n_sec[event] * R;
+    const long long n0 = I.ev_n[event];
+    std::vector<int> row_all(RSe + 2);
+    CUDA_TRY(ctx, cudaMemcpy(row_all.data(), s.row_off, 4 * (size_t)(RSe + 1), cudaMemcpyDeviceToHost));
+    const int hb = row_all[RSb];   // first sorted hit of the event
+    const int nh = row_all[RSe] - hb;  // its sorted hits
+    std::vector<int> row_off(row_all.begin() + RSb, row_all.begin() + RSe + 1);
+    for (int& v : row_off) v -= hb;
     std::vector<int> hcid(nh), hrow(nh);
     if (nh) {
-        CUDA_TRY(ctx, cudaMemcpy(hcid.data(), s.hcid, 4 * (size_t)nh, cudaMemcpyDeviceToHost));
-        CUDA_TRY(ctx, cudaMemcpy(hrow.data(), s.hrow, 4 * (size_t)nh, cudaMemcpyDeviceToHost));
+        CUDA_TRY(ctx, cudaMemcpy(hcid.data(), s.hcid + hb, 4 * (size_t)nh, cudaMemcpyDeviceToHost));
+        CUDA_TRY(ctx, cudaMemcpy(hrow.data(), s.hrow + hb, 4 * (size_t)nh, cudaMemcpyDeviceToHost));
     }
-    auto row_of = [&](int i) { return (hrow[i] >> 8) * R + (hrow[i] & 255); };
+    const int sb = I.ev_sec_base[event];
+    // row index within the event's rows (hrow holds the launch-wide sector)
+    auto row_of = [&](int i) { return ((hrow[i] >> 8) - sb) * R + (hrow[i] & 255); };
     std::vector<char> out;
     auto put = [&](const void* p, size_t b) {
         const char* c = (const char*)p;
@@ -952,8 +961,8 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* 
     } else if (stage == TPC_DUMP_LINKS || stage == TPC_DUMP_CLEAN) {
         std::vector<int16_t> u(nh), d(nh);
         if (nh) {
-            CUDA_TRY(ctx, cudaMemcpy(u.data(), stage == TPC_DUMP_LINKS ? s.up : s.upc, 2 * (size_t)nh, cudaMemcpyDeviceToHost));
-            CUDA_TRY(ctx, cudaMemcpy(d.data(), stage == TPC_DUMP_LINKS ? s.dn : s.dnc, 2 * (size_t)nh, cudaMemcpyDeviceToHost));
+            CUDA_TRY(ctx, cudaMemcpy(u.data(), (stage == TPC_DUMP_LINKS ? s.up : s.upc) + hb, 2 * (size_t)nh, cudaMemcpyDeviceToHost));
+            CUDA_TRY(ctx, cudaMemcpy(d.data(), (stage == TPC_DUMP_LINKS ? s.dn : s.dnc) + hb, 2 * (size_t)nh, cudaMemcpyDeviceToHost));
         }
         std::vector<int32_t> uc(n0, -1), dc(n0, -1);
         for (int i = 0; i < nh; ++i) {
@@ -971,14 +980,16 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* 
             CUDA_TRY(ctx, cudaMemcpy(st.data(), s.starts, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
             CUDA_TRY(ctx, cudaMemcpy(tl.data(), s.tl, sizeof(TrackletHdr) * (size_t)ns, cudaMemcpyDeviceToHost));
         }
-        std::vector<std::pair<int, int>> order;  // (start cid, tracklet) of event 0
+        std::vector<std::pair<int, int>> order;  // (start cid, tracklet) of the event
         for (int t = 0; t < ns; ++t)
-            if (st[t] < nh) order.push_back({hcid[st[t]], t});
+            if (st[t] >= hb && st[t] < hb + nh) order.push_back({hcid[st[t] - hb], t});
         std::sort(order.begin(), order.end());
         if (stage == TPC_DUMP_STARTS) {
             for (auto& o : order) put(&o.first, 4);
         } else {
-            std::vector<int32_t> rh((size_t)R);
+            // the rowhit rows of every start at once (global sorted indices)
+            std::vector<int32_t> rh_all((size_t)ns * R);
+            if (ns) CUDA_TRY(ctx, cudaMemcpy(rh_all.data(), s.tl_rowhit, 4 * (size_t)ns * R, cudaMemcpyDeviceToHost));
             int32_t count = 0;
             for (auto& o : order)
                 if (tl[o.second].chain_len >= s.info.L.min_chain) ++count;
@@ -989,7 +1000,7 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* 
                 tpc_dump_tracklet D;
                 std::memset(&D, 0, sizeof(D));
                 D.start_cid = o.first;
-                D.sector = hrow[H.start] >> 8;
+                D.sector = (hrow[H.start - hb] >> 8) - sb;
                 D.valid = H.valid;
                 D.nhits = H.nhits;
                 D.first_row = H.first;
@@ -1000,16 +1011,16 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, void* buf, size_t cap, size_t* 
                 std::memcpy(D.cov, H.C, sizeof(D.cov));
                 D.chi2 = H.chi2;
                 put(&D, sizeof(D));
-                CUDA_TRY(ctx, cudaMemcpy(rh.data(), s.tl_rowhit + (size_t)o.second * R, 4 * (size_t)R, cudaMemcpyDeviceToHost));
+                const int32_t* rh = rh_all.data() + (size_t)o.second * R;
                 std::vector<int32_t> rc(R, -1);
                 for (int r = H.first; r <= H.last && r >= 0; ++r)
-                    if (rh[r] >= 0 && rh[r] < nh) rc[r] = hcid[rh[r]];
+                    if (rh[r] >= hb && rh[r] < hb + nh) rc[r] = hcid[rh[r] - hb];
                 put(rc.data(), 4 * (size_t)R);
             }
         }
     } else if (stage == TPC_DUMP_WEIGHTS) {
         std::vector<unsigned long long> w(nh);
-        if (nh) CUDA_TRY(ctx, cudaMemcpy(w.data(), s.weight, 8 * (size_t)nh, cudaMemcpyDeviceToHost));
+        if (nh) CUDA_TRY(ctx, cudaMemcpy(w.data(), s.weight + hb, 8 * (size_t)nh, cudaMemcpyDeviceToHost));
         std::vector<unsigned long long> wc(n0, 0ULL);
         for (int i = 0; i < nh; ++i) wc[hcid[i]] = w[i];
         put(wc.data(), 8 * (size_t)n0);
@@ -1628,7 +1639,15 @@ int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t c
 {
     if (!ctx) return TPC_EINVAL;
     cudaSetDevice(ctx->cfg.device);
-    return dump(ctx, *ctx->slots[ctx->last_slot], stage, host_buf, cap, used);
+    return dump(ctx, *ctx->slots[ctx->last_slot], stage, 0, host_buf, cap, used);
+}
+
+int tpc_track_debug_dump_event(tpc_track_ctx* ctx, int stage, int event, void* host_buf,
+                               size_t cap, size_t* used)
+{
+    if (!ctx) return TPC_EINVAL;
+    cudaSetDevice(ctx->cfg.device);
+    return dump(ctx, *ctx->slots[ctx->last_slot], stage, event, host_buf, cap, used);
 }
 
 const char* tpc_track_last_error(const tpc_track_ctx* ctx)

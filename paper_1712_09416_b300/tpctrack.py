@@ -25,7 +25,8 @@ EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "
             "tpc_track_release", "tpc_track_get_counters", "tpc_track_stream",
             "tpc_track_set_profiling", "tpc_track_kernel_times",
             "tpc_track_get_schedule", "tpc_track_set_schedule", "tpc_track_autotune",
-            "tpc_track_debug_dump", "tpc_track_last_error", "tpc_track_destroy",
+            "tpc_track_debug_dump", "tpc_track_debug_dump_event", "tpc_track_last_error",
+            "tpc_track_destroy",
             "tpc_track_links_noalloc", "tpc_track_set_params", "tpc_track_get_params",
             "tpc_track_ticket_params", "tpc_async_create", "tpc_async_start", "tpc_async_poll",
             "tpc_async_get_stats", "tpc_async_destroy", "tpc_chi2_calib_create",
@@ -151,6 +152,8 @@ def lib():
                                          C.POINTER(tpc_geometry), C.c_float, C.c_int,
                                          C.POINTER(tpc_track_schedule)]
         L.tpc_track_debug_dump.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.tpc_track_debug_dump_event.argtypes = [P, C.c_int, C.c_int, P, C.c_size_t,
+                                                 C.POINTER(C.c_size_t)]
         L.tpc_track_last_error.argtypes = [P]
         L.tpc_track_last_error.restype = C.c_char_p
         L.tpc_track_destroy.argtypes = [P]
@@ -552,11 +555,11 @@ def tpc_track_autotune(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz
     return _schedule_dict(s)
 
 
-def tpc_track_debug_dump(ctx, stage: int) -> bytes:
+def tpc_track_debug_dump(ctx, stage: int, event: int = 0) -> bytes:
     used = C.c_size_t()
-    _check(ctx, lib().tpc_track_debug_dump(ctx, stage, None, 0, C.byref(used)))
+    _check(ctx, lib().tpc_track_debug_dump_event(ctx, stage, event, None, 0, C.byref(used)))
     buf = C.create_string_buffer(max(1, used.value))
-    _check(ctx, lib().tpc_track_debug_dump(ctx, stage, buf, used.value, C.byref(used)))
+    _check(ctx, lib().tpc_track_debug_dump_event(ctx, stage, event, buf, used.value, C.byref(used)))
     return buf.raw[:used.value]
 
 
@@ -582,21 +585,22 @@ def tpc_track_destroy(ctx):
 # decoded debug dumps
 # --------------------------------------------------------------------------
 
-def dump_links(ctx, n: int, clean: bool = False) -> tuple[np.ndarray, np.ndarray]:
-    b = np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_CLEAN if clean else TPC_DUMP_LINKS), np.int32)
+def dump_links(ctx, n: int, clean: bool = False, event: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    b = np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_CLEAN if clean else TPC_DUMP_LINKS, event),
+                      np.int32)
     return b[:n].copy(), b[n:2 * n].copy()
 
 
-def dump_starts(ctx) -> np.ndarray:
-    return np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_STARTS), np.int32).copy()
+def dump_starts(ctx, event: int = 0) -> np.ndarray:
+    return np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_STARTS, event), np.int32).copy()
 
 
-def dump_weights(ctx) -> np.ndarray:
-    return np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_WEIGHTS), np.uint64).copy()
+def dump_weights(ctx, event: int = 0) -> np.ndarray:
+    return np.frombuffer(tpc_track_debug_dump(ctx, TPC_DUMP_WEIGHTS, event), np.uint64).copy()
 
 
-def dump_tracklets(ctx, n_rows: int) -> dict:
-    raw = tpc_track_debug_dump(ctx, TPC_DUMP_TRACKLETS)
+def dump_tracklets(ctx, n_rows: int, event: int = 0) -> dict:
+    raw = tpc_track_debug_dump(ctx, TPC_DUMP_TRACKLETS, event)
     count = int(np.frombuffer(raw[:4], np.int32)[0])
     rec = C.sizeof(tpc_dump_tracklet) + 4 * n_rows
     hdr_dt = np.dtype([("start_cid", "<i4"), ("sector", "<i4"), ("valid", "<i4"), ("nhits", "<i4"),

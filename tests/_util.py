@@ -78,3 +78,57 @@ def isolated_event(n_tracks=6, seed=11, sigma=0.01, pt_range=(1.0, 5.0)):
                         vx=np.zeros(n_tracks), vy=np.zeros(n_tracks), vz=np.zeros(n_tracks))
     return synth.make_event(rng, p, n_sectors_phi=1, split_z=False, sigma=sigma,
                             noise_frac=0.0)
+
+
+def oracle_by_sector(ev, orc, sectors=None, workers=None):
+    """The oracle's record of a whole event (or of the given sectors) from one
+    call per sector on all host cores: sectors are independent, so this
+    equals one call on the whole event (the hit weights aside, whose keys
+    hold sector-local cids; they are left out).  Cluster ids are those of ev;
+    per-hit arrays of clusters outside the sectors hold -1 (links) or 0."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    n_sec = ev.n_sectors_phi * (2 if ev.split_z else 1)
+    sectors = list(range(n_sec)) if sectors is None else list(sectors)
+    parts = [ev.select_sectors([s]) for s in sectors]
+    with ThreadPoolExecutor(max_workers=workers or os.cpu_count() or 1) as pool:
+        outs = list(pool.map(orc.track_event, parts))
+    n = ev.n
+
+    def cid_map(p, a):
+        a = np.asarray(a)
+        return np.where(a >= 0, p.info["parent_index"][np.maximum(a, 0)], -1).astype(np.int32)
+    o = {}
+    for k in ("up", "dn", "up_c", "dn_c"):
+        o[k] = np.full(n, -1, np.int32)
+        for p, r in zip(parts, outs):
+            o[k][p.info["parent_index"]] = cid_map(p, r[k])
+    o["c2_tie"] = np.zeros(n, np.int32)
+    for p, r in zip(parts, outs):
+        o["c2_tie"][p.info["parent_index"]] = r["c2_tie"]
+    for k in ("t_sector", "t_chain_len", "t_valid", "t_nhits", "t_first_row", "t_last_row",
+              "t_flags", "t_ndf", "t_x", "t_p", "t_C", "t_chi2", "k_x", "k_p", "k_C", "k_chi2",
+              "k_ndf", "k_sector"):
+        o[k] = np.concatenate([r[k] for r in outs])
+    o["t_start"] = np.concatenate([cid_map(p, r["t_start"]) for p, r in zip(parts, outs)])
+    o["t_rowhit"] = np.concatenate([cid_map(p, r["t_rowhit"]) for p, r in zip(parts, outs)])
+    base = np.cumsum([0] + [r["n_tracklets"] for r in outs])
+    o["k_tracklet"] = np.concatenate([r["k_tracklet"] + b for r, b in zip(outs, base)])
+    o["k_hit_cid"] = np.concatenate([cid_map(p, r["k_hit_cid"]) for p, r in zip(parts, outs)])
+    o["k_hit_off"] = np.concatenate([[0], np.cumsum(np.concatenate(
+        [np.diff(r["k_hit_off"]) for r in outs]))]).astype(np.int32)
+    for k in ("n_tracklets", "n_tracks", "n_track_hits", "n_links", "n_c2_ties", "n_starts"):
+        o[k] = int(sum(r[k] for r in outs))
+    return o
+
+
+def gpu_stages(tp, ctx, ev, event=0):
+    """The stage dumps of one event of the context's last launch, by cid:
+    links, cleaned links, start hits, tracklets, hit weights."""
+    n = ev.n
+    up, dn = tp.dump_links(ctx, n, event=event)
+    upc, dnc = tp.dump_links(ctx, n, clean=True, event=event)
+    return {"up": up, "dn": dn, "up_c": upc, "dn_c": dnc,
+            "starts": tp.dump_starts(ctx, event=event),
+            "tracklets": tp.dump_tracklets(ctx, len(ev.row_x), event=event),
+            "weights": tp.dump_weights(ctx, event=event)}

@@ -39,6 +39,28 @@ MUTATIONS = {
         "    C[2][2] = cfg->seed_var_s * c2 * c2 * c2;", "    C[2][2] = cfg->seed_var_s * c2 * c2;"),
     "transport: path length without the arc": (
         "    double dS = (h > 0.0) ? ch * asin(h) / h : ch;", "    double dS = ch;"),
+    # the neighbour rule (pin: the hand-derived golden case)
+    "neighbours: z term of D dropped": (
+        "            const double D = (syu - syd) * (syu - syd) + (szu - szd) * (szu - szd);",
+        "            const double D = (syu - syd) * (syu - syd);"),
+    "neighbours: sign of sy_d": (
+        "            const double syd = (H->y[h] - H->y[d]) / (xh - xd);",
+        "            const double syd = (H->y[d] - H->y[h]) / (xh - xd);"),
+    "neighbours: window edge excluded": (
+        "        if (!(fabs(H->y[u] - H->y[h]) <= wyu) || !(fabs(H->z[u] - H->z[h]) <= wzu)) continue;",
+        "        if (!(fabs(H->y[u] - H->y[h]) < wyu) || !(fabs(H->z[u] - H->z[h]) < wzu)) continue;"),
+    "neighbours: ties to the higher cid(u)": (
+        "            if (bu < 0 || D < bestD || (D == bestD && (u < bu || (u == bu && d < bd)))) {\n                if (bu >= 0) second = bestD;",
+        "            if (bu < 0 || D < bestD || (D == bestD && (u > bu || (u == bu && d < bd)))) {\n                if (bu >= 0) second = bestD;"),
+    "neighbours: pair near-tie bit lost": (
+        "    if (bu >= 0 && bestD <= dmax + cfg->tie_d && second - bestD <= cfg->tie_d)",
+        "    if (bu >= 0 && bestD <= dmax + cfg->tie_d && second - bestD < 0.0)"),
+    "neighbours: window near-tie bit lost": (
+        "        if (ay <= wy + tw && az <= wz + tw && (ay > wy - tw || az > wz - tw))",
+        "        if (ay <= wy - tw && az <= wz + tw && (ay > wy - tw || az > wz - tw))"),
+    "cleaner: up link kept without the partner's down link": (
+        "        res->up_c[i] = (u >= 0 && res->dn[u] == (int32_t)i) ? u : -1;",
+        "        res->up_c[i] = u;"),
 }
 
 
@@ -151,6 +173,11 @@ def prior_ok(orc):
                for s0, tt in ((0.0, 0.0), (0.25, 0.5), (-0.4, -0.9), (0.6, 0.1)))
 
 
+def golden_ok(orc):
+    from tests import test_oracle_event as t
+    return passes(t.test_golden_neighbours, orc)
+
+
 def crossings_ok(orc):
     from tests import test_oracle_transport as t
     return passes(t.test_transport_matches_closed_form_crossings, orc, 1.0, 0.35, 0.4,
@@ -162,7 +189,13 @@ PINS = {"rotation turned the wrong way": closed_form_ok, "sign of ds'/dy": jacob
         "transport: q/pT column of dy lost": transport_jacobian_ok,
         "update: sign of the off-diagonal gain": update_ok,
         "seed: sin(phi) variance with cos^4": prior_ok,
-        "transport: path length without the arc": crossings_ok}
+        "transport: path length without the arc": crossings_ok,
+        "neighbours: z term of D dropped": golden_ok, "neighbours: sign of sy_d": golden_ok,
+        "neighbours: window edge excluded": golden_ok,
+        "neighbours: ties to the higher cid(u)": golden_ok,
+        "neighbours: pair near-tie bit lost": golden_ok,
+        "neighbours: window near-tie bit lost": golden_ok,
+        "cleaner: up link kept without the partner's down link": golden_ok}
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
