@@ -348,12 +348,18 @@ int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, in
  *   streams            slots that consecutive direct launches go to in turn,
  *                      each on its own stream (1..max_streams, the context's
  *                      max_events_in_flight; see tpc_track_launch)
+ *   tl_mode            tracklet constructor: 0 persistent lanes (one lane per
+ *                      tracklet, refilled from a work counter), 1 row sweep
+ *                      (a block sweeps the pad rows of a chunk of tracklets
+ *                      with each row's hits staged in shared memory); both
+ *                      give the same tracklets
  * tpc_track_set_schedule rejects other values with TPC_EINVAL and returns
  * TPC_EBUSY while the context serves submitted events. */
 typedef struct {
     int n_sm, tl_max_per_sm;
     int bin_blocks_per_sm, sort_threads, nb_threads, tl_blocks_per_sm;
     int max_streams, streams;
+    int tl_mode;
 } tpc_track_schedule;
 int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out);
 int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);
@@ -396,6 +402,20 @@ typedef struct {
 } tpc_dump_tracklet;
 int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t cap,
                          size_t* used);
+
+/* Test hook of the bounded device waits (the decoupled look-back scans that
+ * order binning, start hits, the selector's output and the merger's output
+ * wait on their predecessor tiles; a component that stalls must not stall
+ * the event stream, paper Sect. 3 item 4 and Sect. 5.1).  For the launches
+ * that follow on this context: a wait gives up after spin_limit polls
+ * (0 = the default, 2^22), and with stall_hit_tile >= 0 the hit tile of that
+ * index (tiles of 2048 sorted hits in the start-hit compaction) never
+ * publishes its state, so that every tile after it gives up.  A launch whose
+ * wait gave up runs none of its later kernels and fails with TPC_ETIMEOUT and
+ * no result; the context stays usable.  (0, -1) restores normal launches.
+ * TPC_EINVAL for spin_limit outside [0, 2^40] or stall_hit_tile < -1,
+ * TPC_EBUSY while the context serves submitted events. */
+int tpc_track_set_debug_waits(tpc_track_ctx* ctx, int64_t spin_limit, int32_t stall_hit_tile);
 
 /* The same dump for event `event` (0 .. n_ev - 1) of the last completed
  * launch, so that each event of a batch can be compared stage by stage; cids,

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kScanThreads) k_rowscan(Launch L)
     unsigned long long total;
     const unsigned long long excl = block_excl_scan(sum, &total);
     if (threadIdx.x < 32) {
-        const unsigned long long p = lookback_warp(L.tile_state, tile, total, L.cnt);
+        const unsigned long long p = lookback_warp(L.tile_state, tile, total, L.cnt, L.spin_limit);
         if (threadIdx.x == 0) prefix_s = p;
     }
     __syncthreads();
@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(kScanThreads) k_rowscan(Launch L)
 
 __global__ void k_scatter(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     __shared__ long long off_s[kEvSmem + 1];
     load_offsets(L, off_s);
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -264,6 +265,7 @@ constexpr size_t sort_smem(int cap)
 template <bool BIG>
 __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     constexpr int CAP = BIG ? kMaxRowHits : kSmallRowHits;
     extern __shared__ unsigned char smem[];
     int* hist = reinterpret_cast<int*>(smem);                           // [nb + 1]

@@ -192,6 +192,7 @@ __device__ __forceinline__ void best_pair(const RowView& U, const RowView& D, fl
 // through the L1 cache (the hits of a block share one or two rows).
 __global__ void __launch_bounds__(kNbThreads) k_neighbours(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int n_hits = L.row_off[L.RS];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_hits; i += gridDim.x * blockDim.x) {
         const int hr = __ldg(&L.hrow[i]);
@@ -236,6 +237,7 @@ static_assert(kCsItems * kCsThreads == kHitTile, "hit tile");
 
 __global__ void __launch_bounds__(kCsThreads) k_clean_starts(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     __shared__ int tile_s;
     __shared__ unsigned long long prefix_s;
     __shared__ int warp_links[kCsThreads / 32];
@@ -312,7 +314,8 @@ __global__ void __launch_bounds__(kCsThreads) k_clean_starts(Launch L)
         }
         run = __shfl_sync(0xffffffffu, run, 0);
         const unsigned long long p =
-            lookback_warp(L.tile_state + L.n_row_tiles, tile, (unsigned long long)run, L.cnt);
+            lookback_warp(L.tile_state + L.n_row_tiles, tile, (unsigned long long)run, L.cnt,
+                          L.spin_limit, L.stall_hit_tile == tile + 1);
         if (threadIdx.x == 0) {
             prefix_s = p;
             if (tile == (int)gridDim.x - 1) L.cnt->n_starts = (int)(p + run);

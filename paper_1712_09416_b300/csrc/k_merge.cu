@@ -125,6 +125,7 @@ __device__ __forceinline__ int n_tracks(const Launch& L) { return L.cnt->n_track
 // M1, and the scratch of the later kernels
 __global__ void __launch_bounds__(kMgThreads) k_mg_outer(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int T = n_tracks(L);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < T; j += gridDim.x * blockDim.x) {
         const int e = L.sec_event[L.k_gsec[j]];
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_outer(Launch L)
 constexpr int kSortXThreads = 512;
 __global__ void __launch_bounds__(kSortXThreads) k_mg_sortx(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     extern __shared__ float sx[];                   // [kMaxSectorTracks]
     int* si = reinterpret_cast<int*>(sx + kMaxSectorTracks);  // [kMaxSectorTracks]
     const int g = blockIdx.x;
@@ -224,6 +226,7 @@ __device__ __forceinline__ int warp_lower_bound(const float* xs, int n, float v)
 // M2-M3: one warp per track a, its lanes over the candidate tracks b
 __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int T = n_tracks(L);
     const int N = L.n_sectors_phi;
     const int lane = threadIdx.x & 31;
@@ -319,6 +322,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_match(Launch L)
 // M4
 __global__ void __launch_bounds__(kMgThreads) k_mg_link(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int T = n_tracks(L);
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T; a += gridDim.x * blockDim.x) {
         const int b = L.mg_best[a];
@@ -339,6 +343,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_link(Launch L)
 // the refit reads one float4 per hit instead of three dependent loads
 __global__ void k_mg_gather(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int T = n_tracks(L);
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -356,6 +361,7 @@ __global__ void k_mg_gather(Launch L)
 // M5: one thread per chain head (a track with an outgoing and no incoming link)
 __global__ void __launch_bounds__(kMgThreads) k_mg_refit(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int T = n_tracks(L);
     const int N = L.n_sectors_phi;
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < T; h += gridDim.x * blockDim.x) {
@@ -430,6 +436,7 @@ __device__ __forceinline__ int out_hits(const Launch& L, int j)
 // output index and hit offset of every track (surviving tracks keep their order)
 __global__ void __launch_bounds__(kScanThreads) k_mg_scan(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     __shared__ int s_cnt[kScanThreads / 32], s_hit[kScanThreads / 32];
     __shared__ unsigned long long s_prefix;
     const int T = n_tracks(L);
@@ -476,7 +483,8 @@ __global__ void __launch_bounds__(kScanThreads) k_mg_scan(Launch L)
         tc = __shfl_sync(0xffffffffu, tc, 0);
         th = __shfl_sync(0xffffffffu, th, 0);
         const unsigned long long p = lookback_warp(
-            L.tile_state + L.n_row_tiles + L.n_hit_tiles + L.S, tile, pack2((unsigned)tc, (unsigned)th), L.cnt);
+            L.tile_state + L.n_row_tiles + L.n_hit_tiles + L.S, tile, pack2((unsigned)tc, (unsigned)th), L.cnt,
+            L.spin_limit);
         if (threadIdx.x == 0) {
             s_prefix = p;
             if (t0 + kMgTile >= T) {  // the last tile: totals
@@ -505,6 +513,7 @@ __global__ void __launch_bounds__(kScanThreads) k_mg_scan(Launch L)
 // one warp per surviving track: header, then its hits (a chain's tracks in turn)
 __global__ void k_mg_write(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int T = n_tracks(L);
     const int lane = threadIdx.x & 31;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;

@@ -31,6 +31,7 @@ constexpr unsigned long long kNone = ~0ULL;
 // one warp per tracklet, lanes over its rows
 __global__ void k_sel_decide(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int n_st = min(L.cnt->n_starts, L.t_cap);
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -77,6 +78,7 @@ constexpr int kRankSortMax = kMaxSectorTracks / 2;
 
 __global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     extern __shared__ unsigned long long keys[];         // [kMaxSectorTracks]
     int* idx = reinterpret_cast<int*>(keys + kMaxSectorTracks);  // [kMaxSectorTracks]
     __shared__ int m_s, tile_s;
@@ -178,7 +180,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
         }
         run = __shfl_sync(0xffffffffu, run, 0);
         const unsigned long long p = lookback_warp(L.tile_state + L.n_row_tiles + L.n_hit_tiles,
-                                                   g, pack2((unsigned)m, (unsigned)run), L.cnt);
+                                                   g, pack2((unsigned)m, (unsigned)run), L.cnt,
+                                                   L.spin_limit);
         if (threadIdx.x == 0) {
             prefix_s = p;
             const int tb = (int)unpack_a(p), hb = (int)unpack_b(p);
@@ -207,6 +210,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sel_sort(Launch L)
 // one warp per tracklet: header by lane 0, owned hits by all lanes in row order
 __global__ void k_sel_write(Launch L)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int n_st = min(L.cnt->n_starts, L.t_cap);
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;

@@ -167,6 +167,12 @@ struct Launch {
     int* m_sector; float* m_x; float* m_param; float* m_cov; float* m_chi2; int* m_ndf;
     int* m_hit_off; int* m_hit_cid; int* m_sec_trk_off; int* m_sec_hit_off;
     Counters* cnt;
+    // bounded waits: polls of a look-back before it gives up (0 = kSpinLimit);
+    // test hook: 1 + the index of a hit tile whose look-back state is never
+    // published, so that the tiles after it give up (0 = none)
+    long long spin_limit;
+    int stall_hit_tile;
+    int pad_dbg;
 };
 
 // ---------------------------------------------------------------------------
@@ -203,11 +209,16 @@ __device__ __forceinline__ unsigned unpack_b(unsigned long long v)
 // returns the exclusive prefix of `tile` on every lane.  Each round reads the
 // states of the 32 nearest unread predecessors at once (lane j reads tile
 // base - j): when every state up to the nearest inclusive one is published,
-// their payloads are summed; the walk ends at an inclusive state.
+// their payloads are summed; the walk ends at an inclusive state.  After
+// `limit` polls without progress the wait gives up: cnt->timeout is set (the
+// kernels after it return at once and the launch reports TPC_ETIMEOUT).
 __device__ inline unsigned long long lookback_warp(unsigned long long* state, int tile,
-                                                   unsigned long long aggregate, Counters* cnt)
+                                                   unsigned long long aggregate, Counters* cnt,
+                                                   long long limit, bool stall = false)
 {
     const int lane = threadIdx.x & 31;
+    if (limit <= 0) limit = kSpinLimit;
+    if (stall) return 0;  // test hook: publish nothing, the tiles after this one give up
     if (tile == 0) {
         if (lane == 0) st_release(&state[0], (2ULL << 62) | aggregate);
         return 0;
@@ -225,7 +236,7 @@ __device__ inline unsigned long long lookback_warp(unsigned long long* state, in
         const int first_p = pm ? __ffs(pm) - 1 : 31;
         const unsigned upto = first_p == 31 ? 0xffffffffu : ((2u << first_p) - 1u);
         if (zm & upto) {
-            if (++spins > kSpinLimit) {
+            if (++spins > limit) {
                 if (lane == 0) atomicExch(&cnt->timeout, 1);
                 break;
             }
@@ -276,6 +287,8 @@ struct Schedule {
     int nb_threads = 128;      // k_neighbours block (64, 128 or 256)
     int tl_blocks_per_sm = 0;  // persistent k_constructor blocks per SM (<= tl_max_per_sm)
     int tl_max_per_sm = 0;     // occupancy limit of k_constructor
+    int tl_mode = 0;           // 0 persistent lanes, 1 row-synchronous sweep (same results)
+    int sw_max_per_sm = 0;     // occupancy limit of the sweep kernel
 };
 
 // Once per device (current device): kernel attributes and the default
@@ -286,6 +299,7 @@ void prepare_binning();
 void prepare_selector();
 void prepare_merger();
 int constructor_occupancy();
+int sweep_occupancy();
 
 // host-side launchers (one translation unit each)
 void launch_binning(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);

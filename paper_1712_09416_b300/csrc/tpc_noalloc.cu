@@ -57,6 +57,7 @@ Schedule g_na_sched[kNaMaxDevices];
 // Links of every sorted hit as input cluster ids (or -1).
 __global__ void k_links_by_cid(Launch L, int32_t* up_cid, int32_t* dn_cid)
 {
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int n = L.row_off[L.RS];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int hr = L.hrow[i];

@@ -194,7 +194,8 @@ struct tpc_track_ctx {
     uint64_t next_ticket = 1;
     uint64_t prm_version = 0;  // bumped by every tpc_track_set_params (cfg.params under mu)
     std::atomic<int> direct_busy{0};
-    bool trace = false;  // TPC_TRACE=1: one stderr line per served launch
+    long long dbg_spin = 0;   // look-back poll limit of the next launches (0 = default)
+    int dbg_stall = 0;        // 1 + hit tile that never publishes (test hook), 0 = none
     bool graphs = true;  // TPC_NO_GRAPH=1: launch the kernels one by one
     tpc::Schedule sched;
     // direct launches: spread over `streams` slots in turn; the launches not
@@ -565,6 +566,8 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
         L.mg_ring = g->n_sectors_phi * d > 2.0 * M_PI - 1e-6 ? 1 : 0;
     }
     L.n_mg_tiles = (int)(((long long)s.caps.t + kMgTile - 1) / kMgTile);
+    L.spin_limit = ctx->dbg_spin;
+    L.stall_hit_tile = ctx->dbg_stall;
     L.ev = (EventDesc*)s.desc_dev;
     L.ev_off = (long long*)((char*)s.desc_dev + sizeof(EventDesc) * s.caps.e);
     L.sec_event = (int*)((char*)L.ev_off + sizeof(long long) * (s.caps.e + 1));
@@ -814,6 +817,7 @@ void prepare_kernels(Schedule* s)
     prepare_merger();
     s->tl_max_per_sm = constructor_occupancy();
     s->tl_blocks_per_sm = s->tl_max_per_sm;
+    s->sw_max_per_sm = sweep_occupancy();
 }
 
 namespace {
@@ -1099,12 +1103,6 @@ void worker(tpc_track_ctx* ctx, Slot* s)
             done[i]->prm_version = it->second->prm_version;
             std::swap(*it->second, *done[i]);
         }
-        if (ctx->trace) {
-            const auto t3 = std::chrono::steady_clock::now();
-            auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
-            std::fprintf(stderr, "[tpctrack slot %d] events %zu enqueue %.3f ms, device+collect %.3f ms, publish %.3f ms, queue %zu\n",
-                         s->id, batch.size(), ms(t0, t1), ms(t1, t2), ms(t2, t3), ctx->queue.size());
-        }
         ctx->cv_done.notify_all();
         lk.unlock();
         for (auto& d : done) pool_put(ctx, d->buf);  // tickets released meanwhile
@@ -1167,8 +1165,6 @@ int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out)
     if (!params_ok(cfg->params)) return TPC_EINVAL;
     auto ctx = std::make_unique<tpc_track_ctx>();
     ctx->cfg = *cfg;
-    const char* tr = std::getenv("TPC_TRACE");
-    ctx->trace = tr && tr[0] == '1';
     const char* ng = std::getenv("TPC_NO_GRAPH");
     ctx->graphs = !(ng && ng[0] == '1');
     if (cudaSetDevice(cfg->device) != cudaSuccess) {
@@ -1455,6 +1451,7 @@ int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out)
     out->tl_blocks_per_sm = S.tl_blocks_per_sm;
     out->max_streams = (int)ctx->slots.size();
     out->streams = ctx->streams;
+    out->tl_mode = S.tl_mode;
     return TPC_OK;
 }
 
@@ -1467,7 +1464,7 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* q)
         (q->sort_threads != 256 && q->sort_threads != 512) ||
         (q->nb_threads != 64 && q->nb_threads != 128 && q->nb_threads != 256) ||
         q->tl_blocks_per_sm < 1 || q->tl_blocks_per_sm > S.tl_max_per_sm || q->streams < 1 ||
-        q->streams > (int)ctx->slots.size())
+        q->streams > (int)ctx->slots.size() || (q->tl_mode != 0 && q->tl_mode != 1))
         return fail(ctx, TPC_EINVAL, "schedule value out of range");
     ctx->streams = q->streams;
     ctx->next_slot = 0;
@@ -1475,6 +1472,7 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* q)
     ctx->sched.sort_threads = q->sort_threads;
     ctx->sched.nb_threads = q->nb_threads;
     ctx->sched.tl_blocks_per_sm = q->tl_blocks_per_sm;
+    ctx->sched.tl_mode = q->tl_mode;
     return TPC_OK;
 }
 
@@ -1640,6 +1638,17 @@ int tpc_track_debug_dump(tpc_track_ctx* ctx, int stage, void* host_buf, size_t c
     if (!ctx) return TPC_EINVAL;
     cudaSetDevice(ctx->cfg.device);
     return dump(ctx, *ctx->slots[ctx->last_slot], stage, 0, host_buf, cap, used);
+}
+
+int tpc_track_set_debug_waits(tpc_track_ctx* ctx, int64_t spin_limit, int32_t stall_hit_tile)
+{
+    if (!ctx) return TPC_EINVAL;
+    if (spin_limit < 0 || spin_limit > (1LL << 40) || stall_hit_tile < -1)
+        return fail(ctx, TPC_EINVAL, "debug wait settings out of range");
+    if (!ctx->workers.empty()) return fail(ctx, TPC_EBUSY, "context is serving submitted events");
+    ctx->dbg_spin = (long long)spin_limit;
+    ctx->dbg_stall = stall_hit_tile + 1;
+    return TPC_OK;
 }
 
 int tpc_track_debug_dump_event(tpc_track_ctx* ctx, int stage, int event, void* host_buf,

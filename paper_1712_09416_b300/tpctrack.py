@@ -25,7 +25,8 @@ EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "
             "tpc_track_release", "tpc_track_get_counters", "tpc_track_stream",
             "tpc_track_set_profiling", "tpc_track_kernel_times",
             "tpc_track_get_schedule", "tpc_track_set_schedule", "tpc_track_autotune",
-            "tpc_track_debug_dump", "tpc_track_debug_dump_event", "tpc_track_last_error",
+            "tpc_track_debug_dump", "tpc_track_debug_dump_event", "tpc_track_set_debug_waits",
+            "tpc_track_last_error",
             "tpc_track_destroy",
             "tpc_track_links_noalloc", "tpc_track_set_params", "tpc_track_get_params",
             "tpc_track_ticket_params", "tpc_async_create", "tpc_async_start", "tpc_async_poll",
@@ -89,7 +90,7 @@ class tpc_kernel_time(C.Structure):
 class tpc_track_schedule(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("n_sm", "tl_max_per_sm", "bin_blocks_per_sm",
                                        "sort_threads", "nb_threads", "tl_blocks_per_sm",
-                                       "max_streams", "streams")]
+                                       "max_streams", "streams", "tl_mode")]
 
 
 class tpc_dump_tracklet(C.Structure):
@@ -154,6 +155,7 @@ def lib():
         L.tpc_track_debug_dump.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_size_t)]
         L.tpc_track_debug_dump_event.argtypes = [P, C.c_int, C.c_int, P, C.c_size_t,
                                                  C.POINTER(C.c_size_t)]
+        L.tpc_track_set_debug_waits.argtypes = [P, C.c_int64, C.c_int32]
         L.tpc_track_last_error.argtypes = [P]
         L.tpc_track_last_error.restype = C.c_char_p
         L.tpc_track_destroy.argtypes = [P]
@@ -561,6 +563,12 @@ def tpc_track_debug_dump(ctx, stage: int, event: int = 0) -> bytes:
     buf = C.create_string_buffer(max(1, used.value))
     _check(ctx, lib().tpc_track_debug_dump_event(ctx, stage, event, buf, used.value, C.byref(used)))
     return buf.raw[:used.value]
+
+
+def tpc_track_set_debug_waits(ctx, spin_limit: int, stall_hit_tile: int = -1):
+    """Bounded-wait test hook (see the header): poll limit of the look-back
+    waits and a hit tile that never publishes, for the launches that follow."""
+    _check(ctx, lib().tpc_track_set_debug_waits(ctx, spin_limit, stall_hit_tile))
 
 
 def tpc_track_links_noalloc(clusters: tpc_clusters, geom: tpc_geometry,

@@ -170,7 +170,7 @@ def compare_tracklets(gt, ot, n_rows, c2_chain=None):
     o_index = {int(c): i for i, c in enumerate(ot["t_start"])}
     rep = {"n_oracle": len(o_index), "n_gpu": len(g_index), "flagged": 0, "flagged_diff": [],
            "hitset_mismatch": [], "valid_mismatch": [], "param_scaled": [], "param_abs": [],
-           "taint": set()}
+           "param_sig": [], "taint": set()}
 
     def c2(c):
         return c2_chain is not None and bool(c2_chain[c])
@@ -217,8 +217,10 @@ def compare_tracklets(gt, ot, n_rows, c2_chain=None):
             d, s = param_errors(gt["p"][gi], ot["t_p"][oi])
             rep["param_scaled"].append(s)
             rep["param_abs"].append(d)
+            rep["param_sig"].append(sigma_errors(gt["p"][gi], ot["t_p"][oi], ot["t_C"][oi]))
     rep["param_scaled"] = np.array(rep["param_scaled"]).reshape(-1, 5)
     rep["param_abs"] = np.array(rep["param_abs"]).reshape(-1, 5)
+    rep["param_sig"] = np.array(rep["param_sig"]).reshape(-1, 5)
     return rep
 
 
@@ -229,7 +231,7 @@ def check_tracklets(rep, max_diff_frac=1e-3):
         (len(rep["flagged_diff"]), rep["n_oracle"])
     assert rep["valid_mismatch"] == [], rep["valid_mismatch"][:10]
     assert rep["hitset_mismatch"] == [], rep["hitset_mismatch"][:10]
-    check_param_bars(rep["param_scaled"], "tracklets")
+    check_param_bars(rep["param_scaled"], "tracklets", rep["param_sig"])
 
 
 def tainted_hits(ot):

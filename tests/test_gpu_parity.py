@@ -208,7 +208,8 @@ def test_schedule_changes_speed_not_results(tp):
         assert s0["tl_blocks_per_sm"] == s0["tl_max_per_sm"] >= 1 and s0["n_sm"] >= 1
         variants = [dict(nb_threads=64), dict(nb_threads=256), dict(sort_threads=256),
                     dict(bin_blocks_per_sm=1), dict(bin_blocks_per_sm=16),
-                    dict(tl_blocks_per_sm=1), dict(tl_blocks_per_sm=max(1, s0["tl_max_per_sm"] // 2))]
+                    dict(tl_blocks_per_sm=1), dict(tl_blocks_per_sm=max(1, s0["tl_max_per_sm"] // 2)),
+                    dict(tl_mode=1)]
         for v in variants:
             tp.tpc_track_set_schedule(t.ctx, **{**s0, **v})
             got = t.batch(evs)
@@ -216,7 +217,7 @@ def test_schedule_changes_speed_not_results(tp):
                 for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
                     assert np.array_equal(getattr(a, f), getattr(b, f)), (v, f)
         for bad in (dict(nb_threads=96), dict(sort_threads=128), dict(bin_blocks_per_sm=0),
-                    dict(tl_blocks_per_sm=s0["tl_max_per_sm"] + 1)):
+                    dict(tl_blocks_per_sm=s0["tl_max_per_sm"] + 1), dict(tl_mode=2)):
             with pytest.raises(tp.TpcError):
                 tp.tpc_track_set_schedule(t.ctx, **{**s0, **bad})
         g, keep_x = tp.geometry_of(evs[0])
@@ -229,6 +230,39 @@ def test_schedule_changes_speed_not_results(tp):
         for a, b in zip(ref, got):
             for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
                 assert np.array_equal(getattr(a, f), getattr(b, f)), ("tuned", f)
+
+
+@pytest.mark.parametrize("which", ["central", "batch", "pileup"])
+def test_constructor_modes_give_identical_tracklets(tp, which):
+    """The row-synchronous constructor (shared-memory row staging) and the
+    persistent-lane constructor do the same arithmetic per tracklet: every
+    tracklet, weight and track is bit-identical, on the central event, a
+    batch of events of uneven multiplicity (many sectors per chunk, global
+    fallback) and the pile-up event (rows above the staging capacity)."""
+    if which == "central":
+        evs = [synth.central_event()]
+    elif which == "batch":
+        evs = synth.batch_events(n_events=12, seed0=3000)
+    else:
+        evs = [synth.pileup_event()]
+    cap = sum(e.n for e in evs) + 65536
+    with tp.Tracker(cap, max_events_per_launch=len(evs)) as t:
+        s0 = tp.tpc_track_get_schedule(t.ctx)
+        res = {}
+        for mode in (0, 1):
+            tp.tpc_track_set_schedule(t.ctx, **{**s0, "tl_mode": mode})
+            trs = t.batch(evs)
+            dumps = [tp.dump_tracklets(t.ctx, len(e.row_x), event=k) for k, e in enumerate(evs)]
+            res[mode] = (trs, dumps, t.counters())
+        for k in range(len(evs)):
+            a, b = res[0][0][k], res[1][0][k]
+            for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+                assert np.array_equal(getattr(a, f), getattr(b, f)), (which, k, f)
+            da, db = res[0][1][k], res[1][1][k]
+            for f in da:
+                assert np.array_equal(da[f], db[f], equal_nan=True), (which, k, f)
+        for c in ("n_valid_tracklets", "n_tracklet_hits", "n_tracks", "n_track_hits"):
+            assert res[0][2][c] == res[1][2][c], c
 
 
 def test_launches_on_several_streams_give_the_same_tracks(tp):
@@ -380,6 +414,31 @@ def test_invalid_input_is_rejected(tp, trk):
         assert ei.value.code == tp.TPC_EINVAL
     # the context stays usable
     assert trk.event(ev).n_tracks > 0
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(tp, orc):
+    """A look-back tile that never publishes (test hook) makes the tiles after
+    it give up after a short poll limit: the launch fails with TPC_ETIMEOUT
+    and no result, and the next launch on the same context, with the hook
+    off, gives the oracle's tracks."""
+    ev = synth.one_sector_event()  # 16,671 clusters: 9 tiles of 2048 sorted hits
+    with tp.Tracker(200_000) as t:
+        ok = t.event(ev)
+        for stall in (0, 3):
+            tp.tpc_track_set_debug_waits(t.ctx, 4096, stall)
+            with pytest.raises(tp.TpcError) as ei:
+                t.event(ev)
+            assert ei.value.code == tp.TPC_ETIMEOUT, ei.value
+        # the last tile has no successor: no wait, the launch completes
+        tp.tpc_track_set_debug_waits(t.ctx, 4096, -1)
+        with pytest.raises(tp.TpcError):
+            tp.tpc_track_set_debug_waits(t.ctx, -1, -1)
+        with pytest.raises(tp.TpcError):
+            tp.tpc_track_set_debug_waits(t.ctx, 0, -2)
+        tp.tpc_track_set_debug_waits(t.ctx, 0, -1)
+        g, o, rep, trep = check_event(tp, t, ev, orc, what="after a timeout")
+        for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+            assert np.array_equal(getattr(ok, f), getattr(g["tracks"], f)), f
 
 
 def test_row_capacity_overflow_is_reported(tp, trk):
