@@ -128,7 +128,11 @@ def kernel_bytes(c: dict) -> dict:
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while running (clocks, throttle reasons)."""
+    """nvidia-smi samples every 200 ms (clocks, throttle reasons), each stamped
+    with the host time it arrived.  Started before the warm-up; the summary
+    covers the samples between two marks (the timed region, extended by a
+    hold window of the same steps so that a timed region shorter than the
+    sampling period still gets samples)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -137,7 +141,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, line)
+        self.t0 = self.t1 = None
+        self.t_timed = None
 
     def __enter__(self):
         try:
@@ -153,7 +159,22 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout_s: float = 5.0):
+        """Block until the first sample arrived (nvidia-smi takes a moment)."""
+        t_end = time.perf_counter() + timeout_s
+        while self.proc and not self.lines and time.perf_counter() < t_end:
+            time.sleep(0.02)
+
+    def mark(self, which: str):
+        now = time.perf_counter()
+        if which == "start":
+            self.t0 = now
+        elif which == "timed_end":
+            self.t_timed = now
+        else:
+            self.t1 = now
 
     def __exit__(self, *a):
         if self.proc:
@@ -166,7 +187,12 @@ class ClockSampler:
     def summary(self) -> dict:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo = self.t0 if self.t0 is not None else -1e30
+        hi = self.t1 if self.t1 is not None else 1e30
+        in_timed = 0
+        for t, ln in self.lines:
+            if not (lo <= t <= hi + 0.25):  # a sample reports the 200 ms before it
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -175,14 +201,20 @@ class ClockSampler:
                 mx.append(float(f[2]))
             except ValueError:
                 continue
+            if self.t_timed is not None and t <= self.t_timed + 0.25:
+                in_timed += 1
             for n, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        window = {"window_s": (hi - lo) if self.t0 is not None and self.t1 is not None else None,
+                  "window": "the timed region and a hold of the same steps after it",
+                  "samples_in_timed_region": in_timed}
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "warning": "nvidia-smi gave no sample in the window", **window}
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), **window}
 
 
 def cpu_baseline(ev_full, n_sectors: int = 4) -> dict:
@@ -321,19 +353,56 @@ def compare_point(tp, events, ns, arrivals, geom, bz, n_max, rate):
 
 
 def at_equal_p99(points, targets_ms=(10.0, 20.0)) -> list:
-    """For each p99 target: the highest clusters/s each server sustained
-    among the measured rates whose p99 latency met the target."""
+    """For each p99 target and each server: the highest clusters/s among the
+    measured rates whose p99 latency met the target, and that throughput
+    interpolated to p99 = target between the last rate that met it and the
+    next one (linear in p99), which does not favour the server whose
+    measured points happen to lie closer to the target."""
     out = []
     for tgt in targets_ms:
         row = {"p99_target_ms": tgt}
         for side in ("one_event", "served"):
-            ok = [p[side]["clusters_per_s"] for p in points if p[side]["p99_ms"] <= tgt]
+            pts = sorted(points, key=lambda p: p["rate_per_s"])
+            ok = [p[side]["clusters_per_s"] for p in pts if p[side]["p99_ms"] <= tgt]
             row[side + "_clusters_per_s"] = max(ok) if ok else None
+            interp = None
+            for a, b in zip(pts, pts[1:]):
+                la, lb = a[side]["p99_ms"], b[side]["p99_ms"]
+                if la <= tgt < lb:
+                    w = (tgt - la) / (lb - la)
+                    interp = a[side]["clusters_per_s"] + w * (b[side]["clusters_per_s"] -
+                                                              a[side]["clusters_per_s"])
+            if interp is None and ok and pts[-1][side]["p99_ms"] <= tgt:
+                interp = pts[-1][side]["clusters_per_s"]  # met at every measured rate
+            row[side + "_interp_clusters_per_s"] = interp
         out.append(row)
     return out
 
 
-def served_vs_one(tp, torch, host_events, geom, bz, n_per_event, rate_factors=(0.7, 1.5, 3.0),
+def served_summary(served, line) -> dict:
+    """Compact record of the served-form comparison (and the headline
+    fractions), written as the last key of the bench line."""
+    out = {"value": line["value"], "e2e": (line.get("e2e") or {}).get("value"),
+           "roofline_frac": line["roofline"]["frac"],
+           "path_roofline_frac": line["path_roofline"]["frac"]}
+    if not served or "points" not in served:
+        out["served"] = None
+        return out
+
+    def pick(rows):
+        return [{k: (round(v, 4) if isinstance(v, float) and k.endswith("_ms") else
+                     (float(f"{v:.4g}") if isinstance(v, float) else v))
+                 for k, v in r.items()} for r in rows]
+    out["central_events_at_equal_p99"] = pick(served.get("at_equal_p99", []))
+    out["central_events_rates"] = len(served["points"])
+    st = served.get("stream") or {}
+    if "at_equal_p99" in st:
+        out["event_stream_at_equal_p99"] = pick(st["at_equal_p99"])
+    return out
+
+
+def served_vs_one(tp, torch, host_events, geom, bz, n_per_event,
+                  rate_factors=(0.5, 0.6, 0.7, 0.8, 0.9, 1.0, 1.1, 1.2, 1.3, 1.5, 3.0),
                   n_events=120, seed=4):
     """Poisson arrivals of central events: one-at-a-time FIFO server vs the
     served form (continuous batching over SERVED_SLOTS slots of up to
@@ -850,17 +919,36 @@ def run_ours(args):
 
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        e0.record(stream)
-        for i in range(args.steps):
-            step(i)  # the kernel sequence replays as one CUDA graph per step
-        tp.tpc_track_join(ctx)  # the stream waits for the steps on every slot
-        e1.record(stream)
-        barrier()
+    clk = ClockSampler(local)
+    clk.__enter__()
+    clk.wait_first()
+    barrier()
+    clk.mark("start")
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)  # the kernel sequence replays as one CUDA graph per step
+    tp.tpc_track_join(ctx)  # the stream waits for the steps on every slot
+    e1.record(stream)
+    barrier()
+    clk.mark("timed_end")
     ms_total = e0.elapsed_time(e1)
     for _ in range(n_streams):  # status of the last step of every slot
         tp.tpc_track_results(ctx, 1, copy=False)
+    # hold: the same steps for about a second more (untimed), so that the
+    # clock record covers the load even when the timed region is shorter
+    # than nvidia-smi's 200 ms sampling period
+    t_hold = time.perf_counter() + 1.0
+    i = 0
+    while time.perf_counter() < t_hold:
+        for _ in range(16):
+            step(i)
+            i += 1
+        tp.tpc_track_join(ctx)
+        torch.cuda.synchronize()
+        for _ in range(min(16, n_streams)):
+            tp.tpc_track_results(ctx, 1, copy=False)
+    clk.mark("end")
+    clk.__exit__()
     # the same steps on 1..max streams with the tuned grid shapes (outside the
     # timed region): what running consecutive events' kernels together buys
     streams_sweep = {}
@@ -1049,6 +1137,9 @@ def run_ours(args):
             "side_task": side_task, "merge": merged,
             "streams_ms_per_event": streams_sweep,
         }
+        # last key (a driver that keeps the tail of the line keeps it): served
+        # against one event at a time at equal p99, and the roofline fractions
+        line["served_summary"] = served_summary(served, line)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

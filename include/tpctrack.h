@@ -353,13 +353,16 @@ int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, in
  *                      (a block sweeps the pad rows of a chunk of tracklets
  *                      with each row's hits staged in shared memory); both
  *                      give the same tracklets
+ *   nb_mode            neighbour finder: 0 one thread per hit, 1 one block
+ *                      per pad row with the two adjacent rows staged in
+ *                      shared memory; both give the same links
  * tpc_track_set_schedule rejects other values with TPC_EINVAL and returns
  * TPC_EBUSY while the context serves submitted events. */
 typedef struct {
     int n_sm, tl_max_per_sm;
     int bin_blocks_per_sm, sort_threads, nb_threads, tl_blocks_per_sm;
     int max_streams, streams;
-    int tl_mode;
+    int tl_mode, nb_mode;
 } tpc_track_schedule;
 int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out);
 int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);
@@ -443,15 +446,81 @@ int tpc_track_debug_dump_event(tpc_track_ctx* ctx, int stage, int event, void* h
  * held on every device that loads the library until the process exits.  No
  * context, cudaMalloc or cudaFree is involved.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture.  Every
- * call on a device shares the array and clears what must start at zero, so
- * calls whose work overlaps on the GPU (other threads, other streams) race:
- * serialise them.  Returns after the work has completed: TPC_OK, TPC_EINVAL
- * (bad argument or invalid cluster), TPC_ECAPACITY (a row above 4096
- * clusters), TPC_ETIMEOUT or TPC_ECUDA. */
+ * device current) and sets up the kernels.  Every call copies its small
+ * descriptor from the host and synchronises cuda_stream before it returns
+ * (it reads the status back), so no call can be made while that stream is
+ * being captured into a CUDA graph.  Every call on a device shares the array
+ * and clears what must start at zero, so calls whose work overlaps on the
+ * GPU (other threads, other streams) race: serialise them.  Returns after the
+ * work has completed: TPC_OK, TPC_EINVAL (bad argument or invalid cluster),
+ * TPC_ECAPACITY (a row above 4096 clusters), TPC_ETIMEOUT or TPC_ECUDA (also
+ * when a launch error from earlier work is pending on the calling thread; it
+ * is left pending). */
 int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometry* geom,
                             const tpc_track_params* params, int32_t* up_cid, int32_t* dn_cid,
                             void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Round-robin dispatcher over tracker instances.  The paper runs several
+ * instances of a component and hands them whole events in turn to balance
+ * the load (Sect. 2); events are independent, so the instances exchange
+ * nothing.  An instance is any object with these three calls (with the
+ * meaning of tpc_track_submit / poll / release); tpc_dispatch_create makes
+ * one tracker context per listed device and uses those.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int (*submit)(void* instance, const tpc_clusters* ev, const tpc_geometry* geom,
+                  float bz_tesla, uint64_t* ticket);
+    int (*poll)(void* instance, uint64_t ticket, int timeout_us, tpc_tracks* out);
+    int (*release)(void* instance, uint64_t ticket);
+} tpc_instance_ops;
+
+typedef struct tpc_dispatch tpc_dispatch;
+
+/* One context per entry of devices[n_dev] (a device may be listed more than
+ * once), each created with *cfg (device and cuda_stream replaced), owned and
+ * destroyed by the dispatcher.  Errors of tpc_track_create are returned;
+ * nothing is left allocated then. */
+int tpc_dispatch_create(const int* devices, int n_dev, const tpc_track_config* cfg,
+                        tpc_dispatch** out);
+
+/* A dispatcher over n caller-owned instances (1..1024) driven through ops;
+ * the instances must outlive the dispatcher.  TPC_EINVAL for a NULL call or
+ * instance. */
+int tpc_dispatch_create_custom(const tpc_instance_ops* ops, void* const* instances, int n,
+                               tpc_dispatch** out);
+
+/* Hand one event to the next healthy instance in turn.  *ticket numbers the
+ * events 1, 2, ... in submission order.  The caller keeps ev's buffers (and
+ * geom's row_x) valid until the ticket is released: an event is submitted
+ * again to another instance when the one holding it fails.  An instance whose
+ * submit, or a later poll of one of its tickets, fails with TPC_ECUDA,
+ * TPC_ETIMEOUT or TPC_ENOMEM leaves the rotation and its events go to the
+ * others; any other error (TPC_EINVAL: the event's own invalid clusters)
+ * fails that ticket only.  TPC_ECUDA when no healthy instance is left. */
+int tpc_dispatch_submit(tpc_dispatch* d, const tpc_clusters* ev, const tpc_geometry* geom,
+                        float bz_tesla, uint64_t* ticket);
+
+/* Wait up to timeout_us for a ticket (as tpc_track_poll); *out stays valid
+ * until tpc_dispatch_release.  Tickets may be polled in any order and from
+ * several threads. */
+int tpc_dispatch_poll(tpc_dispatch* d, uint64_t ticket, int timeout_us, tpc_tracks* out);
+
+/* Release a ticket's results (and the caller's input buffers). */
+int tpc_dispatch_release(tpc_dispatch* d, uint64_t ticket);
+
+/* Take an instance out of the rotation as if it had failed (host-side fault
+ * injection for tests and for an operator who drains a device); its
+ * unreleased events not yet polled go to the other instances. */
+int tpc_dispatch_fail_instance(tpc_dispatch* d, int instance);
+
+/* Events submitted to each instance (re-issued ones included), whether it is
+ * healthy, and the number of re-issued events; returns the instance count. */
+int tpc_dispatch_stats(tpc_dispatch* d, int cap, int64_t* events_per_instance,
+                       int32_t* healthy, int64_t* reissued);
+
+/* Release everything; contexts made by tpc_dispatch_create are destroyed. */
+void tpc_dispatch_destroy(tpc_dispatch* d);
 
 /* One-line description of the last error on the context (never NULL).  The
  * string belongs to the calling thread and stays valid until its next call

@@ -230,6 +230,86 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbours(Launch L)
     }
 }
 
+// Row blocks (schedule nb_mode = 1): a block takes one (sector, row) at a
+// time, stages the hits, cids and bin offsets of the two adjacent rows in
+// shared memory (cp.async; a row above kNrCap hits is read from global
+// memory instead), then its threads run the same per-hit search as
+// k_neighbours over the row's hits.  Identical links; the candidates come
+// from shared memory instead of L1/L2.
+constexpr int kNrThreads = 128;
+constexpr int kNrCap = 1024;              // staged hits of one adjacent row
+constexpr int kNrBinCap = 2 * kNrCap + 2; // its bin offsets (2 bins per hit, + 1)
+
+constexpr size_t nr_smem()
+{
+    return 2 * (sizeof(float2) * kNrCap + sizeof(int) * kNrCap + sizeof(int) * kNrBinCap);
+}
+
+__device__ __forceinline__ void nr_stage(const Launch& L, int g, float2* syz, int* scid,
+                                         int* sbins, RowView& V)
+{
+    const int a = L.row_off[g], n = L.row_off[g + 1] - a;
+    V.G = L.grid[g];
+    const int nb = V.G.ny * V.G.nz + 1;
+    const int* gb = L.bin_start + V.G.bin_off;
+    if (n <= kNrCap && nb <= kNrBinCap) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            cp_async8(syz + i, L.hyz + a + i);
+            cp_async4(scid + i, L.hcid + a + i);
+        }
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) cp_async4(sbins + i, gb + i);
+        V.yz = syz;
+        V.cid = scid;
+        V.bins = sbins;
+    } else {
+        V.yz = L.hyz + a;
+        V.cid = L.hcid + a;
+        V.bins = gb;
+    }
+}
+
+__global__ void __launch_bounds__(kNrThreads) k_neighbours_rows(Launch L)
+{
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
+    extern __shared__ __align__(16) unsigned char nr_sm[];
+    float2* syz = reinterpret_cast<float2*>(nr_sm);  // [2][kNrCap]: up row, down row
+    int* scid = reinterpret_cast<int*>(syz + 2 * kNrCap);
+    int* sbins = scid + 2 * kNrCap;                  // [2][kNrBinCap]
+    for (int g = blockIdx.x; g < L.RS; g += gridDim.x) {
+        const int r = g % L.R;
+        const int a = L.row_off[g], n = L.row_off[g + 1] - a;
+        if (n == 0) continue;
+        if (r == 0 || r == L.R - 1) {
+            for (int i = a + threadIdx.x; i < a + n; i += blockDim.x) {
+                L.up[i] = -1;
+                L.dn[i] = -1;
+            }
+            continue;
+        }
+        RowView U, D;
+        nr_stage(L, g + 1, syz, scid, sbins, U);
+        nr_stage(L, g - 1, syz + kNrCap, scid + kNrCap, sbins + kNrBinCap, D);
+        const float xh = __ldg(&L.xr[r]), xu = __ldg(&L.xr[r + 1]), xd = __ldg(&L.xr[r - 1]);
+        const float iu = __frcp_rn(__fsub_rn(xu, xh)), id = __frcp_rn(__fsub_rn(xh, xd));
+        const float wyu = __fmul_rn(L.slope_win_y, fabsf(__fsub_rn(xu, xh)));
+        const float wzu = __fmul_rn(L.slope_win_z, fabsf(__fsub_rn(xu, xh)));
+        const float wyd = __fmul_rn(L.slope_win_y, fabsf(__fsub_rn(xd, xh)));
+        const float wzd = __fmul_rn(L.slope_win_z, fabsf(__fsub_rn(xd, xh)));
+        cp_async_wait_all();
+        __syncthreads();
+        for (int i = a + threadIdx.x; i < a + n; i += blockDim.x) {
+            const float2 ch = L.hyz[i];
+            float bestD = 0.0f;
+            int bcu = -1, bcd = -1, biu = -1, bid = -1;
+            best_pair(U, D, ch.x, ch.y, iu, id, wyu, wzu, wyd, wzd, bestD, bcu, bcd, biu, bid);
+            const bool link = bcu >= 0 && bestD <= L.d_max;
+            L.up[i] = link ? (int16_t)biu : (int16_t)-1;
+            L.dn[i] = link ? (int16_t)bid : (int16_t)-1;
+        }
+        __syncthreads();  // the staged rows are overwritten by the next row
+    }
+}
+
 constexpr int kCsThreads = 256;
 constexpr int kCsItems = kHitTile / kCsThreads;
 constexpr int kCsTile = kHitTile;
@@ -336,14 +416,30 @@ __global__ void __launch_bounds__(kCsThreads) k_clean_starts(Launch L)
 
 }  // namespace
 
+int neighbour_rows_occupancy()
+{
+    cudaFuncSetAttribute(k_neighbours_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)nr_smem());
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_neighbours_rows, kNrThreads, nr_smem());
+    return per_sm < 1 ? 1 : per_sm;
+}
+
 void launch_finder(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
 {
     cudaStream_t stream = (cudaStream_t)stream_;
-    const int th = (S.nb_threads == 64 || S.nb_threads == 256) ? S.nb_threads : 128;
-    long long nb = (L.n_total + th - 1) / th;
-    if (nb > (long long)S.n_sm * 64) nb = (long long)S.n_sm * 64;
-    if (nb < 1) nb = 1;
-    k_neighbours<<<(int)nb, th, 0, stream>>>(L);
+    if (S.nb_mode == 1) {
+        long long nb = (long long)S.n_sm * (S.nr_max_per_sm > 0 ? S.nr_max_per_sm : 1);
+        if (nb > L.RS) nb = L.RS;
+        if (nb < 1) nb = 1;
+        k_neighbours_rows<<<(int)nb, kNrThreads, nr_smem(), stream>>>(L);
+    } else {
+        const int th = (S.nb_threads == 64 || S.nb_threads == 256) ? S.nb_threads : 128;
+        long long nb = (L.n_total + th - 1) / th;
+        if (nb > (long long)S.n_sm * 64) nb = (long long)S.n_sm * 64;
+        if (nb < 1) nb = 1;
+        k_neighbours<<<(int)nb, th, 0, stream>>>(L);
+    }
     hook_after(hook, "k_neighbours");
     k_clean_starts<<<L.n_hit_tiles, kCsThreads, 0, stream>>>(L);
     hook_after(hook, "k_clean_starts");

@@ -486,21 +486,6 @@ constexpr size_t sweep_smem()
            sizeof(float) * kMaxRows;
 }
 
-__device__ __forceinline__ void cp_async8(void* dst, const void* src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 // Least-chi2 hit of a row described by D (same rule and arithmetic as search()).
 __device__ __forceinline__ int search_sw(const Fit& f, float yref, float zref, const SwDesc& D,
                                          const Launch& L, float& my, float& mz)

@@ -254,6 +254,24 @@ __device__ inline unsigned long long lookback_warp(unsigned long long* state, in
     return excl;
 }
 
+// Asynchronous global -> shared copies of one 8- or 4-byte element
+// (cp.async, completed by cp_async_wait_all and made visible to the block by
+// the barrier after it).
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Bin of a coordinate in a row grid, clamped to the edge bins.  The same
 // monotone arithmetic sorts the hits and bounds every window query, so a
 // window [lo, hi] maps onto bins [bin(lo), bin(hi)] that hold all its hits.
@@ -289,6 +307,8 @@ struct Schedule {
     int tl_max_per_sm = 0;     // occupancy limit of k_constructor
     int tl_mode = 0;           // 0 persistent lanes, 1 row-synchronous sweep (same results)
     int sw_max_per_sm = 0;     // occupancy limit of the sweep kernel
+    int nb_mode = 0;           // 0 one thread per hit, 1 row blocks with staged rows (same results)
+    int nr_max_per_sm = 0;     // occupancy limit of the row-block neighbour kernel
 };
 
 // Once per device (current device): kernel attributes and the default
@@ -300,6 +320,7 @@ void prepare_selector();
 void prepare_merger();
 int constructor_occupancy();
 int sweep_occupancy();
+int neighbour_rows_occupancy();
 
 // host-side launchers (one translation unit each)
 void launch_binning(const Launch& L, const Schedule& S, void* stream, const KernelHook* hook);

@@ -200,7 +200,9 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
     launch_finder(L, sched, st, nullptr);
     const int blocks = (int)((n + 255) / 256) > 0 ? (int)((n + 255) / 256) : 1;
     k_links_by_cid<<<blocks < 1184 ? blocks : 1184, 256, 0, st>>>(L, up_cid, dn_cid);
-    if (cudaGetLastError() != cudaSuccess) return TPC_ECUDA;
+    // a launch error is left pending for the caller (an error already pending
+    // on this thread from earlier work is reported the same way)
+    if (cudaPeekAtLastError() != cudaSuccess) return TPC_ECUDA;
     Counters c;
     if (cudaMemcpyAsync(&c, L.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return TPC_ECUDA;

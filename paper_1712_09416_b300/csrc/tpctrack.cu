@@ -818,6 +818,7 @@ void prepare_kernels(Schedule* s)
     s->tl_max_per_sm = constructor_occupancy();
     s->tl_blocks_per_sm = s->tl_max_per_sm;
     s->sw_max_per_sm = sweep_occupancy();
+    s->nr_max_per_sm = neighbour_rows_occupancy();
 }
 
 namespace {
@@ -1452,6 +1453,7 @@ int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out)
     out->max_streams = (int)ctx->slots.size();
     out->streams = ctx->streams;
     out->tl_mode = S.tl_mode;
+    out->nb_mode = S.nb_mode;
     return TPC_OK;
 }
 
@@ -1464,7 +1466,8 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* q)
         (q->sort_threads != 256 && q->sort_threads != 512) ||
         (q->nb_threads != 64 && q->nb_threads != 128 && q->nb_threads != 256) ||
         q->tl_blocks_per_sm < 1 || q->tl_blocks_per_sm > S.tl_max_per_sm || q->streams < 1 ||
-        q->streams > (int)ctx->slots.size() || (q->tl_mode != 0 && q->tl_mode != 1))
+        q->streams > (int)ctx->slots.size() || (q->tl_mode != 0 && q->tl_mode != 1) ||
+        (q->nb_mode != 0 && q->nb_mode != 1))
         return fail(ctx, TPC_EINVAL, "schedule value out of range");
     ctx->streams = q->streams;
     ctx->next_slot = 0;
@@ -1473,6 +1476,7 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* q)
     ctx->sched.nb_threads = q->nb_threads;
     ctx->sched.tl_blocks_per_sm = q->tl_blocks_per_sm;
     ctx->sched.tl_mode = q->tl_mode;
+    ctx->sched.nb_mode = q->nb_mode;
     return TPC_OK;
 }
 
@@ -1556,7 +1560,9 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     for (int v : {mx * 3 / 4, mx / 2})
         if (v >= 1 && std::find(tl.begin(), tl.end(), v) == tl.end()) tl.push_back(v);
     int rc = tune(&Schedule::tl_blocks_per_sm, tl, {"k_constructor"});
+    if (!rc) rc = tune(&Schedule::tl_mode, {0, 1}, {"k_constructor"});
     if (!rc) rc = tune(&Schedule::nb_threads, {64, 128, 256}, {"k_neighbours"});
+    if (!rc) rc = tune(&Schedule::nb_mode, {0, 1}, {"k_neighbours"});
     if (!rc) rc = tune(&Schedule::sort_threads, {256, 512}, {"k_rowsort"});
     if (!rc) rc = tune(&Schedule::bin_blocks_per_sm, {2, 4, 8, 16}, {"k_count", "k_scatter"});
     if (rc) return rc;

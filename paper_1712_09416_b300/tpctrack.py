@@ -32,7 +32,9 @@ EXPORTED = ["tpc_track_default_params", "tpc_track_create", "tpc_track_event", "
             "tpc_track_ticket_params", "tpc_async_create", "tpc_async_start", "tpc_async_poll",
             "tpc_async_get_stats", "tpc_async_destroy", "tpc_chi2_calib_create",
             "tpc_chi2_calib_add", "tpc_chi2_calib_poll", "tpc_chi2_calib_stats",
-            "tpc_chi2_calib_destroy"]
+            "tpc_chi2_calib_destroy", "tpc_dispatch_create", "tpc_dispatch_create_custom",
+            "tpc_dispatch_submit", "tpc_dispatch_poll", "tpc_dispatch_release",
+            "tpc_dispatch_fail_instance", "tpc_dispatch_stats", "tpc_dispatch_destroy"]
 
 
 class TpcError(RuntimeError):
@@ -90,7 +92,8 @@ class tpc_kernel_time(C.Structure):
 class tpc_track_schedule(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("n_sm", "tl_max_per_sm", "bin_blocks_per_sm",
                                        "sort_threads", "nb_threads", "tl_blocks_per_sm",
-                                       "max_streams", "streams", "tl_mode")]
+                                       "max_streams", "streams", "tl_mode",
+                                       "nb_mode")]
 
 
 class tpc_dump_tracklet(C.Structure):
@@ -110,6 +113,16 @@ class tpc_chi2_fit(C.Structure):
                                           "params_version")] + \
         [("n_tracks", C.c_int64), ("n_kept", C.c_int64), ("n_iter", C.c_int32), ("pad", C.c_int32),
          ("scale2", C.c_double)]
+
+
+tpc_submit_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry),
+                            C.c_float, C.POINTER(C.c_uint64))
+tpc_poll_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_uint64, C.c_int, C.POINTER(tpc_tracks))
+tpc_release_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_uint64)
+
+
+class tpc_instance_ops(C.Structure):
+    _fields_ = [("submit", tpc_submit_fn), ("poll", tpc_poll_fn), ("release", tpc_release_fn)]
 
 
 tpc_async_init_fn = C.CFUNCTYPE(C.c_int, C.c_void_p)
@@ -183,6 +196,19 @@ def lib():
         L.tpc_chi2_calib_stats.argtypes = [P, C.POINTER(tpc_async_stats)]
         L.tpc_chi2_calib_destroy.argtypes = [P]
         L.tpc_chi2_calib_destroy.restype = None
+        L.tpc_dispatch_create.argtypes = [C.POINTER(C.c_int), C.c_int, C.POINTER(tpc_track_config),
+                                          C.POINTER(C.c_void_p)]
+        L.tpc_dispatch_create_custom.argtypes = [C.POINTER(tpc_instance_ops), C.POINTER(C.c_void_p),
+                                                 C.c_int, C.POINTER(C.c_void_p)]
+        L.tpc_dispatch_submit.argtypes = [P, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry),
+                                          C.c_float, C.POINTER(C.c_uint64)]
+        L.tpc_dispatch_poll.argtypes = [P, C.c_uint64, C.c_int, C.POINTER(tpc_tracks)]
+        L.tpc_dispatch_release.argtypes = [P, C.c_uint64]
+        L.tpc_dispatch_fail_instance.argtypes = [P, C.c_int]
+        L.tpc_dispatch_stats.argtypes = [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int64)]
+        L.tpc_dispatch_destroy.argtypes = [P]
+        L.tpc_dispatch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -277,10 +303,10 @@ def tpc_track_default_params() -> tpc_track_params:
     return p
 
 
-def tpc_track_create(max_clusters_per_event: int, *, device: int = 0, mem_budget: int = 0,
-                     max_events_in_flight: int = 1, cuda_stream: int | None = None,
-                     max_rows: int = 159, max_events_per_launch: int = 64,
-                     params: tpc_track_params | None = None):
+def _config(max_clusters_per_event: int, *, device: int = 0, mem_budget: int = 0,
+            max_events_in_flight: int = 1, cuda_stream: int | None = None,
+            max_rows: int = 159, max_events_per_launch: int = 64,
+            params: tpc_track_params | None = None) -> tpc_track_config:
     cfg = tpc_track_config()
     cfg.device = device
     cfg.mem_budget = mem_budget
@@ -290,6 +316,11 @@ def tpc_track_create(max_clusters_per_event: int, *, device: int = 0, mem_budget
     cfg.max_rows = max_rows
     cfg.max_events_per_launch = max_events_per_launch
     cfg.params = params if params is not None else tpc_track_default_params()
+    return cfg
+
+
+def tpc_track_create(max_clusters_per_event: int, **kw):
+    cfg = _config(max_clusters_per_event, **kw)
     ctx = C.c_void_p()
     rc = lib().tpc_track_create(C.byref(cfg), C.byref(ctx))
     if rc != TPC_OK:
@@ -623,6 +654,79 @@ def dump_tracklets(ctx, n_rows: int, event: int = 0) -> dict:
             "last_row": h["last_row"].copy(), "ndf": h["ndf"].copy(), "x": h["x"].copy(),
             "p": h["param"].copy(), "C": h["cov"].copy(), "chi2": h["chi2"].copy(),
             "rowhit": a["rowhit"].copy()}
+
+
+class Dispatcher:
+    """Round-robin dispatcher of whole events over tracker instances
+    (tpc_dispatch_*): one context per listed device, or caller-made instances
+    driven through Python callables (submit, poll, release) with the C
+    signatures of tpc_instance_ops."""
+
+    def __init__(self, devices=None, max_clusters_per_event: int = 0, *, ops=None,
+                 instances=None, **kw):
+        self.d = C.c_void_p()
+        self._keep = []
+        if ops is not None:
+            cops = tpc_instance_ops(tpc_submit_fn(ops[0]), tpc_poll_fn(ops[1]),
+                                    tpc_release_fn(ops[2]))
+            arr = (C.c_void_p * len(instances))(*instances)
+            self._keep += [cops, arr]
+            rc = lib().tpc_dispatch_create_custom(C.byref(cops), arr, len(instances),
+                                                  C.byref(self.d))
+        else:
+            cfg = _config(max_clusters_per_event, **kw)
+            devs = (C.c_int * len(devices))(*devices)
+            rc = lib().tpc_dispatch_create(devs, len(devices), C.byref(cfg), C.byref(self.d))
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_dispatch_create failed")
+
+    def submit(self, clusters: tpc_clusters, geom: tpc_geometry, bz: float) -> int:
+        t = C.c_uint64()
+        rc = lib().tpc_dispatch_submit(self.d, C.byref(clusters), C.byref(geom), bz, C.byref(t))
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_dispatch_submit failed")
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = -1, *, copy: bool = True):
+        out = tpc_tracks()
+        rc = lib().tpc_dispatch_poll(self.d, ticket, timeout_us, C.byref(out))
+        if rc == TPC_EBUSY:
+            return None
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_dispatch_poll failed")
+        return tracks_to_numpy(out, copy)
+
+    def release(self, ticket: int):
+        rc = lib().tpc_dispatch_release(self.d, ticket)
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_dispatch_release failed")
+
+    def fail_instance(self, k: int):
+        rc = lib().tpc_dispatch_fail_instance(self.d, k)
+        if rc != TPC_OK:
+            raise TpcError(rc, "tpc_dispatch_fail_instance failed")
+
+    def stats(self) -> dict:
+        cap = 1024
+        ev = (C.c_int64 * cap)()
+        ok = (C.c_int32 * cap)()
+        re = C.c_int64()
+        n = lib().tpc_dispatch_stats(self.d, cap, ev, ok, C.byref(re))
+        if n < 0:
+            raise TpcError(n, "tpc_dispatch_stats failed")
+        return {"events": list(ev[:n]), "healthy": [bool(x) for x in ok[:n]],
+                "reissued": re.value}
+
+    def close(self):
+        if self.d:
+            lib().tpc_dispatch_destroy(self.d)
+            self.d = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Tracker:

@@ -209,7 +209,7 @@ def test_schedule_changes_speed_not_results(tp):
         variants = [dict(nb_threads=64), dict(nb_threads=256), dict(sort_threads=256),
                     dict(bin_blocks_per_sm=1), dict(bin_blocks_per_sm=16),
                     dict(tl_blocks_per_sm=1), dict(tl_blocks_per_sm=max(1, s0["tl_max_per_sm"] // 2)),
-                    dict(tl_mode=1)]
+                    dict(tl_mode=1), dict(nb_mode=1)]
         for v in variants:
             tp.tpc_track_set_schedule(t.ctx, **{**s0, **v})
             got = t.batch(evs)
@@ -217,7 +217,8 @@ def test_schedule_changes_speed_not_results(tp):
                 for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
                     assert np.array_equal(getattr(a, f), getattr(b, f)), (v, f)
         for bad in (dict(nb_threads=96), dict(sort_threads=128), dict(bin_blocks_per_sm=0),
-                    dict(tl_blocks_per_sm=s0["tl_max_per_sm"] + 1), dict(tl_mode=2)):
+                    dict(tl_blocks_per_sm=s0["tl_max_per_sm"] + 1), dict(tl_mode=2),
+                    dict(nb_mode=-1)):
             with pytest.raises(tp.TpcError):
                 tp.tpc_track_set_schedule(t.ctx, **{**s0, **bad})
         g, keep_x = tp.geometry_of(evs[0])
@@ -233,12 +234,13 @@ def test_schedule_changes_speed_not_results(tp):
 
 
 @pytest.mark.parametrize("which", ["central", "batch", "pileup"])
-def test_constructor_modes_give_identical_tracklets(tp, which):
-    """The row-synchronous constructor (shared-memory row staging) and the
-    persistent-lane constructor do the same arithmetic per tracklet: every
-    tracklet, weight and track is bit-identical, on the central event, a
-    batch of events of uneven multiplicity (many sectors per chunk, global
-    fallback) and the pile-up event (rows above the staging capacity)."""
+def test_kernel_modes_give_identical_results(tp, which):
+    """The row-synchronous constructor and the row-block neighbour finder
+    (both with shared-memory row staging) do the same arithmetic per tracklet
+    and per hit as the persistent-lane constructor and the thread-per-hit
+    finder: every link, tracklet and track is bit-identical, on the central
+    event, a batch of events of uneven multiplicity (many sectors per chunk,
+    global fallback) and the pile-up event (rows above the staging capacity)."""
     if which == "central":
         evs = [synth.central_event()]
     elif which == "batch":
@@ -250,9 +252,13 @@ def test_constructor_modes_give_identical_tracklets(tp, which):
         s0 = tp.tpc_track_get_schedule(t.ctx)
         res = {}
         for mode in (0, 1):
-            tp.tpc_track_set_schedule(t.ctx, **{**s0, "tl_mode": mode})
+            tp.tpc_track_set_schedule(t.ctx, **{**s0, "tl_mode": mode, "nb_mode": mode})
             trs = t.batch(evs)
-            dumps = [tp.dump_tracklets(t.ctx, len(e.row_x), event=k) for k, e in enumerate(evs)]
+            dumps = []
+            for k, e in enumerate(evs):
+                d = tp.dump_tracklets(t.ctx, len(e.row_x), event=k)
+                d["up"], d["dn"] = tp.dump_links(t.ctx, e.n, event=k)
+                dumps.append(d)
             res[mode] = (trs, dumps, t.counters())
         for k in range(len(evs)):
             a, b = res[0][0][k], res[1][0][k]
