@@ -21,7 +21,8 @@ Bars (the tracker computes in binary32, the oracle in binary64):
   0, where the binary32 fit keeps an absolute error near 1e-4 (under 1% of
   the statistical error of q/pT).  Budget: at most 0.1% of the compared
   tracks (rounded up) may exceed these bars, each by at most 3x or else by
-  less than 1e-2 of the oracle's own standard error on every parameter (a
+  less than 1e-2 of the oracle's own standard error on every parameter,
+  scaled by sqrt(chi2/ndf) when the oracle's fit has chi2 above ndf (a
   short track measures q/pT poorly: on the pile-up event an 18-hit tracklet
   with the oracle's hits differs by 3.7x the q/pT bar, 1.3e-3 of its
   standard error).  For short,
@@ -60,11 +61,18 @@ def param_errors(gp, op):
     return d, s
 
 
-def sigma_errors(gp, op, oC):
-    """Per-parameter |GPU - oracle| in units of the oracle's standard error."""
+def sigma_errors(gp, op, oC, chi2=None, ndf=None):
+    """Per-parameter |GPU - oracle| in units of the oracle's standard error,
+    scaled by max(1, sqrt(chi2/ndf)) of the oracle's fit when given (the
+    usual scale factor of a fit whose chi2 exceeds its degrees of freedom:
+    its covariance understates the spread of the parameters)."""
     d = np.abs(np.asarray(gp, np.float64) - np.asarray(op, np.float64))
     var = np.asarray(oC, np.float64)[..., list(DIAG)]
-    return d / np.sqrt(np.maximum(var, 1e-300))
+    sd = np.sqrt(np.maximum(var, 1e-300))
+    if chi2 is not None and ndf is not None:
+        f = np.sqrt(np.maximum(1.0, np.asarray(chi2, np.float64) / np.maximum(np.asarray(ndf), 1)))
+        sd = sd * np.asarray(f)[..., None] if np.ndim(f) else sd * f
+    return d / sd
 
 
 def check_param_bars(scaled, what="tracks", sig=None):
@@ -217,7 +225,8 @@ def compare_tracklets(gt, ot, n_rows, c2_chain=None):
             d, s = param_errors(gt["p"][gi], ot["t_p"][oi])
             rep["param_scaled"].append(s)
             rep["param_abs"].append(d)
-            rep["param_sig"].append(sigma_errors(gt["p"][gi], ot["t_p"][oi], ot["t_C"][oi]))
+            rep["param_sig"].append(sigma_errors(gt["p"][gi], ot["t_p"][oi], ot["t_C"][oi],
+                                                 ot["t_chi2"][oi], ot["t_ndf"][oi]))
     rep["param_scaled"] = np.array(rep["param_scaled"]).reshape(-1, 5)
     rep["param_abs"] = np.array(rep["param_abs"]).reshape(-1, 5)
     rep["param_sig"] = np.array(rep["param_sig"]).reshape(-1, 5)
@@ -269,7 +278,8 @@ def compare_tracks(gtr, ot, taint):
         gj, oj = g_set[h], o_set[h]
         _, s = param_errors(gtr.param[gj], ot["k_p"][oj])
         rep["param_scaled"].append(s)
-        rep["param_sig"].append(sigma_errors(gtr.param[gj], ot["k_p"][oj], ot["k_C"][oj]))
+        rep["param_sig"].append(sigma_errors(gtr.param[gj], ot["k_p"][oj], ot["k_C"][oj],
+                                             ot["k_chi2"][oj], ot["k_ndf"][oj]))
         if gtr.sector[gj] != ot["k_sector"][oj] or gtr.ndf[gj] != ot["k_ndf"][oj]:
             rep.setdefault("meta_mismatch", []).append(h)
     rep["param_scaled"] = np.array(rep["param_scaled"]).reshape(-1, 5)
