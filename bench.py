@@ -88,22 +88,50 @@ def peaks():
 # Algorithmic bytes per cluster of each step of the method (each stage's
 # arrays read or written once, the brute-force pair search not counted; f_a,
 # the share of clusters on a tracklet, taken as 0.9): a1 binning 40, a2
-# neighbours 14, a3 cleaner 12, a4 start hits 4, a5 tracklet construction
-# (weight init, chain link, y z forward and backward, rowhit, weight
-# read-modify-write, header) 43, a6 selector 15; 128 in all.  These are the
-# roofline's bytes; kernel_bytes() below counts what this implementation's
-# kernels move (with ~2.8 tracklets per track), reported beside them.
+# neighbours 14, a3 cleaner 12, a4 start hits 4, a5 tracklet construction 43,
+# a6 selector 15; 128 in all.  Each kernel gets the part of its stage that it
+# moves: a1 histogram read 12 (k_count), scan 4 (k_rowscan), scatter read 12
+# + write 12 (k_scatter); a5 chain links 2 f_a (k_chains), y z 8 and rowhit 4
+# per hit forward (k_constructor_fwd), y z 8 per hit and the header 0.7
+# backward (k_constructor_bwd), weight init 8 and read-modify-write 16 per
+# hit (k_weights); a6 rowhit 4 and weight 8 per hit (k_sel_decide), header
+# 0.7 (k_sel_sort), hit cids out 4 per hit (k_sel_write).  Kernels that the
+# method's byte model has no part for (the in-row sort, the dominance check)
+# get 0.  kernel_bytes() below counts what this implementation's kernels
+# move, reported beside them.
+F_A = 0.9
 STAGE_BYTES = {"a1": 40, "a2": 14, "a3": 12, "a4": 4, "a5": 43, "a6": 15}
 PATH_BYTES = sum(STAGE_BYTES.values())
 KERNEL_STAGE = {"k_count": "a1", "k_rowscan": "a1", "k_scatter": "a1", "k_rowsort": "a1",
                 "k_rowsort_big": "a1", "k_neighbours": "a2", "k_clean_starts": "a3+a4",
-                "k_chains": "a5", "k_constructor": "a5", "k_weights": "a5",
+                "k_chains": "a5", "k_constructor_fwd": "a5", "k_dominance": "a5",
+                "k_constructor_bwd": "a5", "k_weights": "a5",
                 "k_sel_decide": "a6", "k_sel_sort": "a6", "k_sel_write": "a6"}
+KERNEL_BYTES = {"k_count": 12, "k_rowscan": 4, "k_scatter": 24, "k_rowsort": 0,
+                "k_rowsort_big": 0, "k_neighbours": 14, "k_clean_starts": 16,
+                "k_chains": 2 * F_A, "k_constructor_fwd": 12 * F_A, "k_dominance": 0,
+                "k_constructor_bwd": 8.7 * F_A, "k_weights": 8 + 16 * F_A,
+                "k_sel_decide": 12 * F_A, "k_sel_sort": 0.7, "k_sel_write": 4 * F_A}
 ROOFLINE_TARGET = 0.40  # share of the HBM roofline asked of the path
 
 
-def stage_bytes_per_cluster(kernel: str) -> int:
-    return sum(STAGE_BYTES[s] for s in KERNEL_STAGE[kernel].split("+"))
+def stage_bytes_per_cluster(kernel: str) -> float:
+    return KERNEL_BYTES.get(kernel, 0.0)
+
+
+def stage_rooflines(ktimes: dict, n: int, peak: float) -> dict:
+    """Each step of the method (a1 .. a6) as one unit: its algorithmic bytes
+    over the summed mean launch times of its kernels."""
+    out = {}
+    for st, b in STAGE_BYTES.items():
+        ks = [k for k, v in KERNEL_STAGE.items() if st in v.split("+") and k in ktimes]
+        ms = sum(ktimes[k][0] / ktimes[k][1] for k in ks)
+        if ms <= 0:
+            continue
+        out[st] = {"kernels": ks, "ms": ms, "bytes_per_cluster": b,
+                   "achieved_gbs": b * n / (ms * 1e-3) / 1e9,
+                   "frac": b * n / (ms * 1e-3) / 1e9 / peak}
+    return out
 
 
 def kernel_bytes(c: dict) -> dict:
@@ -119,7 +147,10 @@ def kernel_bytes(c: dict) -> dict:
         "k_neighbours": 8 * N + 4 * N + 4 * B,
         "k_clean_starts": 4 * N + 4 * N + 4 * N + 4 * N + 4 * T,
         "k_chains": 8 * c["n_chain_hits"] + 32 * T,
-        "k_constructor": 24 * Th + 116 * Tl,
+        # forward passes of every chain, backward passes of the chains kept
+        "k_constructor_fwd": 12 * (c["n_chain_hits"] + Th) + 40 * (Tl + c["n_dominated_chains"]),
+        "k_dominance": 8 * c["n_chain_hits"],
+        "k_constructor_bwd": 16 * Th + 116 * Tl,
         "k_weights": 20 * Th + 32 * Tl,
         "k_sel_decide": 10 * Th + 32 * T,
         "k_sel_sort": 12 * T + 8 * K,
@@ -1119,6 +1150,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": dom_bytes,
                          "algorithmic_bytes_per_cluster": stage_bytes_per_cluster(dom),
                          "stage": KERNEL_STAGE[dom], "launch_ms": dom_ms,
+                         "stages": stage_rooflines(ktimes, n, peak),
                          "impl_bytes_per_launch": kb[dom],
                          "frac_impl_bytes": kb[dom] / (dom_ms * 1e-3) / 1e9 / peak},
             "path_roofline": {"bytes_per_cluster": PATH_BYTES,

@@ -310,10 +310,13 @@ void tpc_chi2_calib_destroy(tpc_chi2_calib* c);
 
 /* Per-launch counters of the last tpc_track_results (for the byte model
  * of the benchmark and for tests).  n_chain_hits is the number of hits on
- * the chains of all start hits (every start hit included). */
+ * the chains of all start hits (every start hit included); n_tracklets
+ * counts the chains that got a tracklet, n_dominated_chains those that did
+ * not because other tracklets' forward extensions took all their hits. */
 typedef struct {
     int64_t n_clusters, n_rows_total, n_bins, n_links, n_starts, n_tracklets,
             n_valid_tracklets, n_tracklet_hits, n_tracks, n_track_hits, n_chain_hits;
+    int64_t n_dominated_chains;
     int64_t n_merge_links, n_merge_chains;  /* merger: links, refitted chains (0 without merge) */
     int64_t n_sector_tracks;                /* tracks before merging (= n_tracks without merge) */
     int64_t max_row_hits;       /* high-water marks: clusters of the fullest (sector, row) of the */
@@ -348,11 +351,6 @@ int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, in
  *   streams            slots that consecutive direct launches go to in turn,
  *                      each on its own stream (1..max_streams, the context's
  *                      max_events_in_flight; see tpc_track_launch)
- *   tl_mode            tracklet constructor: 0 persistent lanes (one lane per
- *                      tracklet, refilled from a work counter), 1 row sweep
- *                      (a block sweeps the pad rows of a chunk of tracklets
- *                      with each row's hits staged in shared memory); both
- *                      give the same tracklets
  *   nb_mode            neighbour finder: 0 one thread per hit, 1 one block
  *                      per pad row with the two adjacent rows staged in
  *                      shared memory; both give the same links
@@ -362,7 +360,7 @@ typedef struct {
     int n_sm, tl_max_per_sm;
     int bin_blocks_per_sm, sort_threads, nb_threads, tl_blocks_per_sm;
     int max_streams, streams;
-    int tl_mode, nb_mode;
+    int nb_mode;
 } tpc_track_schedule;
 int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out);
 int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);

@@ -66,7 +66,7 @@ _P = C.c_void_p
 
 class OrcResult(C.Structure):
     _fields_ = [("up", _P), ("dn", _P), ("c2_tie", _P), ("up32", _P), ("dn32", _P),
-                ("up_c", _P), ("dn_c", _P),
+                ("fwd_mark", _P), ("up_c", _P), ("dn_c", _P),
                 ("cap_tracklets", C.c_int64),
                 ("t_start", _P), ("t_sector", _P), ("t_chain_len", _P), ("t_valid", _P),
                 ("t_nhits", _P), ("t_first_row", _P), ("t_last_row", _P), ("t_flags", _P),
@@ -76,7 +76,7 @@ class OrcResult(C.Structure):
                 ("k_C", _P), ("k_chi2", _P), ("k_hit_off", _P), ("k_hit_cid", _P),
                 ("n_tracklets", C.c_int64), ("n_tracks", C.c_int64), ("n_track_hits", C.c_int64),
                 ("n_links", C.c_int64), ("n_link_flips32", C.c_int64), ("n_c2_ties", C.c_int64),
-                ("n_starts", C.c_int64)]
+                ("n_starts", C.c_int64), ("n_dominated", C.c_int64)]
 
 
 @dataclass
@@ -146,6 +146,7 @@ def track_event(ev, params: Params | None = None, *, shadow32: bool = False) -> 
     o = {
         "up": np.empty(n, np.int32), "dn": np.empty(n, np.int32),
         "c2_tie": np.empty(n, np.int32),
+        "fwd_mark": np.empty(n, np.int32),
         "up32": np.empty(n, np.int32) if shadow32 else None,
         "dn32": np.empty(n, np.int32) if shadow32 else None,
         "up_c": np.empty(n, np.int32), "dn_c": np.empty(n, np.int32),
@@ -174,7 +175,7 @@ def track_event(ev, params: Params | None = None, *, shadow32: bool = False) -> 
     nt, nk, nh = res.n_tracklets, res.n_tracks, res.n_track_hits
     out = {"status": rc, "n_tracklets": nt, "n_tracks": nk, "n_track_hits": nh,
            "n_links": res.n_links, "n_link_flips32": res.n_link_flips32,
-           "n_c2_ties": res.n_c2_ties,
+           "n_c2_ties": res.n_c2_ties, "n_dominated": res.n_dominated,
            "n_starts": res.n_starts}
     for k, a in o.items():
         if a is None:

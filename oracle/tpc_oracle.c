@@ -76,6 +76,8 @@ typedef struct {
     int32_t* c2_tie; /* C2 near-tie bits per hit (ORC_C2_TIE_*) */
     int32_t* up32;   /* C2, binary32 restatement (diagnostic, may be NULL) */
     int32_t* dn32;
+    int32_t* fwd_mark; /* C7a: 1 if a forward extension search took the hit, | 2 if
+                          one whose pass carries near-tie bits did (may be NULL) */
     int32_t* up_c;   /* C3 */
     int32_t* dn_c;
     /* tracklets (one per chain of >= min_chain hits), capacity cap_tracklets */
@@ -109,7 +111,7 @@ typedef struct {
     int32_t* k_hit_cid;   /* [n] */
     /* counters (out) */
     int64_t n_tracklets, n_tracks, n_track_hits;
-    int64_t n_links, n_link_flips32, n_c2_ties, n_starts;
+    int64_t n_links, n_link_flips32, n_c2_ties, n_starts, n_dominated;
 } orc_result;
 
 enum {
@@ -488,7 +490,7 @@ static int32_t search_row(const hits_t* H, const orc_config* cfg, int sec, int r
 }
 
 /*
- * Near-tie bits (T->flags): a chi2 decision within tie_chi2 of the cut or of
+ * Near-tie bits (flags): a chi2 decision within tie_chi2 of the cut or of
  * the runner-up, |s| within tie_sin of sin_max at a transport, |y| or |z|
  * within tie_edge of a stop bound, and ORC_TIE_CHAIN when a chain hit is
  * updated (without a test, as the chain prescribes) with a chi2 increment
@@ -496,28 +498,31 @@ static int32_t search_row(const hits_t* H, const orc_config* cfg, int sec, int r
  * joined two particles), the fit is pulled far outside its own covariance,
  * and its later decisions depend on the precision of the arithmetic.
  *
- * Chain h[0..k] on consecutive rows of sector sec (k + 1 >= min_chain).
- * Seed at x of h0: (y, z) of h0, tan(phi) and dz/dx from the chord h0 -> hk,
- * s = tan(phi)/sqrt(1 + tan^2 phi), t = (dz/dx) cos(phi), q/pT = 0, C = seed.
- * Forward: update at h0, transport + update at each chain hit (no test), then
- * extend outward row by row with the chi2 search, ending after max_gap misses
- * in a row, at a transport failure or outside the sector.  Backward: from the
- * last assigned row L with the state kept there and C reset to the seed,
- * update at L, then go inward: rows assigned forward are updated without a
- * test, rows below the first forward row are searched as above.  The result
- * is the state and covariance right after the last backward update (the
- * innermost hit); chi2 and ndf = 2 nUpd - 5 come from the backward pass.
- * rowhit[] receives the backward hit set (cid per row, -1 elsewhere).
+ * The tracklet of a chain h[0..k] on consecutive rows of sector sec
+ * (k + 1 >= min_chain) is built in two passes.
+ *
+ * Forward: seed at x of h0 with (y, z) of h0, tan(phi) and dz/dx from the
+ * chord h0 -> hk, s = tan(phi)/sqrt(1 + tan^2 phi), t = (dz/dx) cos(phi),
+ * q/pT = 0, C = seed; update at h0, transport + update at each chain hit (no
+ * test), then extend outward row by row with the chi2 search, ending after
+ * max_gap misses in a row, at a transport failure or outside the sector.
+ * The hits the extension search takes are the forward extension hits.
  */
-static void build_tracklet(const hits_t* H, const orc_config* cfg, int sec,
-                           const int32_t* chain, int k1, tracklet_t* T, int32_t* rowhit)
+typedef struct {
+    int32_t* fwd;       /* [n_rows] forward hit per row (cid or -1) */
+    int r0, rk, last;   /* first and last chain row, last assigned row */
+    int flags;
+    double pL[5];       /* state right after the update at row last */
+} fwdpass_t;
+
+static void forward_pass(const hits_t* H, const orc_config* cfg, int sec, const int32_t* chain,
+                         int k1, fwdpass_t* F)
 {
     const int R = H->n_rows;
     const double vy = cfg->sigma_y * cfg->sigma_y, vz = cfg->sigma_z * cfg->sigma_z;
-    int32_t fwd[512];
+    int32_t* fwd = F->fwd;
     for (int r = 0; r < R; ++r) fwd[r] = -1;
     int flags = 0;
-
     const int r0 = H->row[chain[0]];
     const int rk = H->row[chain[k1 - 1]];
     double p[5], C[5][5];
@@ -525,12 +530,11 @@ static void build_tracklet(const hits_t* H, const orc_config* cfg, int sec,
                H->z[chain[k1 - 1]], p);
     seed_cov(cfg, C, p[2]);
     double x = H->xr[r0];
-    /* forward pass over the chain */
+    /* over the chain */
     orc_update(p, C, H->y[chain[0]], H->z[chain[0]], vy, vz);
     fwd[r0] = chain[0];
     int last = r0;
-    double pL[5];
-    memcpy(pL, p, sizeof(pL));
+    memcpy(F->pL, p, sizeof(F->pL));
     int stopped = 0;
     for (int i = 1; i < k1; ++i) {
         const int r = H->row[chain[i]];
@@ -543,9 +547,9 @@ static void build_tracklet(const hits_t* H, const orc_config* cfg, int sec,
             flags |= ORC_TIE_CHAIN;
         fwd[r] = chain[i];
         last = r;
-        memcpy(pL, p, sizeof(pL));
+        memcpy(F->pL, p, sizeof(F->pL));
     }
-    /* forward extension */
+    /* extension */
     if (!stopped) {
         int gap = 0;
         for (int r = rk + 1; r < R; ++r) {
@@ -558,19 +562,41 @@ static void build_tracklet(const hits_t* H, const orc_config* cfg, int sec,
                 orc_update(p, C, H->y[c], H->z[c], vy, vz);
                 fwd[r] = c;
                 last = r;
-                memcpy(pL, p, sizeof(pL));
+                memcpy(F->pL, p, sizeof(F->pL));
                 gap = 0;
             } else if (++gap >= cfg->max_gap) {
                 break;
             }
         }
     }
+    F->r0 = r0;
+    F->rk = rk;
+    F->last = last;
+    F->flags = flags;
+}
 
-    /* backward pass */
+/*
+ * Backward: from the last assigned row L with the forward state kept there
+ * and C reset to the seed, update at L, then go inward: rows assigned forward
+ * are updated without a test, rows below the first chain row are searched as
+ * above.  The result is the state and covariance right after the last
+ * backward update (the innermost hit); chi2 and ndf = 2 nUpd - 5 come from
+ * the backward pass.  rowhit[] receives the backward hit set (cid per row,
+ * -1 elsewhere).
+ */
+static void backward_pass(const hits_t* H, const orc_config* cfg, int sec, const fwdpass_t* F,
+                          tracklet_t* T, int32_t* rowhit)
+{
+    const int R = H->n_rows;
+    const double vy = cfg->sigma_y * cfg->sigma_y, vz = cfg->sigma_z * cfg->sigma_z;
+    const int32_t* fwd = F->fwd;
+    const int r0 = F->r0, last = F->last;
+    int flags = F->flags;
+    double p[5], C[5][5];
     for (int r = 0; r < R; ++r) rowhit[r] = -1;
-    memcpy(p, pL, sizeof(pL));
+    memcpy(p, F->pL, sizeof(p));
     seed_cov(cfg, C, p[2]);
-    x = H->xr[last];
+    double x = H->xr[last];
     double chi2 = orc_update(p, C, H->y[fwd[last]], H->z[fwd[last]], vy, vz);
     int nupd = 1;
     rowhit[last] = fwd[last];
@@ -708,39 +734,86 @@ int orc_track_event(const orc_config* cfg, const float* row_x, int64_t n, const 
         res->up_c[i] = (u >= 0 && res->dn[u] == (int32_t)i) ? u : -1;
         res->dn_c[i] = (d >= 0 && res->up[d] == (int32_t)i) ? d : -1;
     }
-    /* C4 + C7: chains from start hits, in (sector, row, cid) order */
+    /* C4 + C7: chains from start hits, in (sector, row, cid) order.  First
+     * the forward pass of every chain, marking the hits its extension search
+     * takes; then C7a: a chain all of whose hits are marked lies on a track
+     * that other tracklets already follow outward, and gets no tracklet (it
+     * is dominated); the others get their backward pass. */
     int status = 0;
     int64_t nt = 0;
     res->n_starts = 0;
-    int32_t chain[512];
-    for (int64_t k = 0; k < (int64_t)S * R && status == 0; ++k) {
+    res->n_dominated = 0;
+    int64_t cap_ch = 64, n_ch = 0, n_chain_hits = 0, cap_hits = 1024;
+    int32_t* ch_start = malloc(sizeof(int32_t) * cap_ch);
+    int32_t* ch_sec = malloc(sizeof(int32_t) * cap_ch);
+    int64_t* ch_off = malloc(sizeof(int64_t) * (cap_ch + 1));
+    int32_t* ch_hits = malloc(sizeof(int32_t) * cap_hits);
+    ch_off[0] = 0;
+    for (int64_t k = 0; k < (int64_t)S * R; ++k) {
         const int sec = (int)(k / R);
         for (int64_t a = H.list_off[k]; a < H.list_off[k + 1]; ++a) {
             const int32_t h = H.list_cid[a];
             if (!(res->up_c[h] >= 0 && res->dn_c[h] < 0)) continue;
             res->n_starts++;
             int len = 0;
-            for (int32_t c = h; c >= 0 && len < 512; c = res->up_c[c]) chain[len++] = c;
+            for (int32_t c = h; c >= 0 && len < R; c = res->up_c[c]) ++len;
             if (len < cfg->min_chain) continue;
-            if (nt >= res->cap_tracklets) { status = -4; break; }
-            tracklet_t T;
-            build_tracklet(&H, cfg, sec, chain, len, &T, res->t_rowhit + nt * R);
-            res->t_start[nt] = h;
-            res->t_sector[nt] = sec;
-            res->t_chain_len[nt] = len;
-            res->t_valid[nt] = T.valid;
-            res->t_nhits[nt] = T.nhits;
-            res->t_first_row[nt] = T.first_row;
-            res->t_last_row[nt] = T.last_row;
-            res->t_flags[nt] = T.flags;
-            res->t_ndf[nt] = T.ndf;
-            res->t_x[nt] = T.x;
-            memcpy(res->t_p + nt * 5, T.p, sizeof(T.p));
-            cov_to_tri(T.C, res->t_C + nt * 15);
-            res->t_chi2[nt] = T.chi2;
-            ++nt;
+            if (n_ch + 1 >= cap_ch) {
+                cap_ch *= 2;
+                ch_start = realloc(ch_start, sizeof(int32_t) * cap_ch);
+                ch_sec = realloc(ch_sec, sizeof(int32_t) * cap_ch);
+                ch_off = realloc(ch_off, sizeof(int64_t) * (cap_ch + 1));
+            }
+            while (n_chain_hits + len > cap_hits) {
+                cap_hits *= 2;
+                ch_hits = realloc(ch_hits, sizeof(int32_t) * cap_hits);
+            }
+            int q = 0;
+            for (int32_t c = h; c >= 0 && q < len; c = res->up_c[c]) ch_hits[n_chain_hits + q++] = c;
+            n_chain_hits += len;
+            ch_start[n_ch] = h;
+            ch_sec[n_ch] = sec;
+            ch_off[++n_ch] = n_chain_hits;
         }
     }
+    fwdpass_t* F = malloc(sizeof(fwdpass_t) * (n_ch + 1));
+    int32_t* fwd_rows = malloc(sizeof(int32_t) * (size_t)(n_ch + 1) * R);
+    unsigned char* marked = calloc((size_t)n + 1, 1);
+    for (int64_t i = 0; i < n_ch; ++i) {
+        F[i].fwd = fwd_rows + (size_t)i * R;
+        forward_pass(&H, cfg, ch_sec[i], ch_hits + ch_off[i], (int)(ch_off[i + 1] - ch_off[i]), &F[i]);
+        for (int r = F[i].rk + 1; r <= F[i].last; ++r)
+            if (F[i].fwd[r] >= 0) marked[F[i].fwd[r]] |= F[i].flags ? 3 : 1;
+    }
+    if (res->fwd_mark)
+        for (int64_t i = 0; i < n; ++i) res->fwd_mark[i] = marked[i];
+    for (int64_t i = 0; i < n_ch && status == 0; ++i) {
+        int all = 1;
+        for (int64_t q = ch_off[i]; q < ch_off[i + 1]; ++q) all = all && marked[ch_hits[q]];
+        if (all) {
+            res->n_dominated++;
+            continue;
+        }
+        if (nt >= res->cap_tracklets) { status = -4; break; }
+        tracklet_t T;
+        backward_pass(&H, cfg, ch_sec[i], &F[i], &T, res->t_rowhit + nt * R);
+        res->t_start[nt] = ch_start[i];
+        res->t_sector[nt] = ch_sec[i];
+        res->t_chain_len[nt] = (int32_t)(ch_off[i + 1] - ch_off[i]);
+        res->t_valid[nt] = T.valid;
+        res->t_nhits[nt] = T.nhits;
+        res->t_first_row[nt] = T.first_row;
+        res->t_last_row[nt] = T.last_row;
+        res->t_flags[nt] = T.flags;
+        res->t_ndf[nt] = T.ndf;
+        res->t_x[nt] = T.x;
+        memcpy(res->t_p + nt * 5, T.p, sizeof(T.p));
+        cov_to_tri(T.C, res->t_C + nt * 15);
+        res->t_chi2[nt] = T.chi2;
+        ++nt;
+    }
+    free(F); free(fwd_rows); free(marked);
+    free(ch_start); free(ch_sec); free(ch_off); free(ch_hits);
     res->n_tracklets = nt;
     /* C7 weights: key = (nHits << 32) | (0xFFFFFFFF - cid(h0)), max over valid tracklets */
     for (int64_t i = 0; i < n; ++i) res->weight[i] = 0;

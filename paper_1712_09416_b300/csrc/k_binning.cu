@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
                 L.hcid[base + p] = L.tmp_cid[base + p];
                 L.hrow[base + p] = hrow;
                 L.weight[base + p] = 0ULL;
+                if (L.mark) L.mark[base + p] = 0;
             }
             for (int b = threadIdx.x; b <= nb; b += blockDim.x) L.bin_start[G.bin_off + b] = 0;
             continue;
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
             L.hcid[base + p] = scid[i];
             L.hrow[base + p] = hrow;
             L.weight[base + p] = 0ULL;
+            if (L.mark) L.mark[base + p] = 0;
         }
         for (int b = threadIdx.x; b <= nb; b += blockDim.x) L.bin_start[G.bin_off + b] = hist[b];
         __syncthreads();

@@ -3,12 +3,15 @@
 // one-thread-per-track fit (Sect. 4.1, Listing 2).
 //
 // k_chains follows, for every start hit, the chain of cleaned up-links (one
-// thread per start hit).  k_constructor then, one lane per chain, seeds a
+// thread per start hit).  k_constructor<1> then, one lane per chain, seeds a
 // state (y, z, sin phi, tan lambda, q/pT) from the chord of the chain, fits
-// the chain forward, extends it outward row by row (transport to the pad-row
-// plane, least-chi2 hit in the box that bounds the chi2 ellipse, update), then
-// refits backward from the last hit with the covariance reset to the seed,
-// picking up hits below the chain the same way.  The result is the state and
+// the chain forward and extends it outward row by row (transport to the
+// pad-row plane, least-chi2 hit in the box that bounds the chi2 ellipse,
+// update), marking every hit its extension search takes.  k_dominance drops
+// the chains all of whose hits were taken so (other tracklets already follow
+// their track outward).  k_constructor<2> refits the remaining chains
+// backward from the last hit with the covariance reset to the seed, picking
+// up hits below the chain the same way; the result is the state and
 // covariance at the innermost hit.  The 5-vector and the 15 covariance
 // entries live in registers; the forward hit list lives in the tracklet's
 // rowhit slot and the inputs of the next row are loaded one step ahead.
@@ -22,9 +25,10 @@
 //   dS^2 [ (s1/c1) sinc^2(dphi/2) / 2 + (sin dphi - dphi)/dphi^2 ],  dphi = C_k dS,
 // a form without cancellation as C_k -> 0.
 // Bytes: k_chains 8 per chain hit (link read, rowhit write) + 32 per start;
-// k_constructor per assigned hit y z 8 (forward) + 8 (backward), rowhit 4
-// (written) + 4 (read back), about 116 per tracklet (chain record, header);
-// k_weights per assigned hit rowhit 4 + weight read-modify-write 16.
+// forward pass per hit y z 8 + rowhit 4 (+ a mark byte per extension hit),
+// backward pass per hit y z 8 + rowhit 4 (read) + 4 (written), about 116 per
+// tracklet (chain record, header); k_weights per assigned hit rowhit 4 +
+// weight read-modify-write 16.
 #include <cuda_runtime.h>
 
 #include "tpc_internal.cuh"
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(kChThreads) k_chains(Launch L)
         TrackletHdr& H = L.tl[t];
         H.start = s;
         H.chain_len = len;
+        H.dominated = 0;
         my_hits += len;
         if (len < L.min_chain) {
             H.valid = 0;
@@ -197,10 +202,13 @@ __global__ void __launch_bounds__(kChThreads) k_chains(Launch L)
 }
 
 // Persistent lanes: every lane owns one tracklet at a time and advances it by
-// one pad row per loop iteration, forward (chain hits, then search) and then
-// backward (assigned hits, then search below the chain).  Lanes of a warp run
-// the same row-step code whatever the pass, and a lane whose tracklet is done
-// takes the next start hit at once, so the warp stays converged.
+// one pad row per loop iteration; a lane whose tracklet is done takes the
+// next start hit at once, so the warp stays converged.  PASS 1 runs the
+// forward passes (chain hits, then search) of every chain, marks the hits its
+// extension search takes and leaves the forward state at the last hit in the
+// header; PASS 2 (after k_dominance) runs the backward passes (assigned hits,
+// then search below the chain) of the chains that were not dominated.
+template <int PASS>
 __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
 {
     if (L.cnt->timeout) return;  // an earlier bounded wait gave up
@@ -262,7 +270,7 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             // warp-aggregated fetch of the next start hits
             const int leader = __ffs(m) - 1;
             int b = 0;
-            if (lane == leader) b = atomicAdd(&L.cnt->tl_next, __popc(m));
+            if (lane == leader) b = atomicAdd(PASS == 1 ? &L.cnt->tl_next : &L.cnt->tl_next2, __popc(m));
             b = __shfl_sync(0xffffffffu, b, leader);
             if (need) {
                 t = b + __popc(m & ((1u << lane) - 1));
@@ -288,8 +296,41 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
                 continue;
             }
             rowhit = L.tl_rowhit + (size_t)t * L.R;
-            const int h1 = rk > r0 ? rowhit[r0 + 1] : -1;
             const float2 c0 = L.hyz[ch.x];
+            if (PASS == 2) {
+                TrackletHdr& H = L.tl[t];
+                if (H.dominated) {  // header written by k_dominance
+                    t = -1;
+                    continue;
+                }
+                // backward from the last hit with the covariance reset to the
+                // seed, starting from the forward state left in the header
+                yref = c0.x;
+                zref = c0.y;
+                last = H.last;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) f.p[i] = H.p[i];
+                seed_cov(f, L);
+                f.x = xs[last];
+                const float2 c = L.hyz[rowhit[last]];
+                chi2 = update(f, c.x - yref, c.y - zref, L);
+                nupd = 1;
+                first = last;
+                BEST(0) = f.x;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) BEST(1 + i) = f.p[i];
+#pragma unroll
+                for (int i = 0; i < 15; ++i) BEST(6 + i) = f.C[i];
+                gap = 0;
+                phase = 2;
+                r = last - 1;
+                if (r >= 0) {
+                    ph2 = r >= r0 ? rowhit[r] : -1;
+                    stage(r, false);
+                }
+                continue;
+            }
+            const int h1 = rk > r0 ? rowhit[r0 + 1] : -1;
             // seed from the chord h0 -> hk, update at h0
             const float2 ck = L.hyz[ch.z];
             const float x0 = xs[r0], x1 = xs[rk];
@@ -316,7 +357,7 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             if (r < L.R) stage(r, true);
         }
         // ---- one row step of the current pass ----
-        const bool fwd = phase == 1;
+        constexpr bool fwd = PASS == 1;
         bool end_pass = fwd ? r >= L.R : r < 0;
         if (!end_pass) {
             const bool known = pknown;
@@ -337,7 +378,10 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
                     if (h >= 0) {
                         const float dchi2 = update(f, my, mz, L);
                         if (fwd) {
-                            if (!known) rowhit[r] = h;
+                            if (!known) {
+                                rowhit[r] = h;
+                                L.mark[h] = 1;  // taken by a forward extension search
+                            }
                             last = r;
 #pragma unroll
                             for (int i = 0; i < 5; ++i) PL(i) = f.p[i];
@@ -367,27 +411,14 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
         }
         if (!end_pass) continue;
         if (fwd) {
-            // backward from the last hit with the covariance reset to the seed
+            // forward pass done: the state at the last hit (relative to the
+            // start hit) and the last row wait in the header for PASS 2
+            TrackletHdr& H = L.tl[t];
 #pragma unroll
-            for (int i = 0; i < 5; ++i) f.p[i] = PL(i);
-            seed_cov(f, L);
-            f.x = xs[last];
-            const float2 c = L.hyz[rowhit[last]];
-            chi2 = update(f, c.x - yref, c.y - zref, L);
-            nupd = 1;
-            first = last;
-            BEST(0) = f.x;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) BEST(1 + i) = f.p[i];
-#pragma unroll
-            for (int i = 0; i < 15; ++i) BEST(6 + i) = f.C[i];
-            gap = 0;
-            phase = 2;
-            r = last - 1;
-            if (r >= 0) {
-                ph2 = r >= r0 ? rowhit[r] : -1;
-                stage(r, false);
-            }
+            for (int i = 0; i < 5; ++i) H.p[i] = PL(i);
+            H.last = last;
+            t = -1;
+            phase = 0;
             continue;
         }
         // tracklet done: header (the hit weights are raised by k_weights)
@@ -433,6 +464,42 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
     }
 }
 
+// Dominance: one warp per chain, lanes over its rows.  A chain all of whose
+// hits were taken by forward extension searches (of other tracklets: a
+// tracklet's own extension starts above its chain) gets no tracklet; its
+// header is made final here and the backward pass skips it.
+__global__ void k_dominance(Launch L)
+{
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
+    const int n_st = min(L.cnt->n_starts, L.t_cap);
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    int n_dom = 0;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_st; t += warps) {
+        const int4 ch = L.tl_chain[t];
+        const int r0 = ch.y & 255, rk = ch.w;
+        if (rk - r0 + 1 < L.min_chain) continue;
+        const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
+        bool all = true;
+        for (int r = r0 + lane; r <= rk; r += 32) all = all && L.mark[rowhit[r]];
+        if (!__all_sync(0xffffffffu, all)) continue;
+        if (lane == 0) {
+            TrackletHdr& H = L.tl[t];
+            H.dominated = 1;
+            H.valid = 0;
+            H.nhits = 0;
+            H.first = -1;
+            H.last = -1;
+            H.ndf = 0;
+            ++n_dom;
+        }
+    }
+    if (n_dom) {
+        atomicAdd(&L.cnt->n_dominated, n_dom);
+        atomicSub(&L.cnt->n_tracklets, n_dom);
+    }
+}
+
 // Hit weights: one warp per tracklet, lanes over its rows; every hit of a
 // valid tracklet gets atomicMax(weight, (nHits << 32) | (0xFFFFFFFF - cid(h0))).
 __global__ void k_weights(Launch L)
@@ -454,442 +521,14 @@ __global__ void k_weights(Launch L)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Row-synchronous constructor (schedule tl_mode = 1): a block takes a chunk of
-// kSwThreads consecutive start hits (one tracklet per thread; consecutive
-// starts lie in few sectors and a narrow band of rows) and sweeps the pad rows
-// once outward (every forward pass of the chunk advances by one row per
-// step) and once inward (every backward pass).  The hits and bin offsets of
-// the row being swept are staged in shared memory for up to kSwSecs sectors
-// of the chunk (one copy warp each, cp.async, one row ahead), so the window
-// searches and the known-hit reads hit shared memory instead of L2.  A sector
-// row that does not fit, or a sector beyond the first kSwSecs, is read from
-// global memory.  Every tracklet does exactly the arithmetic of k_constructor,
-// so the results are identical; only the schedule differs.
-constexpr int kSwThreads = 128;
-constexpr int kSwSecs = kSwThreads / 32;  // staged sectors: one copy warp each
-constexpr int kSwCap = 1024;              // staged hits of one row step, all slots
-constexpr int kSwBinCap = 2 * kSwCap + 2 * kSwSecs;
-
-struct SwDesc {          // one (sector, row) of a row step
-    const float2* yz;    // its hits (shared memory when staged)
-    const int* bins;     // its bin offsets (shared memory when staged)
-    RowGrid G;
-    int base;            // global sorted index of the row's first hit
-    int pad[3];
-};
-
-constexpr size_t sweep_smem()
-{
-    return sizeof(float2) * 2 * kSwCap + sizeof(int) * 2 * kSwBinCap +
-           sizeof(SwDesc) * 2 * kSwSecs + sizeof(float) * 26 * kSwThreads +
-           sizeof(float) * kMaxRows;
-}
-
-// Least-chi2 hit of a row described by D (same rule and arithmetic as search()).
-__device__ __forceinline__ int search_sw(const Fit& f, float yref, float zref, const SwDesc& D,
-                                         const Launch& L, float& my, float& mz)
-{
-    const RowGrid& G = D.G;
-    const float* C = f.C;
-    const float S00 = C[0] + L.sy2, S01 = C[1], S11 = C[2] + L.sz2;
-    const float id = __fdividef(1.0f, S00 * S11 - S01 * S01);
-    const float wy = 1.01f * sqrtf(L.chi2_hit * S00) + 1e-3f;
-    const float wz = 1.01f * sqrtf(L.chi2_hit * S11) + 1e-3f;
-    const float ya = f.p[0] + yref, za = f.p[1] + zref;
-    const int y0 = bin_y(G, ya - wy), y1 = bin_y(G, ya + wy);
-    const int z0 = bin_z(G, za - wz), z1 = bin_z(G, za + wz);
-    const int* bins = D.bins;
-    const float2* yz = D.yz;
-    float best = 3.0e38f, by = 0.0f, bzv = 0.0f;
-    int bk = -1;
-    for (int bz = z0; bz <= z1; bz += 2) {
-        // two z-bins per pass, their hit ranges walked as one list
-        const int a0 = bins[bz * G.ny + y0], b0 = bins[bz * G.ny + y1 + 1];
-        int a1 = 0, b1 = 0;
-        if (bz + 1 <= z1) {
-            a1 = bins[(bz + 1) * G.ny + y0];
-            b1 = bins[(bz + 1) * G.ny + y1 + 1];
-        }
-        const int n0 = b0 - a0, tot = n0 + (b1 - a1);
-        for (int q = 0; q < tot; q += 4) {
-            int kk[4];
-            float2 c[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int qj = q + j < tot ? q + j : 0;
-                kk[j] = qj < n0 ? a0 + qj : a1 + (qj - n0);
-                c[j] = yz[kk[j]];
-                c[j].x -= yref;
-                c[j].y -= zref;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (q + j >= tot) break;
-                const float r0 = c[j].x - f.p[0];
-                const float r1 = c[j].y - f.p[1];
-                const float chi2 = (S11 * r0 * r0 - 2.0f * S01 * r0 * r1 + S00 * r1 * r1) * id;
-                if (chi2 < best ||
-                    (chi2 == best && bk >= 0 && L.hcid[D.base + kk[j]] < L.hcid[D.base + bk])) {
-                    best = chi2;
-                    bk = kk[j];
-                    by = c[j].x;
-                    bzv = c[j].y;
-                }
-            }
-        }
-    }
-    my = by;
-    mz = bzv;
-    return (bk >= 0 && best <= L.chi2_hit) ? D.base + bk : -1;
-}
-
-// Copy warp of slot w: stage (sector sec, row rr) into buffer b of the row
-// slabs, or point the descriptor at global memory when it does not fit.
-// (a, n, G) are the row's offset, hit count and grid, loaded a step ahead.
-__device__ __forceinline__ void sw_stage(const Launch& L, float2* s_yz, int* s_bins,
-                                         SwDesc* s_desc, int b, int w, int nslot, int a, int n,
-                                         const RowGrid& G)
-{
-    const int lane = threadIdx.x & 31;
-    const int cap_h = kSwCap / nslot, cap_b = kSwBinCap / nslot;
-    const int nb = G.ny * G.nz + 1;
-    const int* gbins = L.bin_start + G.bin_off;
-    SwDesc d;
-    d.G = G;
-    d.base = a;
-    if (n <= cap_h && nb <= cap_b) {
-        float2* dy = s_yz + b * kSwCap + w * cap_h;
-        int* db = s_bins + b * kSwBinCap + w * cap_b;
-        for (int i = lane; i < n; i += 32) cp_async8(dy + i, L.hyz + a + i);
-        for (int i = lane; i < nb; i += 32) cp_async4(db + i, gbins + i);
-        d.yz = dy;
-        d.bins = db;
-    } else {
-        d.yz = L.hyz + a;
-        d.bins = gbins;
-    }
-    if (lane == 0) s_desc[b * kSwSecs + w] = d;
-}
-
-__global__ void __launch_bounds__(kSwThreads) k_sweep(Launch L)
-{
-    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
-    extern __shared__ __align__(16) unsigned char sw_smem[];
-    float2* s_yz = reinterpret_cast<float2*>(sw_smem);                  // [2][kSwCap]
-    int* s_bins = reinterpret_cast<int*>(s_yz + 2 * kSwCap);            // [2][kSwBinCap]
-    SwDesc* s_desc = reinterpret_cast<SwDesc*>(s_bins + 2 * kSwBinCap); // [2][kSwSecs]
-    float* s_best = reinterpret_cast<float*>(s_desc + 2 * kSwSecs);     // [21][threads]
-    float* s_pl = s_best + 21 * kSwThreads;                             // [5][threads]
-    float* xs = s_pl + 5 * kSwThreads;                                  // [kMaxRows]
-    __shared__ int s_sec[kSwThreads];
-    __shared__ int s_slot_sec[kSwSecs];
-    __shared__ int s_nslot, s_chunk, s_rlo, s_rhi;
-#define SBEST(i) s_best[(i) * kSwThreads + threadIdx.x]
-#define SPL(i) s_pl[(i) * kSwThreads + threadIdx.x]
-    for (int i = threadIdx.x; i < L.R; i += blockDim.x) xs[i] = L.xr[i];
-    const int n_st = min(L.cnt->n_starts, L.t_cap);
-    const int n_chunks = (n_st + kSwThreads - 1) / kSwThreads;
-    const int wid = threadIdx.x >> 5;
-    int my_valid = 0, my_hits = 0;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            s_chunk = atomicAdd(&L.cnt->tl_next, 1);
-            s_rlo = L.R;
-            s_rhi = -1;
-        }
-        __syncthreads();
-        const int chunk = s_chunk;
-        if (chunk >= n_chunks) break;
-        // ---- set-up of the chunk's tracklets (as k_constructor's phase 0)
-        int t = chunk * kSwThreads + threadIdx.x;
-        int r0 = 0, rk = 0, last = 0, first = 0, gap = 0, nupd = 0, gs = -1;
-        float chi2 = 0.0f, yref = 0.0f, zref = 0.0f, mly = 0.0f, mlz = 0.0f;
-        int* rowhit = nullptr;
-        int hk = -1;  // hit of the next known row, read a step ahead
-        Fit f;
-        bool fwd_on = false;
-        if (t < n_st) {
-            const int4 ch = L.tl_chain[t];
-            gs = ch.y >> 8;
-            r0 = ch.y & 255;
-            rk = ch.w;
-            if (rk - r0 + 1 < L.min_chain) {
-                t = -1;
-                gs = -1;
-            } else {
-                rowhit = L.tl_rowhit + (size_t)t * L.R;
-                const float2 c0 = L.hyz[ch.x];
-                const float2 ckk = L.hyz[ch.z];
-                const float x0 = xs[r0], x1 = xs[rk];
-                const float tphi = (ckk.x - c0.x) / (x1 - x0);
-                const float dzdx = (ckk.y - c0.y) / (x1 - x0);
-                const float cphi = rsqrtf(1.0f + tphi * tphi);
-                yref = c0.x;
-                zref = c0.y;
-                f.x = x0;
-                f.p[0] = 0.0f;
-                f.p[1] = 0.0f;
-                f.p[2] = tphi * cphi;
-                f.p[3] = dzdx * cphi;
-                f.p[4] = 0.0f;
-                seed_cov(f, L);
-                update(f, 0.0f, 0.0f, L);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) SPL(i) = f.p[i];
-                mly = 0.0f;
-                mlz = 0.0f;
-                last = r0;
-                fwd_on = r0 + 1 < L.R;
-                hk = rk > r0 ? rowhit[r0 + 1] : -1;
-                if (fwd_on) atomicMin(&s_rlo, r0 + 1);
-                else atomicMax(&s_rhi, last);
-            }
-        } else {
-            t = -1;
-        }
-        s_sec[threadIdx.x] = gs;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            // distinct sectors of the chunk in order (starts are sorted by
-            // sector); the first kSwSecs are staged
-            int ns = 0, prev = -1;
-            for (int i = 0; i < kSwThreads; ++i) {
-                const int v = s_sec[i];
-                if (v >= 0 && v != prev) {
-                    if (ns < kSwSecs) s_slot_sec[ns] = v;
-                    ++ns;
-                    prev = v;
-                }
-            }
-            s_nslot = min(ns, kSwSecs);
-        }
-        __syncthreads();
-        const int nslot = s_nslot;
-        int slot = -1;
-        for (int j = 0; j < nslot; ++j)
-            if (s_slot_sec[j] == gs) slot = j;
-        const int gbase = gs * L.R;
-
-        // ---- the two sweeps: dir = +1 (forward passes), then -1 (backward)
-        for (int dir = 1; dir >= -1; dir -= 2) {
-            int r = dir > 0 ? s_rlo : s_rhi;
-            if (dir > 0 ? r >= L.R : r < 0) {
-                __syncthreads();
-                if (dir > 0) continue;
-                break;
-            }
-            // copy warps: row r now, the next row's offsets and grid ahead
-            int na = 0, nn = 0;
-            RowGrid nG;
-            const bool copier = wid < nslot;
-            if (copier) {
-                const int g = s_slot_sec[wid] * L.R + r;
-                const int a = L.row_off[g];
-                sw_stage(L, s_yz, s_bins, s_desc, r & 1, wid, nslot, a, L.row_off[g + 1] - a,
-                         L.grid[g]);
-                const int rn = r + dir;
-                if (rn >= 0 && rn < L.R) {
-                    na = L.row_off[g + dir];
-                    nn = L.row_off[g + dir + 1] - na;
-                    nG = L.grid[g + dir];
-                }
-            }
-            cp_async_wait_all();
-            __syncthreads();
-            bool bwd_wait = dir < 0 && t >= 0;   // backward pass not yet begun
-            bool bwd_on = false;
-            for (;;) {
-                const int rn = r + dir;
-                // (A) stage the next row
-                if (copier && rn >= 0 && rn < L.R) {
-                    sw_stage(L, s_yz, s_bins, s_desc, rn & 1, wid, nslot, na, nn, nG);
-                    const int rnn = rn + dir;
-                    if (rnn >= 0 && rnn < L.R) {
-                        const int g = s_slot_sec[wid] * L.R + rnn;
-                        na = L.row_off[g];
-                        nn = L.row_off[g + 1] - na;
-                        nG = L.grid[g];
-                    }
-                }
-                // (B) one row step of every tracklet in its pass
-                SwDesc D;
-                const bool stepping = dir > 0 ? (fwd_on && r > r0) : (bwd_on && r < last);
-                if (stepping || (bwd_wait && r == last)) {
-                    if (slot >= 0) {
-                        D = s_desc[(r & 1) * kSwSecs + slot];
-                    } else {
-                        const int g = gbase + r;
-                        D.base = L.row_off[g];
-                        D.G = L.grid[g];
-                        D.yz = L.hyz + D.base;
-                        D.bins = L.bin_start + D.G.bin_off;
-                    }
-                }
-                if (dir > 0) {
-                    int hk_next = -1;
-                    if (fwd_on && rn > r0 && rn <= rk) hk_next = rowhit[rn];
-                    if (stepping) {
-                        const bool known = r <= rk;
-                        bool end_pass = false;
-                        int h = known ? hk : -1;
-                        float my = 0.0f, mz = 0.0f;
-                        if (!transport(f, xs[r], L)) {
-                            end_pass = true;
-                        } else {
-                            if (known) {
-                                const float2 c = D.yz[h - D.base];
-                                my = c.x - yref;
-                                mz = c.y - zref;
-                            } else if (outside(f, yref, zref, L)) {
-                                end_pass = true;
-                            } else {
-                                h = search_sw(f, yref, zref, D, L, my, mz);
-                            }
-                            if (!end_pass) {
-                                if (h >= 0) {
-                                    update(f, my, mz, L);
-                                    if (!known) rowhit[r] = h;
-                                    last = r;
-                                    mly = my;
-                                    mlz = mz;
-#pragma unroll
-                                    for (int i = 0; i < 5; ++i) SPL(i) = f.p[i];
-                                    if (!known) gap = 0;
-                                } else if (!known) {
-                                    rowhit[r] = -1;
-                                    if (++gap >= L.max_gap) end_pass = true;
-                                }
-                            }
-                        }
-                        if (end_pass || r == L.R - 1) fwd_on = false;
-                        if (!fwd_on) atomicMax(&s_rhi, last);
-                    }
-                    hk = hk_next;
-                } else {
-                    int hk_next = hk;
-                    if (bwd_wait && r == last) {
-                        // backward from the last hit, covariance reset to the seed
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) f.p[i] = SPL(i);
-                        seed_cov(f, L);
-                        f.x = xs[last];
-                        chi2 = update(f, mly, mlz, L);
-                        nupd = 1;
-                        first = last;
-                        SBEST(0) = f.x;
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) SBEST(1 + i) = f.p[i];
-#pragma unroll
-                        for (int i = 0; i < 15; ++i) SBEST(6 + i) = f.C[i];
-                        gap = 0;
-                        bwd_wait = false;
-                        bwd_on = last > 0;
-                        hk_next = (rn >= r0 && rn >= 0) ? rowhit[rn] : -1;
-                    } else if (stepping) {
-                        const bool known = r >= r0;
-                        bool end_pass = false;
-                        int h = known ? hk : -1;
-                        float my = 0.0f, mz = 0.0f;
-                        if (rn >= r0 && rn >= 0) hk_next = rowhit[rn];
-                        if (!transport(f, xs[r], L)) {
-                            end_pass = true;
-                        } else {
-                            if (!known) {
-                                if (outside(f, yref, zref, L)) end_pass = true;
-                                else h = search_sw(f, yref, zref, D, L, my, mz);
-                            } else if (h >= 0) {
-                                const float2 c = D.yz[h - D.base];
-                                my = c.x - yref;
-                                mz = c.y - zref;
-                            }
-                            if (!end_pass) {
-                                if (h >= 0) {
-                                    chi2 += update(f, my, mz, L);
-                                    ++nupd;
-                                    rowhit[r] = h;
-                                    first = r;
-                                    SBEST(0) = f.x;
-#pragma unroll
-                                    for (int i = 0; i < 5; ++i) SBEST(1 + i) = f.p[i];
-#pragma unroll
-                                    for (int i = 0; i < 15; ++i) SBEST(6 + i) = f.C[i];
-                                    if (!known) gap = 0;
-                                } else if (!known) {
-                                    if (++gap >= L.max_gap) end_pass = true;
-                                }
-                            }
-                        }
-                        if (end_pass || r == 0) bwd_on = false;
-                    }
-                    hk = hk_next;
-                    if (t >= 0 && !bwd_wait && !bwd_on) {
-                        // tracklet done: header (weights are raised by k_weights)
-                        bool fin = isfinite(chi2);
-#pragma unroll
-                        for (int i = 0; i < 20; ++i) fin = fin && isfinite(SBEST(1 + i));
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) fin = fin && SBEST(6 + CI(i, i)) > 0.0f;
-                        const bool valid = nupd >= L.min_tracklet_hits && fin;
-                        TrackletHdr& H = L.tl[t];
-                        H.x = SBEST(0);
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) H.p[i] = SBEST(1 + i);
-                        H.p[0] += yref;
-                        H.p[1] += zref;
-#pragma unroll
-                        for (int i = 0; i < 15; ++i) H.C[i] = SBEST(6 + i);
-                        H.chi2 = chi2;
-                        H.nhits = nupd;
-                        H.first = first;
-                        H.last = last;
-                        H.ndf = 2 * nupd - 5;
-                        H.valid = valid ? 1 : 0;
-                        if (valid) {
-                            ++my_valid;
-                            my_hits += nupd;
-                        }
-                        t = -1;
-                    }
-                }
-                // (C) the next row is staged and every step of this row done
-                cp_async_wait_all();
-                const bool more = dir > 0 ? fwd_on : (bwd_wait || bwd_on);
-                if (!__syncthreads_or(more ? 1 : 0)) break;
-                r = rn;
-                if (r < 0 || r >= L.R) break;  // (a pass ends at the last row)
-            }
-        }
-    }
-#undef SBEST
-#undef SPL
-    __shared__ int red[2];
-    if (threadIdx.x == 0) red[0] = red[1] = 0;
-    __syncthreads();
-    if (my_valid) atomicAdd(&red[0], my_valid);
-    if (my_hits) atomicAdd(&red[1], my_hits);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (red[0]) atomicAdd(&L.cnt->n_valid, red[0]);
-        if (red[1]) atomicAdd(&L.cnt->n_tracklet_hits, red[1]);
-    }
-}
-
 }  // namespace
 
 int constructor_occupancy()
 {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_constructor, kTlThreads, 0);
-    return per_sm < 1 ? 1 : per_sm;
-}
-
-int sweep_occupancy()
-{
-    cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem());
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep, kSwThreads, sweep_smem());
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_constructor<1>, kTlThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_constructor<2>, kTlThreads, 0);
+    const int per_sm = a < b ? a : b;
     return per_sm < 1 ? 1 : per_sm;
 }
 
@@ -908,21 +547,21 @@ void launch_constructor(const Launch& L, const Schedule& S, void* stream_, const
         k_chains<<<(int)cb, kChThreads, 0, stream>>>(L);
         hook_after(hook, "k_chains");
     }
-    if (S.tl_mode == 1) {
-        int sb = (S.sw_max_per_sm > 0 ? S.sw_max_per_sm : 1) * n_sm;
-        const int chunks = (L.t_cap + kSwThreads - 1) / kSwThreads;
-        if (sb > chunks) sb = chunks;
-        if (sb < 1) sb = 1;
-        k_sweep<<<sb, kSwThreads, sweep_smem(), stream>>>(L);
-        hook_after(hook, "k_constructor");
-    } else {
-        int blocks = per_sm * n_sm;
-        const int need = (L.t_cap + kTlThreads - 1) / kTlThreads;
-        if (blocks > need) blocks = need;
-        if (blocks < 1) blocks = 1;
-        k_constructor<<<blocks, kTlThreads, 0, stream>>>(L);
-        hook_after(hook, "k_constructor");
+    int blocks = per_sm * n_sm;
+    const int need = (L.t_cap + kTlThreads - 1) / kTlThreads;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    k_constructor<1><<<blocks, kTlThreads, 0, stream>>>(L);
+    hook_after(hook, "k_constructor_fwd");
+    {
+        int db = (L.t_cap + 7) / 8;
+        if (db > n_sm * 16) db = n_sm * 16;
+        if (db < 1) db = 1;
+        k_dominance<<<db, 256, 0, stream>>>(L);
+        hook_after(hook, "k_dominance");
     }
+    k_constructor<2><<<blocks, kTlThreads, 0, stream>>>(L);
+    hook_after(hook, "k_constructor_bwd");
     int wblocks = (L.t_cap + 7) / 8;
     if (wblocks > n_sm * 16) wblocks = n_sm * 16;
     if (wblocks < 1) wblocks = 1;

@@ -55,7 +55,8 @@ struct RowGrid {        // y-z bin grid of one (sector,row)
 struct TrackletHdr {
     float x, p[5], C[15], chi2;
     int start;          // global sorted index of the chain start h0
-    int nhits, first, last, ndf, valid, chain_len, pad;
+    int nhits, first, last, ndf, valid, chain_len;
+    int dominated;      // every chain hit taken by other tracklets' forward extensions
 };
 
 // Device counters and status, zeroed before every launch.
@@ -74,7 +75,9 @@ struct Counters {
     int n_track_hits;
     int n_bins;
     int ticket_rows, ticket_hits, ticket_sectors;
-    int tl_next;          // work counter of the persistent constructor
+    int tl_next;          // work counters of the persistent constructor passes
+    int tl_next2;
+    int n_dominated;      // chains whose tracklet is not built (dominated)
     int n_chain_hits;     // hits on the chains of all start hits
     int n_big_rows;       // rows too large for the small row sort
     int n_mg_links;       // merger: links between sector tracks
@@ -82,7 +85,7 @@ struct Counters {
     int n_mg_tracks;      // merger: tracks after merging
     int max_row_hits;     // high-water marks: hits of the fullest (sector, row)
     int max_sector_tracks;  // ... and emitted tracks of the fullest sector
-    int pad[8];
+    int pad[6];
 };
 
 // Merger scratch: a sector track's outer state, and the refit of a chain
@@ -134,6 +137,7 @@ struct Launch {
     int16_t* up; int16_t* dn; int16_t* upc; int16_t* dnc;
     int* upg;                   // [N] cleaned up link, global index or -1
     unsigned long long* weight;
+    unsigned char* mark;        // [N] hit taken by a forward extension search (or null)
     int* starts;                // [t_cap] global sorted index
     TrackletHdr* tl;            // [t_cap]
     int4* tl_chain;             // [t_cap] start hit, its sector << 8 | row, chain end hit, end row
@@ -305,8 +309,6 @@ struct Schedule {
     int nb_threads = 128;      // k_neighbours block (64, 128 or 256)
     int tl_blocks_per_sm = 0;  // persistent k_constructor blocks per SM (<= tl_max_per_sm)
     int tl_max_per_sm = 0;     // occupancy limit of k_constructor
-    int tl_mode = 0;           // 0 persistent lanes, 1 row-synchronous sweep (same results)
-    int sw_max_per_sm = 0;     // occupancy limit of the sweep kernel
     int nb_mode = 0;           // 0 one thread per hit, 1 row blocks with staged rows (same results)
     int nr_max_per_sm = 0;     // occupancy limit of the row-block neighbour kernel
 };
@@ -319,7 +321,6 @@ void prepare_binning();
 void prepare_selector();
 void prepare_merger();
 int constructor_occupancy();
-int sweep_occupancy();
 int neighbour_rows_occupancy();
 
 // host-side launchers (one translation unit each)

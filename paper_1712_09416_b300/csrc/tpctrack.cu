@@ -93,6 +93,7 @@ struct Slot {
     int *hcid, *hrow, *bin_start;
     int16_t *up, *dn, *upc, *dnc;
     unsigned long long* weight;
+    unsigned char* mark;
     int* starts;
     TrackletHdr* tl;
     int4* tl_chain;
@@ -277,6 +278,7 @@ size_t layout(Slot& s, char* base)
     s.upc = (int16_t*)take(2 * k.n);
     s.dnc = (int16_t*)take(2 * k.n);
     s.weight = (unsigned long long*)take(8 * k.n);
+    s.mark = (unsigned char*)take(k.n);
     s.starts = (int*)take(4 * (size_t)k.t);
     s.tl = (TrackletHdr*)take(sizeof(TrackletHdr) * (size_t)k.t);
     s.tl_chain = (int4*)take(16 * (size_t)k.t);
@@ -611,6 +613,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.upc = s.upc;
     L.dnc = s.dnc;
     L.weight = s.weight;
+    L.mark = s.mark;
     L.starts = s.starts;
     L.tl = s.tl;
     L.tl_chain = s.tl_chain;
@@ -730,6 +733,7 @@ void fill_counters(Slot& s)
     K.n_tracks = c.n_tracks;
     K.n_track_hits = c.n_track_hits;
     K.n_chain_hits = c.n_chain_hits;
+    K.n_dominated_chains = c.n_dominated;
     K.n_sector_tracks = c.n_tracks;
     K.max_row_hits = c.max_row_hits;
     K.max_sector_tracks = c.max_sector_tracks;
@@ -817,7 +821,6 @@ void prepare_kernels(Schedule* s)
     prepare_merger();
     s->tl_max_per_sm = constructor_occupancy();
     s->tl_blocks_per_sm = s->tl_max_per_sm;
-    s->sw_max_per_sm = sweep_occupancy();
     s->nr_max_per_sm = neighbour_rows_occupancy();
 }
 
@@ -997,11 +1000,11 @@ int dump(tpc_track_ctx* ctx, Slot& s, int stage, int event, void* buf, size_t ca
             if (ns) CUDA_TRY(ctx, cudaMemcpy(rh_all.data(), s.tl_rowhit, 4 * (size_t)ns * R, cudaMemcpyDeviceToHost));
             int32_t count = 0;
             for (auto& o : order)
-                if (tl[o.second].chain_len >= s.info.L.min_chain) ++count;
+                if (tl[o.second].chain_len >= s.info.L.min_chain && !tl[o.second].dominated) ++count;
             put(&count, 4);
             for (auto& o : order) {
                 const TrackletHdr& H = tl[o.second];
-                if (H.chain_len < s.info.L.min_chain) continue;
+                if (H.chain_len < s.info.L.min_chain || H.dominated) continue;
                 tpc_dump_tracklet D;
                 std::memset(&D, 0, sizeof(D));
                 D.start_cid = o.first;
@@ -1452,7 +1455,6 @@ int tpc_track_get_schedule(const tpc_track_ctx* ctx, tpc_track_schedule* out)
     out->tl_blocks_per_sm = S.tl_blocks_per_sm;
     out->max_streams = (int)ctx->slots.size();
     out->streams = ctx->streams;
-    out->tl_mode = S.tl_mode;
     out->nb_mode = S.nb_mode;
     return TPC_OK;
 }
@@ -1466,8 +1468,7 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* q)
         (q->sort_threads != 256 && q->sort_threads != 512) ||
         (q->nb_threads != 64 && q->nb_threads != 128 && q->nb_threads != 256) ||
         q->tl_blocks_per_sm < 1 || q->tl_blocks_per_sm > S.tl_max_per_sm || q->streams < 1 ||
-        q->streams > (int)ctx->slots.size() || (q->tl_mode != 0 && q->tl_mode != 1) ||
-        (q->nb_mode != 0 && q->nb_mode != 1))
+        q->streams > (int)ctx->slots.size() || (q->nb_mode != 0 && q->nb_mode != 1))
         return fail(ctx, TPC_EINVAL, "schedule value out of range");
     ctx->streams = q->streams;
     ctx->next_slot = 0;
@@ -1475,7 +1476,6 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* q)
     ctx->sched.sort_threads = q->sort_threads;
     ctx->sched.nb_threads = q->nb_threads;
     ctx->sched.tl_blocks_per_sm = q->tl_blocks_per_sm;
-    ctx->sched.tl_mode = q->tl_mode;
     ctx->sched.nb_mode = q->nb_mode;
     return TPC_OK;
 }
@@ -1559,8 +1559,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     std::vector<int> tl = {mx};
     for (int v : {mx * 3 / 4, mx / 2})
         if (v >= 1 && std::find(tl.begin(), tl.end(), v) == tl.end()) tl.push_back(v);
-    int rc = tune(&Schedule::tl_blocks_per_sm, tl, {"k_constructor"});
-    if (!rc) rc = tune(&Schedule::tl_mode, {0, 1}, {"k_constructor"});
+    int rc = tune(&Schedule::tl_blocks_per_sm, tl, {"k_constructor_fwd", "k_constructor_bwd"});
     if (!rc) rc = tune(&Schedule::nb_threads, {64, 128, 256}, {"k_neighbours"});
     if (!rc) rc = tune(&Schedule::nb_mode, {0, 1}, {"k_neighbours"});
     if (!rc) rc = tune(&Schedule::sort_threads, {256, 512}, {"k_rowsort"});

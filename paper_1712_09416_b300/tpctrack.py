@@ -82,6 +82,7 @@ class tpc_track_counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n_clusters", "n_rows_total", "n_bins", "n_links", "n_starts", "n_tracklets",
         "n_valid_tracklets", "n_tracklet_hits", "n_tracks", "n_track_hits", "n_chain_hits",
+        "n_dominated_chains",
         "n_merge_links", "n_merge_chains", "n_sector_tracks", "max_row_hits", "max_sector_tracks")]
 
 
@@ -92,8 +93,7 @@ class tpc_kernel_time(C.Structure):
 class tpc_track_schedule(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("n_sm", "tl_max_per_sm", "bin_blocks_per_sm",
                                        "sort_threads", "nb_threads", "tl_blocks_per_sm",
-                                       "max_streams", "streams", "tl_mode",
-                                       "nb_mode")]
+                                       "max_streams", "streams", "nb_mode")]
 
 
 class tpc_dump_tracklet(C.Structure):

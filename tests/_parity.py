@@ -12,9 +12,11 @@ Bars (the tracker computes in binary32, the oracle in binary64):
 * tracklet hit sets and validity: identical for every tracklet the oracle
   does not flag as a near-tie (a chi2 within the tie width of the cut or of
   the runner-up, |sin phi| near its bound, a stop bound, or a chain through
-  a neighbour near tie); flagged tracklets may differ, and those that do must
-  stay below 0.1% of all tracklets; the hits of the tracklets that differ
-  (on either side) are the taint of the track comparison;
+  a neighbour near tie); flagged tracklets may differ, and so may the
+  dominance of a chain one of whose hits a flagged forward pass took (the
+  chain is then built on one side only); those that differ must stay below
+  0.1% of all tracklets; the hits of the tracklets that differ (on either
+  side) are the taint of the track comparison;
 * parameters at the innermost hit: |dy|, |dz| <= 1e-3 cm; |d sin phi|,
   |d tan lambda| <= 1e-4 (relative to values of order one); q/pT within
   1e-4 relative to max(|q/pT|, 2 (GeV/c)^-1): stiff tracks have |q/pT| near
@@ -173,15 +175,27 @@ def chain_exempt(o, ex, n_rows):
 def compare_tracklets(gt, ot, n_rows, c2_chain=None):
     """Returns a report dict; keys of tracklets are start cids.  c2_chain
     (from chain_exempt) marks starts whose chains pass a neighbour near tie:
-    their tracklets count as flagged, and may be missing or extra."""
+    their tracklets count as flagged, and may be missing or extra.  A chain
+    may also be built on one side only when its dominance (all its hits
+    taken by forward extension searches) can differ: when one of its hits
+    was taken by a forward pass that carries near-tie bits (oracle fwd_mark
+    bit 2), or lies on a flagged tracklet that differs."""
     g_index = {int(c): i for i, c in enumerate(gt["start"])}
     o_index = {int(c): i for i, c in enumerate(ot["t_start"])}
     rep = {"n_oracle": len(o_index), "n_gpu": len(g_index), "flagged": 0, "flagged_diff": [],
            "hitset_mismatch": [], "valid_mismatch": [], "param_scaled": [], "param_abs": [],
            "param_sig": [], "taint": set()}
+    up_c = np.asarray(ot["up_c"])
+    tie_mark = (np.asarray(ot["fwd_mark"]) & 2) != 0 if "fwd_mark" in ot else None
 
     def c2(c):
         return c2_chain is not None and bool(c2_chain[c])
+
+    def chain_of(c):
+        out = [c]
+        while up_c[out[-1]] >= 0 and len(out) < n_rows:
+            out.append(int(up_c[out[-1]]))
+        return out
 
     def taint_g(gi):
         a = gt["rowhit"][gi]
@@ -190,18 +204,6 @@ def compare_tracklets(gt, ot, n_rows, c2_chain=None):
     def taint_o(oi):
         a = ot["t_rowhit"][oi]
         rep["taint"].update(a[a >= 0].tolist())
-    missing = sorted(set(o_index) - set(g_index))
-    extra = sorted(set(g_index) - set(o_index))
-    rep["missing"] = [c for c in missing if not c2(c)]
-    rep["extra"] = [c for c in extra if not c2(c)]
-    for c in missing:
-        if c2(c):
-            rep["flagged_diff"].append(c)
-            taint_o(o_index[c])
-    for c in extra:
-        if c2(c):
-            rep["flagged_diff"].append(c)
-            taint_g(g_index[c])
     for c, oi in o_index.items():
         if c not in g_index:
             continue
@@ -227,6 +229,27 @@ def compare_tracklets(gt, ot, n_rows, c2_chain=None):
             rep["param_abs"].append(d)
             rep["param_sig"].append(sigma_errors(gt["p"][gi], ot["t_p"][oi], ot["t_C"][oi],
                                                  ot["t_chi2"][oi], ot["t_ndf"][oi]))
+    differ_hits = set(rep["taint"])
+
+    def explained(c):
+        if c2(c):
+            return True
+        ch = chain_of(c)
+        if tie_mark is not None and tie_mark[ch].any():
+            return True
+        return bool(differ_hits.intersection(ch))
+    missing = sorted(set(o_index) - set(g_index))
+    extra = sorted(set(g_index) - set(o_index))
+    rep["missing"] = [c for c in missing if not explained(c)]
+    rep["extra"] = [c for c in extra if not explained(c)]
+    for c in missing:
+        if explained(c):
+            rep["flagged_diff"].append(c)
+            taint_o(o_index[c])
+    for c in extra:
+        if explained(c):
+            rep["flagged_diff"].append(c)
+            taint_g(g_index[c])
     rep["param_scaled"] = np.array(rep["param_scaled"]).reshape(-1, 5)
     rep["param_abs"] = np.array(rep["param_abs"]).reshape(-1, 5)
     rep["param_sig"] = np.array(rep["param_sig"]).reshape(-1, 5)

@@ -104,8 +104,10 @@ def oracle_by_sector(ev, orc, sectors=None, workers=None):
         for p, r in zip(parts, outs):
             o[k][p.info["parent_index"]] = cid_map(p, r[k])
     o["c2_tie"] = np.zeros(n, np.int32)
+    o["fwd_mark"] = np.zeros(n, np.int32)
     for p, r in zip(parts, outs):
         o["c2_tie"][p.info["parent_index"]] = r["c2_tie"]
+        o["fwd_mark"][p.info["parent_index"]] = r["fwd_mark"]
     for k in ("t_sector", "t_chain_len", "t_valid", "t_nhits", "t_first_row", "t_last_row",
               "t_flags", "t_ndf", "t_x", "t_p", "t_C", "t_chi2", "k_x", "k_p", "k_C", "k_chi2",
               "k_ndf", "k_sector"):
@@ -117,7 +119,8 @@ def oracle_by_sector(ev, orc, sectors=None, workers=None):
     o["k_hit_cid"] = np.concatenate([cid_map(p, r["k_hit_cid"]) for p, r in zip(parts, outs)])
     o["k_hit_off"] = np.concatenate([[0], np.cumsum(np.concatenate(
         [np.diff(r["k_hit_off"]) for r in outs]))]).astype(np.int32)
-    for k in ("n_tracklets", "n_tracks", "n_track_hits", "n_links", "n_c2_ties", "n_starts"):
+    for k in ("n_tracklets", "n_tracks", "n_track_hits", "n_links", "n_c2_ties", "n_starts",
+              "n_dominated"):
         o[k] = int(sum(r[k] for r in outs))
     return o
 

@@ -209,7 +209,7 @@ def test_schedule_changes_speed_not_results(tp):
         variants = [dict(nb_threads=64), dict(nb_threads=256), dict(sort_threads=256),
                     dict(bin_blocks_per_sm=1), dict(bin_blocks_per_sm=16),
                     dict(tl_blocks_per_sm=1), dict(tl_blocks_per_sm=max(1, s0["tl_max_per_sm"] // 2)),
-                    dict(tl_mode=1), dict(nb_mode=1)]
+                    dict(nb_mode=1)]
         for v in variants:
             tp.tpc_track_set_schedule(t.ctx, **{**s0, **v})
             got = t.batch(evs)
@@ -217,8 +217,7 @@ def test_schedule_changes_speed_not_results(tp):
                 for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
                     assert np.array_equal(getattr(a, f), getattr(b, f)), (v, f)
         for bad in (dict(nb_threads=96), dict(sort_threads=128), dict(bin_blocks_per_sm=0),
-                    dict(tl_blocks_per_sm=s0["tl_max_per_sm"] + 1), dict(tl_mode=2),
-                    dict(nb_mode=-1)):
+                    dict(tl_blocks_per_sm=s0["tl_max_per_sm"] + 1), dict(nb_mode=-1)):
             with pytest.raises(tp.TpcError):
                 tp.tpc_track_set_schedule(t.ctx, **{**s0, **bad})
         g, keep_x = tp.geometry_of(evs[0])
@@ -235,12 +234,11 @@ def test_schedule_changes_speed_not_results(tp):
 
 @pytest.mark.parametrize("which", ["central", "batch", "pileup"])
 def test_kernel_modes_give_identical_results(tp, which):
-    """The row-synchronous constructor and the row-block neighbour finder
-    (both with shared-memory row staging) do the same arithmetic per tracklet
-    and per hit as the persistent-lane constructor and the thread-per-hit
-    finder: every link, tracklet and track is bit-identical, on the central
-    event, a batch of events of uneven multiplicity (many sectors per chunk,
-    global fallback) and the pile-up event (rows above the staging capacity)."""
+    """The row-block neighbour finder (adjacent rows staged in shared memory)
+    does the same arithmetic per hit as the thread-per-hit finder: every
+    link, tracklet and track is bit-identical, on the central event, a batch
+    of events of uneven multiplicity and the pile-up event (rows above the
+    staging capacity read from global memory)."""
     if which == "central":
         evs = [synth.central_event()]
     elif which == "batch":
@@ -252,7 +250,7 @@ def test_kernel_modes_give_identical_results(tp, which):
         s0 = tp.tpc_track_get_schedule(t.ctx)
         res = {}
         for mode in (0, 1):
-            tp.tpc_track_set_schedule(t.ctx, **{**s0, "tl_mode": mode, "nb_mode": mode})
+            tp.tpc_track_set_schedule(t.ctx, **{**s0, "nb_mode": mode})
             trs = t.batch(evs)
             dumps = []
             for k, e in enumerate(evs):

@@ -289,6 +289,52 @@ def _tracks_of(ev, out, particle):
     return res
 
 
+def test_chain_taken_by_a_forward_extension_gets_no_tracklet(orc):
+    """C7a: one missing row cuts a track's links into an inner and an outer
+    chain; the inner chain's forward extension bridges the gap and takes
+    every hit of the outer chain, so the outer chain is dominated (no
+    tracklet) and the track comes out once with all its clusters."""
+    base = _util.isolated_event()
+    full = orc.track_event(base)
+    assert full["n_dominated"] == 0
+    mid = int(np.median(base.row[base.label == 0]))
+    ev = _drop_rows(base, 0, [mid])
+    out = orc.track_event(ev)
+    assert out["n_dominated"] == 1
+    assert out["n_tracklets"] == full["n_tracklets"]
+    tr = _tracks_of(ev, out, 0)
+    assert len(tr) == 1 and tr[0] == set(np.nonzero(ev.label == 0)[0].tolist())
+    # the surviving tracklet of particle 0 starts on its inner chain
+    t0 = [t for t in range(out["n_tracklets"]) if ev.label[out["t_start"][t]] == 0]
+    assert len(t0) == 1 and ev.row[out["t_start"][t0[0]]] < mid
+
+
+def test_dominance_removes_tracklets_not_tracks(orc):
+    """C7a on a central-event sector: the dominated chains are redundant (their
+    clusters end up on emitted tracks nearly always) and the efficiency stays
+    that of a sector tracker (pT > 0.2 GeV/c segments of >= 30 clusters found
+    with >= 99%); the rule removes about half of the chains' tracklets."""
+    ev = synth.central_event().select_sectors([7])
+    o = orc.track_event(ev)
+    s = _util.mc_summary(ev, o)
+    assert s["eff_pt02"] >= 0.99, s
+    up_c, dn_c = o["up_c"], o["dn_c"]
+    built = set(o["t_start"].tolist())
+    on_track = np.zeros(ev.n, bool)
+    on_track[o["k_hit_cid"]] = True
+    n_dom = n_covered = 0
+    for st in np.nonzero((up_c >= 0) & (dn_c < 0))[0]:
+        c = [int(st)]
+        while up_c[c[-1]] >= 0:
+            c.append(int(up_c[c[-1]]))
+        if len(c) < 3 or st in built:
+            continue
+        n_dom += 1
+        n_covered += bool(on_track[c].all())
+    assert n_dom == o["n_dominated"] and n_dom > 0.4 * (n_dom + o["n_tracklets"])
+    assert n_covered >= 0.95 * n_dom, (n_covered, n_dom)
+
+
 def test_gap_of_max_gap_minus_one_rows_is_bridged(orc):
     """Four consecutive empty rows: the search steps over them (max_gap = 5)."""
     base = _util.isolated_event()

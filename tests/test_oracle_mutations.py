@@ -61,6 +61,13 @@ MUTATIONS = {
     "cleaner: up link kept without the partner's down link": (
         "        res->up_c[i] = (u >= 0 && res->dn[u] == (int32_t)i) ? u : -1;",
         "        res->up_c[i] = u;"),
+    # the dominance rule (pin: a track cut by one missing row comes out whole, once)
+    "dominance: marks also from the tracklet's own chain": (
+        "        for (int r = F[i].rk + 1; r <= F[i].last; ++r)",
+        "        for (int r = F[i].r0; r <= F[i].last; ++r)"),
+    "dominance: one marked hit is enough": (
+        "        for (int64_t q = ch_off[i]; q < ch_off[i + 1]; ++q) all = all && marked[ch_hits[q]];",
+        "        all = 0; for (int64_t q = ch_off[i]; q < ch_off[i + 1]; ++q) all = all || marked[ch_hits[q]];"),
 }
 
 
@@ -173,6 +180,13 @@ def prior_ok(orc):
                for s0, tt in ((0.0, 0.0), (0.25, 0.5), (-0.4, -0.9), (0.6, 0.1)))
 
 
+def dominance_ok(orc):
+    from tests import test_oracle_event as t
+    return passes(t.test_chain_taken_by_a_forward_extension_gets_no_tracklet, orc) and \
+        passes(t.test_isolated_tracks_one_track_each_with_all_clusters, orc) and \
+        passes(t.test_dominance_removes_tracklets_not_tracks, orc)
+
+
 def golden_ok(orc):
     from tests import test_oracle_event as t
     return passes(t.test_golden_neighbours, orc)
@@ -195,7 +209,9 @@ PINS = {"rotation turned the wrong way": closed_form_ok, "sign of ds'/dy": jacob
         "neighbours: ties to the higher cid(u)": golden_ok,
         "neighbours: pair near-tie bit lost": golden_ok,
         "neighbours: window near-tie bit lost": golden_ok,
-        "cleaner: up link kept without the partner's down link": golden_ok}
+        "cleaner: up link kept without the partner's down link": golden_ok,
+        "dominance: marks also from the tracklet's own chain": dominance_ok,
+        "dominance: one marked hit is enough": dominance_ok}
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
