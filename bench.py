@@ -1055,15 +1055,18 @@ def run_ours(args):
         # at once: each event's host inputs are copied in and its tracks copied
         # out inside the timed region, overlapped across slots
         ctx_s = served_ctx(tp, [hc], geom, bz, n)
-        barrier()
-        t0 = time.perf_counter()
-        tks = [tp.tpc_track_submit(ctx_s, hc, geom, bz) for _ in range(k_e2e)]
-        for t in tks:
-            if tp.tpc_track_poll(ctx_s, t, 60_000_000, copy=False) is None:
-                raise TimeoutError("served ticket not done after 60 s")
-            tp.tpc_track_release(ctx_s, t)
-        barrier()
-        srv_s = time.perf_counter() - t0
+        srv_runs = []
+        for _ in range(3):  # three timed bursts; the median is the figure
+            barrier()
+            t0 = time.perf_counter()
+            tks = [tp.tpc_track_submit(ctx_s, hc, geom, bz) for _ in range(k_e2e)]
+            for t in tks:
+                if tp.tpc_track_poll(ctx_s, t, 60_000_000, copy=False) is None:
+                    raise TimeoutError("served ticket not done after 60 s")
+                tp.tpc_track_release(ctx_s, t)
+            barrier()
+            srv_runs.append(time.perf_counter() - t0)
+        srv_s = sorted(srv_runs)[1]
         tp.tpc_track_destroy(ctx_s)
         h2d = 12 * n + 4096
         d2h = 256 + n_tr * (4 + 4 + 20 + 60 + 4 + 4 + 4) + 4 * n_hits + 4 * 37
@@ -1071,6 +1074,7 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h, "steps": k_e2e,
                "api": f"tpc_track_submit/poll, {SERVED_SLOTS} slots x {SERVED_PER_LAUNCH} events, "
                       "pinned host inputs, results read from pinned buffers",
+               "runs_clusters_per_s": [world * n * k_e2e / x for x in srv_runs],
                "one_event_calls": {"value": world * n * k_e2e / seq_s, "unit": UNIT,
                                    "api": "tpc_track_event, one call per event"}}
 

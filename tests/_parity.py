@@ -34,8 +34,8 @@ Bars (the tracker computes in binary32, the oracle in binary64):
   units of each parameter's own statistical error the binary32 deviations
   stay below 1e-2.  The share of tracks within the plain bars (q/pT 1e-4
   relative with no floor) is reported beside these;
-* tracks: identical hit lists and order for every track that shares no hit
-  with a tracklet that differs.
+* tracks: identical hit lists and order for every track whose tracklet
+  shares no hit with a tracklet that differs.
 """
 import numpy as np
 
@@ -287,7 +287,16 @@ def compare_tracks(gtr, ot, taint):
 
     def clean(h):
         return not (set(h) & taint)
-    o_clean = [h for h, _ in o_tracks if clean(h)]
+
+    # an oracle track whose tracklet holds a tainted hit it does not own may
+    # differ too (the hit's owner differs, so the track may keep it on one
+    # side only): test the tracklet's whole hit set when it is known
+    def clean_o(h, j):
+        if "k_tracklet" in ot and "t_rowhit" in ot:
+            rh = ot["t_rowhit"][ot["k_tracklet"][j]]
+            return clean(h) and not (set(rh[rh >= 0].tolist()) & taint)
+        return clean(h)
+    o_clean = [h for h, j in o_tracks if clean_o(h, j)]
     g_clean = [h for h, _ in g_tracks if clean(h)]
     rep = {"n_oracle": len(o_tracks), "n_gpu": len(g_tracks), "compared": 0,
            "missing": [h for h in o_clean if h not in g_set],
