@@ -925,7 +925,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     # four slots: the autotuner may spread consecutive steps over up to four
     # streams, so that one event's kernels overlap the next one's
-    ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, max_events_in_flight=4,
+    ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, max_events_in_flight=8,
                               cuda_stream=stream.cuda_stream)
     # launch schedule picked by the autotuner on this workload (untimed)
     if args.no_autotune:

@@ -370,8 +370,8 @@ int tpc_track_set_schedule(tpc_track_ctx* ctx, const tpc_track_schedule* s);
  * times each (1..50), times the kernel that the field shapes with CUDA
  * events, and keeps the fastest value per field (fields shape different
  * kernels, so they are tuned one after the other).  Last it times rounds
- * (at least 7) of 8K back-to-back launches spread over K = 1 .. min(4,
- * max_streams) streams
+ * (at least 7) of 8K back-to-back launches spread over K = 1, 2, 3, 4, 6, 8
+ * streams (up to max_streams)
  * (from the context's stream to tpc_track_join), for K > 1 with each of the
  * constructor block counts tried before (launches running together share the
  * SMs), and takes the pair with the shortest time per launch (a larger K

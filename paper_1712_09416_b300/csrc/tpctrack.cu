@@ -1571,7 +1571,10 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     // constructor block counts above (concurrent launches share the SMs, so
     // the best count alone need not be the best together); a larger K must
     // win by 1% to be taken
-    const int kmax = std::min(4, (int)ctx->slots.size());
+    const int kmax = std::min(8, (int)ctx->slots.size());
+    std::vector<int> ks;
+    for (int K : {1, 2, 3, 4, 6, 8})
+        if (K <= kmax) ks.push_back(K);
     if (kmax > 1) {
         const Schedule tuned = ctx->sched;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1579,7 +1582,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
         CUDA_TRY(ctx, cudaEventCreate(&e1));
         double best_per = 1e30;
         int best_k = 1, best_tl = tuned.tl_blocks_per_sm;
-        for (int K = 1; K <= kmax && rc == TPC_OK; ++K)
+        for (int K : ks)
         for (int tlv : (K == 1 ? std::vector<int>{tuned.tl_blocks_per_sm} : tl)) {
             if (rc != TPC_OK) break;
             ctx->streams = K;

@@ -31,6 +31,14 @@ def trk(tp):
     t.close()
 
 
+# The merger's near-tie width on its match chi2 (1.0) covers the chi2 change
+# 2 sqrt(chi2) (m_a + m_b) that deviations of Mahalanobis size m_a, m_b of the
+# two sector tracks' states make at the cut (chi2 <= 31): m up to
+# 1.0 / (4 sqrt(31)) = 0.045.  The whole-event comparisons report how many
+# compared tracks exceed it.
+MERGE_TIE_M = 0.045
+
+
 def run(tp, trk, ev):
     tr = trk.event(ev)
     return dict(_util.gpu_stages(tp, trk.ctx, ev), tracks=tr, counters=trk.counters())
@@ -59,7 +67,9 @@ def check_event(tp, trk, ev, orc, *, o=None, max_diff_frac=1e-3, what="event"):
           f"{rep['n_oracle']} tracklets ({len(rep['flagged_diff'])} flagged ones differ), "
           f"{trep['n_oracle']} tracks, compared {trep['compared_share']:.4f}, "
           f"within the plain bars {trep['plain_share']:.4f}, Mahalanobis deviation max "
-          f"{trep['maha'].max() if len(trep['maha']) else 0.0:.2e}")
+          f"{trep['maha'].max() if len(trep['maha']) else 0.0:.2e}, p99.9 "
+          f"{np.quantile(trep['maha'], 0.999) if len(trep['maha']) else 0.0:.2e}, above "
+          f"{MERGE_TIE_M}: {int((trep['maha'] > MERGE_TIE_M).sum())}")
     return g, o, rep, trep
 
 
@@ -104,6 +114,7 @@ def test_central_event_whole(tp, orc):
         g, o, rep, trep = check_event(tp, t, ev, orc, o=_util.oracle_by_sector(ev, orc),
                                       what="central event")
     assert trep["compared_share"] >= 0.95, trep["compared_share"]
+    assert (trep["maha"] > MERGE_TIE_M).sum() <= np.ceil(1e-3 * len(trep["maha"]))
 
 
 def test_pileup_event_whole(tp, orc):
@@ -117,6 +128,7 @@ def test_pileup_event_whole(tp, orc):
                                       what="pile-up event")
     assert g["counters"]["n_clusters"] == ev.n
     assert trep["compared_share"] >= 0.90, trep["compared_share"]
+    assert (trep["maha"] > MERGE_TIE_M).sum() <= np.ceil(1e-3 * len(trep["maha"]))
     mg = _util.mc_summary(ev, g["tracks"])
     mo = _util.mc_summary(ev, o)
     tol = len(rep["taint"]) + 2
