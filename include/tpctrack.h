@@ -150,20 +150,28 @@ typedef struct tpc_track_ctx tpc_track_ctx;
 void tpc_track_default_params(tpc_track_params* p);
 
 /* Create a context: allocates every device arena up front (no allocation
- * happens on the tracking path).  Returns TPC_EINVAL for a bad config,
+ * happens on the tracking path).  Passage: the tracker is one component
+ * instance of the chain that processes one event after another (Sect. 2);
+ * the context is that instance's state on one GPU.  Returns TPC_EINVAL for a bad config,
  * TPC_ENOMEM if the arenas do not fit the device or mem_budget, TPC_ECUDA
  * for other CUDA failures.  *out is NULL on failure. */
 int tpc_track_create(const tpc_track_config* cfg, tpc_track_ctx** out);
 
 /* Track one event: stage inputs (host->device copy unless on_device), run
- * the device pipeline, copy the tracks back.  Blocks until done.  Inputs are
+ * the device pipeline, copy the tracks back.  Blocks until done.  Passage:
+ * the tracker takes the clusters of all TPC links of one event (Sect. 2) and
+ * finds tracks with a cellular automaton and fits them with a Kalman filter
+ * (Abstract); the call wraps the device launch the way FitTracks() wraps
+ * FitTracksGPU (Sect. 4.1, Listings 2-3).  Inputs are
  * checked on the device before any result is produced: an invalid cluster
  * gives TPC_EINVAL, an overflow TPC_ECAPACITY; in both cases out->n_tracks = 0. */
 int tpc_track_event(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geometry* geom,
                     float bz_tesla, tpc_tracks* out);
 
 /* Track n_ev events in one device pass (sectors of all events side by side,
- * one launch per stage).  outs[i] receives event i.  The cluster counts
+ * one launch per stage).  Passage: many events are in flight in the chain at
+ * once (Sect. 2) and different kernels run concurrently (Sect. 4.2, last
+ * paragraph); a batch fills the GPU with the work of many events.  outs[i] receives event i.  The cluster counts
  * summed over the batch must not exceed max_clusters_per_event.  Each
  * event's tracks are identical to those of tpc_track_event on it alone. */
 int tpc_track_batch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
@@ -195,7 +203,10 @@ int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs);
  * runs after those launches. */
 int tpc_track_join(tpc_track_ctx* ctx);
 
-/* Served form: queue one event.  Every slot (a device arena, all of them
+/* Served form: queue one event.  Passage: events arrive one after another
+ * and a component must keep up without its input queue filling (Sect. 2,
+ * Sect. 3 item 4, Fig. 4); continuous batching over slots keeps several
+ * events in flight.  Every slot (a device arena, all of them
  * allocated at creation within mem_budget) has a worker thread that takes
  * the queued events, as many as fit the slot, into its next launch;
  * launches on different slots overlap on the device.  The caller's input
@@ -207,11 +218,15 @@ int tpc_track_submit(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geome
                      float bz_tesla, uint64_t* ticket);
 
 /* Wait up to timeout_us (0 = just test, < 0 = forever) for a ticket.
+ * Passage: the consumer checks for finished work at each event without
+ * waiting (Sect. 5.1, the asynchronous pattern of Fig. 5).
  * TPC_OK fills *out (valid until tpc_track_release); TPC_EBUSY if not done;
  * the ticket's own error code if its launch failed. */
 int tpc_track_poll(tpc_track_ctx* ctx, uint64_t ticket, int timeout_us, tpc_tracks* out);
 
-/* Free the host memory of a finished ticket. */
+/* Free the host memory of a finished ticket (the ticket's results are the
+ * tracks handed on to calibration, Sect. 3; the caller keeps them until this
+ * call). */
 int tpc_track_release(tpc_track_ctx* ctx, uint64_t ticket);
 
 /* Event-synchronous parameter updates (Sect. 3, item 2; Sect. 5.2, 5.3: new
@@ -384,7 +399,10 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
                        tpc_track_schedule* out);
 
 /* Debug dump of an intermediate stage of event 0 of the last completed
- * launch, for parity tests.  Writes at most cap bytes to host_buf and the
+ * launch, for parity tests.  Passage: the paper checks its device code by
+ * running the same algorithm on the CPU and comparing (one common source
+ * for CPU and GPU, Sect. 4.1); here every stage is compared with the
+ * independent CPU oracle.  Writes at most cap bytes to host_buf and the
  * size needed to *used (call with cap = 0 to query).  Stages:
  *   TPC_DUMP_LINKS      int32 [2][n]: up, down link as cid (or -1), by cid
  *   TPC_DUMP_CLEAN      int32 [2][n]: links after cleaning, by cid
