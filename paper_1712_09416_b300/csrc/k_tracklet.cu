@@ -208,14 +208,8 @@ __global__ void __launch_bounds__(kChThreads) k_chains(Launch L)
 // extension search takes and leaves the forward state at the last hit in the
 // header; PASS 2 (after k_dominance) runs the backward passes (assigned hits,
 // then search below the chain) of the chains that were not dominated.
-//
-// A pass runs in rounds: in round 0 the lanes take the start hits; a
-// tracklet still in its pass after `budget` row steps is saved (TlState) and
-// listed for the next round, whose lanes take the listed tracklets densely
-// (budget 0: no limit, the last round).  Lanes whose tracklets end early in a
-// round idle for at most `budget` steps instead of for the rest of the pass.
 template <int PASS>
-__global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L, int round, int budget)
+__global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
 {
     if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     __shared__ float best_s[21][kTlThreads];  // state + covariance at the innermost backward hit
@@ -225,15 +219,9 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L, int round,
     __syncthreads();
 #define BEST(i) best_s[i][threadIdx.x]
 #define PL(i) pl_s[i][threadIdx.x]
-    const int slot = (PASS - 1) * kMaxRounds + round;
-    // round 0 takes the start hits, a later round the previous round's list
-    const int n_st = round == 0 ? min(L.cnt->n_starts, L.t_cap)
-                                : min(L.cnt->tl_round_n[slot - 1], L.t_cap);
-    const int* list_in = L.tl_list + (size_t)((round + 1) & 1) * L.t_cap;
-    int* list_out = L.tl_list + (size_t)(round & 1) * L.t_cap;
+    const int n_st = min(L.cnt->n_starts, L.t_cap);
     const int lane = threadIdx.x & 31;
     int t = -1;
-    int steps = 0;  // row steps of the current tracklet in this round
     int phase = 0;  // 1 forward, 2 backward
     int r = 0, r0 = 0, rk = 0, last = 0, first = 0, gap = 0, nupd = 0, gbase = 0;
     float chi2 = 0.0f;
@@ -282,13 +270,14 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L, int round,
             // warp-aggregated fetch of the next start hits
             const int leader = __ffs(m) - 1;
             int b = 0;
-            if (lane == leader) b = atomicAdd(&L.cnt->tl_fetch[slot], __popc(m));
+            if (lane == leader) b = atomicAdd(PASS == 1 ? &L.cnt->tl_next : &L.cnt->tl_next2, __popc(m));
             b = __shfl_sync(0xffffffffu, b, leader);
             if (need) {
-                const int item = b + __popc(m & ((1u << lane) - 1));
-                t = item < n_st ? (round == 0 ? item : list_in[item]) : -1;
-                exhausted = t < 0;
-                steps = 0;
+                t = b + __popc(m & ((1u << lane) - 1));
+                if (t >= n_st) {
+                    t = -1;
+                    exhausted = true;
+                }
             }
         }
         if (!__any_sync(0xffffffffu, t >= 0)) {
@@ -296,40 +285,6 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L, int round,
             continue;
         }
         if (t < 0) continue;
-        if (phase == 0 && round > 0) {
-            // a tracklet carried over from the previous round: its pass state
-            const int4 ch = L.tl_chain[t];
-            gbase = (ch.y >> 8) * L.R;
-            r0 = ch.y & 255;
-            rk = ch.w;
-            rowhit = L.tl_rowhit + (size_t)t * L.R;
-            const float2 c0 = L.hyz[ch.x];
-            yref = c0.x;
-            zref = c0.y;
-            const TlState& S = L.tl_state[t];
-            f.x = S.x;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) f.p[i] = S.p[i];
-#pragma unroll
-            for (int i = 0; i < 15; ++i) f.C[i] = S.C[i];
-            chi2 = S.chi2;
-            r = S.r;
-            last = S.last;
-            first = S.first;
-            gap = S.gap;
-            nupd = S.nupd;
-            if (PASS == 1) {
-#pragma unroll
-                for (int i = 0; i < 5; ++i) PL(i) = S.pl[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 21; ++i) BEST(i) = S.best[i];
-            }
-            phase = PASS;
-            const bool kn = PASS == 1 ? r <= rk : r >= r0;
-            ph2 = kn ? rowhit[r] : -1;
-            stage(r, PASS == 1);
-        }
         if (phase == 0) {
             // the chain, followed by k_chains: start hit, row, end hit, end row
             const int4 ch = L.tl_chain[t];
@@ -453,42 +408,8 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L, int round,
                     r = rn;
                 }
             }
-            if (fwd ? r >= L.R : r < 0) end_pass = true;
         }
-        if (!end_pass) {
-            if (budget > 0 && ++steps >= budget) {
-                // the round's budget is spent: save the pass state and list
-                // the tracklet for the next round
-                TlState& S = L.tl_state[t];
-                S.x = f.x;
-#pragma unroll
-                for (int i = 0; i < 5; ++i) S.p[i] = f.p[i];
-#pragma unroll
-                for (int i = 0; i < 15; ++i) S.C[i] = f.C[i];
-                S.chi2 = chi2;
-                S.r = r;
-                S.last = last;
-                S.first = first;
-                S.gap = gap;
-                S.nupd = nupd;
-                if (PASS == 1) {
-#pragma unroll
-                    for (int i = 0; i < 5; ++i) S.pl[i] = PL(i);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 21; ++i) S.best[i] = BEST(i);
-                }
-                const unsigned mm = __activemask();
-                const int leader = __ffs(mm) - 1;
-                int b = 0;
-                if (lane == leader) b = atomicAdd(&L.cnt->tl_round_n[slot], __popc(mm));
-                b = __shfl_sync(mm, b, leader);
-                list_out[b + __popc(mm & ((1u << lane) - 1))] = t;
-                t = -1;
-                phase = 0;
-            }
-            continue;
-        }
+        if (!end_pass) continue;
         if (fwd) {
             // forward pass done: the state at the last hit (relative to the
             // start hit) and the last row wait in the header for PASS 2
@@ -630,13 +551,7 @@ void launch_constructor(const Launch& L, const Schedule& S, void* stream_, const
     const int need = (L.t_cap + kTlThreads - 1) / kTlThreads;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    // rounds of kRoundSteps row steps (a pass has at most R - 1), the last
-    // one without a limit
-    int rounds = (L.R - 1 + kRoundSteps - 1) / kRoundSteps;
-    if (rounds < 1) rounds = 1;
-    if (rounds > kMaxRounds) rounds = kMaxRounds;
-    for (int rd = 0; rd < rounds; ++rd)
-        k_constructor<1><<<blocks, kTlThreads, 0, stream>>>(L, rd, rd + 1 < rounds ? kRoundSteps : 0);
+    k_constructor<1><<<blocks, kTlThreads, 0, stream>>>(L);
     hook_after(hook, "k_constructor_fwd");
     {
         int db = (L.t_cap + 7) / 8;
@@ -645,8 +560,7 @@ void launch_constructor(const Launch& L, const Schedule& S, void* stream_, const
         k_dominance<<<db, 256, 0, stream>>>(L);
         hook_after(hook, "k_dominance");
     }
-    for (int rd = 0; rd < rounds; ++rd)
-        k_constructor<2><<<blocks, kTlThreads, 0, stream>>>(L, rd, rd + 1 < rounds ? kRoundSteps : 0);
+    k_constructor<2><<<blocks, kTlThreads, 0, stream>>>(L);
     hook_after(hook, "k_constructor_bwd");
     int wblocks = (L.t_cap + 7) / 8;
     if (wblocks > n_sm * 16) wblocks = n_sm * 16;

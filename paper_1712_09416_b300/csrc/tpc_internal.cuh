@@ -35,11 +35,6 @@ constexpr int kHitTile = 2048;   // sorted hits per look-back tile of k_clean_st
 // Row counters one per 32-byte sector: the clusters of an event hit a few
 // thousand counters with atomics, and counters sharing a sector serialise.
 constexpr int kCntPad = 8;
-// The constructor runs each pass in rounds of at most kRoundSteps row steps
-// per tracklet; the tracklets a round leaves unfinished are saved and packed
-// densely into the next round, so that the lanes of a warp stay busy.
-constexpr int kRoundSteps = 32;
-constexpr int kMaxRounds = 9;   // rows / kRoundSteps rounds, the last one unbounded
 
 struct EventDesc {
     const float* y;
@@ -55,14 +50,6 @@ struct EventDesc {
 struct RowGrid {        // y-z bin grid of one (sector,row)
     float y0, z0, idy, idz;
     int ny, nz, bin_off, pad;
-};
-
-// A tracklet's pass state between constructor rounds.
-struct TlState {
-    float x, p[5], C[15], chi2;
-    float best[21];     // backward: state and covariance after the last update
-    float pl[5];        // forward: state after the last update
-    int r, last, first, gap, nupd, pad[3];
 };
 
 struct TrackletHdr {
@@ -91,8 +78,6 @@ struct Counters {
     int tl_next;          // work counters of the persistent constructor passes
     int tl_next2;
     int n_dominated;      // chains whose tracklet is not built (dominated)
-    int tl_fetch[2 * kMaxRounds];   // constructor rounds: work counter of (pass, round)
-    int tl_round_n[2 * kMaxRounds]; // ... and tracklets left unfinished by it
     int n_chain_hits;     // hits on the chains of all start hits
     int n_big_rows;       // rows too large for the small row sort
     int n_mg_links;       // merger: links between sector tracks
@@ -156,8 +141,6 @@ struct Launch {
     int* starts;                // [t_cap] global sorted index
     TrackletHdr* tl;            // [t_cap]
     int4* tl_chain;             // [t_cap] start hit, its sector << 8 | row, chain end hit, end row
-    TlState* tl_state;          // [t_cap] pass state of tracklets carried to the next round
-    int* tl_list;               // [2 * t_cap] tracklets of the next round (two lists, alternating)
     int* tl_rowhit;             // [t_cap * R] global hit index or -1
     unsigned long long* tl_key; // [t_cap] sector-local sort key or ~0
     int* tl_nown;               // [t_cap]

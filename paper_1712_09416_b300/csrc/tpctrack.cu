@@ -97,8 +97,6 @@ struct Slot {
     int* starts;
     TrackletHdr* tl;
     int4* tl_chain;
-    TlState* tl_state;
-    int* tl_list;
     int* tl_rowhit;
     int* upg;
     unsigned long long* tl_key;
@@ -284,8 +282,6 @@ size_t layout(Slot& s, char* base)
     s.starts = (int*)take(4 * (size_t)k.t);
     s.tl = (TrackletHdr*)take(sizeof(TrackletHdr) * (size_t)k.t);
     s.tl_chain = (int4*)take(16 * (size_t)k.t);
-    s.tl_state = (TlState*)take(sizeof(TlState) * (size_t)k.t);
-    s.tl_list = (int*)take(8 * (size_t)k.t);
     s.tl_rowhit = (int*)take(4 * (size_t)k.t * k.r);
     s.upg = (int*)take(4 * k.n);
     s.tl_key = (unsigned long long*)take(8 * (size_t)k.t);
@@ -621,8 +617,6 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.starts = s.starts;
     L.tl = s.tl;
     L.tl_chain = s.tl_chain;
-    L.tl_state = s.tl_state;
-    L.tl_list = s.tl_list;
     L.tl_rowhit = s.tl_rowhit;
     L.upg = s.upg;
     L.tl_key = s.tl_key;
