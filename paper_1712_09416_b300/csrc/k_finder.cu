@@ -32,83 +32,32 @@ struct RowView {      // one adjacent row
     RowGrid G;
 };
 
-// Admissible candidates of one side, kept in registers (at most kList); the
-// insert is a chain of predicated moves so that the list never spills.
-constexpr int kList = 4;
-struct CandList {
-    float sy[kList], sz[kList];
-    int cid[kList], k[kList];
-    int n;
+// The candidates of one side lie in the window's y-z bins: for each z-bin
+// from z0 to z1 the sorted hits [bins[bz*ny + y0], bins[bz*ny + y1 + 1]).
+// BinWalk enumerates them bin after bin, four indices at a time, so that the
+// loads of a batch are issued together.
+struct BinWalk {
+    int bz, z1, k, kb;
 };
 
-__device__ __forceinline__ void push(CandList& c, float sy, float sz, int k)
+__device__ __forceinline__ void walk_open(const RowView& V, int y0, int y1, int z0, int z1,
+                                          BinWalk& w)
 {
-#pragma unroll
-    for (int j = 0; j < kList; ++j) {
-        if (c.n == j) {
-            c.sy[j] = sy;
-            c.sz[j] = sz;
-            c.k[j] = k;
-        }
-    }
-    ++c.n;
+    w.bz = z0;
+    w.z1 = z1;
+    w.k = V.bins[z0 * V.G.ny + y0];
+    w.kb = V.bins[z0 * V.G.ny + y1 + 1];
 }
 
-// Scan one side's window: admissible candidates and their slopes.  up = true
-// gives slopes (c - h) * inv, up = false gives (h - c) * inv.  The hit ranges
-// of the window's z-bins (up to four) are walked as one flat index space so
-// that lanes with different bin counts stay together, four candidates per
-// step with their loads issued together; the cids of the kept candidates are
-// read at the end.
-__device__ __forceinline__ void collect(const RowView& V, float yh, float zh, float inv, float wy,
-                                       float wz, bool up, CandList& c)
+// next candidate index, or -1 when the window is exhausted
+__device__ __forceinline__ int walk_next(const RowView& V, int y0, int y1, BinWalk& w)
 {
-    const float my = 1e-3f * (1.0f + fabsf(yh)), mz = 1e-3f * (1.0f + fabsf(zh));
-    const int y0 = bin_y(V.G, yh - wy - my), y1 = bin_y(V.G, yh + wy + my);
-    const int z0 = bin_z(V.G, zh - wz - mz), z1 = bin_z(V.G, zh + wz + mz);
-    c.n = 0;
-    auto test = [&](int k, float2 v) {
-        const float ddy = up ? __fsub_rn(v.x, yh) : __fsub_rn(yh, v.x);
-        const float ddz = up ? __fsub_rn(v.y, zh) : __fsub_rn(zh, v.y);
-        if (fabsf(ddy) <= wy && fabsf(ddz) <= wz)
-            push(c, __fmul_rn(ddy, inv), __fmul_rn(ddz, inv), k);
-    };
-    if (z1 - z0 < 4) {
-        int a[4], n[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int bz = z0 + j;
-            a[j] = 0;
-            n[j] = 0;
-            if (bz <= z1) {
-                a[j] = V.bins[bz * V.G.ny + y0];
-                n[j] = V.bins[bz * V.G.ny + y1 + 1] - a[j];
-            }
-        }
-        const int c1 = n[0], c2 = c1 + n[1], c3 = c2 + n[2], tot = c3 + n[3];
-        for (int q = 0; q < tot; q += 4) {
-            int kk[4];
-            float2 v[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int qj = q + j < tot ? q + j : q;
-                kk[j] = qj < c1 ? a[0] + qj : qj < c2 ? a[1] + (qj - c1)
-                                          : qj < c3 ? a[2] + (qj - c2) : a[3] + (qj - c3);
-                v[j] = V.yz[kk[j]];
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (q + j < tot) test(kk[j], v[j]);
-        }
-    } else {
-        for (int bz = z0; bz <= z1; ++bz) {
-            const int ka = V.bins[bz * V.G.ny + y0], kb = V.bins[bz * V.G.ny + y1 + 1];
-            for (int k = ka; k < kb; ++k) test(k, V.yz[k]);
-        }
+    while (w.k >= w.kb) {
+        if (++w.bz > w.z1) return -1;
+        w.k = V.bins[w.bz * V.G.ny + y0];
+        w.kb = V.bins[w.bz * V.G.ny + y1 + 1];
     }
-#pragma unroll
-    for (int j = 0; j < kList; ++j)
-        if (j < c.n) c.cid[j] = V.cid[c.k[j]];
+    return w.k++;
 }
 
 __device__ __forceinline__ void consider(float syu, float szu, int cu, int ku, float syd, float szd,
@@ -127,62 +76,95 @@ __device__ __forceinline__ void consider(float syu, float szu, int cu, int ku, f
     }
 }
 
+// Admissible up candidates are gathered in registers in chunks of up to
+// kUpChunk (slopes, cid, index; batches of four loads until the chunk holds
+// more than kUpChunk - 4); for each chunk every down candidate is streamed
+// from the bins and scored against the whole chunk.  Any number of
+// candidates on either side takes this path (a further chunk re-streams the
+// down side).
+constexpr int kUpChunk = 8;
+
 // Best (down, up) pair of hit (yh, zh): least D over all admissible pairs.
 __device__ __forceinline__ void best_pair(const RowView& U, const RowView& D, float yh, float zh,
                                           float iu, float id, float wyu, float wzu, float wyd,
                                           float wzd, float& bestD, int& bcu, int& bcd, int& biu,
                                           int& bid)
 {
-    CandList cu, cd;
-    collect(U, yh, zh, iu, wyu, wzu, true, cu);
-    collect(D, yh, zh, id, wyd, wzd, false, cd);
-    if (cu.n <= kList && cd.n <= kList) {
-#pragma unroll
-        for (int a = 0; a < kList; ++a) {
-            if (a >= cu.n) break;
-#pragma unroll
-            for (int b = 0; b < kList; ++b) {
-                if (b >= cd.n) break;
-                consider(cu.sy[a], cu.sz[a], cu.cid[a], cu.k[a], cd.sy[b], cd.sz[b], cd.cid[b],
-                         cd.k[b], bestD, bcu, bcd, biu, bid);
-            }
-        }
-        return;
-    }
-    // more candidates than the lists hold: evaluate every pair from the rows
     const float my = 1e-3f * (1.0f + fabsf(yh)), mz = 1e-3f * (1.0f + fabsf(zh));
     const int uy0 = bin_y(U.G, yh - wyu - my), uy1 = bin_y(U.G, yh + wyu + my);
     const int uz0 = bin_z(U.G, zh - wzu - mz), uz1 = bin_z(U.G, zh + wzu + mz);
-    for (int bzu = uz0; bzu <= uz1; ++bzu) {
-        const int ua = U.bins[bzu * U.G.ny + uy0], ub = U.bins[bzu * U.G.ny + uy1 + 1];
-        for (int ku = ua; ku < ub; ++ku) {
-            const float2 cu2 = U.yz[ku];
-            const float ddyu = __fsub_rn(cu2.x, yh);
-            const float ddzu = __fsub_rn(cu2.y, zh);
-            if (!(fabsf(ddyu) <= wyu) || !(fabsf(ddzu) <= wzu)) continue;
-            const float syu = __fmul_rn(ddyu, iu), szu = __fmul_rn(ddzu, iu);
-            const int ccu = U.cid[ku];
-            CandList all = cd;  // re-scan the down side when its list overflowed
-            if (cd.n > kList) {
-                const int dy0 = bin_y(D.G, yh - wyd - my), dy1 = bin_y(D.G, yh + wyd + my);
-                const int dz0 = bin_z(D.G, zh - wzd - mz), dz1 = bin_z(D.G, zh + wzd + mz);
-                for (int bzd = dz0; bzd <= dz1; ++bzd) {
-                    const int da = D.bins[bzd * D.G.ny + dy0], db = D.bins[bzd * D.G.ny + dy1 + 1];
-                    for (int kd = da; kd < db; ++kd) {
-                        const float2 cd2 = D.yz[kd];
-                        const float ddyd = __fsub_rn(yh, cd2.x);
-                        const float ddzd = __fsub_rn(zh, cd2.y);
-                        if (!(fabsf(ddyd) <= wyd) || !(fabsf(ddzd) <= wzd)) continue;
-                        consider(syu, szu, ccu, ku, __fmul_rn(ddyd, id), __fmul_rn(ddzd, id),
-                                 D.cid[kd], kd, bestD, bcu, bcd, biu, bid);
-                    }
-                }
-            } else {
+    const int dy0 = bin_y(D.G, yh - wyd - my), dy1 = bin_y(D.G, yh + wyd + my);
+    const int dz0 = bin_z(D.G, zh - wzd - mz), dz1 = bin_z(D.G, zh + wzd + mz);
+    BinWalk wu;
+    walk_open(U, uy0, uy1, uz0, uz1, wu);
+    bool up_left = true;
+    while (up_left) {
+        // the next chunk of admissible up candidates
+        float csy[kUpChunk], csz[kUpChunk];
+        int ccid[kUpChunk], ck[kUpChunk];
+        int n = 0;
+        while (n <= kUpChunk - 4) {  // a batch of four always fits
+            int kk[4];
+            float2 v[4];
 #pragma unroll
-                for (int b = 0; b < kList; ++b)
-                    if (b < all.n)
-                        consider(syu, szu, ccu, ku, all.sy[b], all.sz[b], all.cid[b], all.k[b],
-                                 bestD, bcu, bcd, biu, bid);
+            for (int j = 0; j < 4; ++j) {
+                kk[j] = walk_next(U, uy0, uy1, wu);
+                if (kk[j] >= 0) v[j] = U.yz[kk[j]];
+            }
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (kk[j] < 0) continue;
+                any = true;
+                const float ddy = __fsub_rn(v[j].x, yh), ddz = __fsub_rn(v[j].y, zh);
+                if (fabsf(ddy) <= wyu && fabsf(ddz) <= wzu) {
+#pragma unroll
+                    for (int q = 0; q < kUpChunk; ++q) {
+                        if (q == n) {
+                            csy[q] = __fmul_rn(ddy, iu);
+                            csz[q] = __fmul_rn(ddz, iu);
+                            ck[q] = kk[j];
+                        }
+                    }
+                    ++n;
+                }
+            }
+            if (!any) {
+                up_left = false;
+                break;
+            }
+        }
+        if (n == 0) break;
+#pragma unroll
+        for (int q = 0; q < kUpChunk; ++q)
+            if (q < n) ccid[q] = U.cid[ck[q]];
+        // stream the down side against this chunk
+        BinWalk wd;
+        walk_open(D, dy0, dy1, dz0, dz1, wd);
+        for (;;) {
+            int kk[4];
+            float2 v[4];
+            int cdv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                kk[j] = walk_next(D, dy0, dy1, wd);
+                if (kk[j] >= 0) {
+                    v[j] = D.yz[kk[j]];
+                    cdv[j] = D.cid[kk[j]];
+                }
+            }
+            if (kk[0] < 0) break;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (kk[j] < 0) break;
+                const float ddy = __fsub_rn(yh, v[j].x), ddz = __fsub_rn(zh, v[j].y);
+                if (!(fabsf(ddy) <= wyd) || !(fabsf(ddz) <= wzd)) continue;
+                const float syd = __fmul_rn(ddy, id), szd = __fmul_rn(ddz, id);
+#pragma unroll
+                for (int q = 0; q < kUpChunk; ++q)
+                    if (q < n)
+                        consider(csy[q], csz[q], ccid[q], ck[q], syd, szd, cdv[j], kk[j], bestD,
+                                 bcu, bcd, biu, bid);
             }
         }
     }
