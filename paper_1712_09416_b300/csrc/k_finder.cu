@@ -32,6 +32,101 @@ struct RowView {      // one adjacent row
     RowGrid G;
 };
 
+// Admissible candidates of one side, kept in registers (at most kList); the
+// insert is a chain of predicated moves so that the list never spills.
+constexpr int kList = 4;
+struct CandList {
+    float sy[kList], sz[kList];
+    int cid[kList], k[kList];
+    int n;
+};
+
+__device__ __forceinline__ void push(CandList& c, float sy, float sz, int k)
+{
+#pragma unroll
+    for (int j = 0; j < kList; ++j) {
+        if (c.n == j) {
+            c.sy[j] = sy;
+            c.sz[j] = sz;
+            c.k[j] = k;
+        }
+    }
+    ++c.n;
+}
+
+// Scan one side's window: admissible candidates and their slopes.  up = true
+// gives slopes (c - h) * inv, up = false gives (h - c) * inv.  The hit ranges
+// of the window's z-bins (up to four) are walked as one flat index space so
+// that lanes with different bin counts stay together, four candidates per
+// step with their loads issued together; the cids of the kept candidates are
+// read at the end.
+__device__ __forceinline__ void collect(const RowView& V, float yh, float zh, float inv, float wy,
+                                       float wz, bool up, CandList& c)
+{
+    const float my = 1e-3f * (1.0f + fabsf(yh)), mz = 1e-3f * (1.0f + fabsf(zh));
+    const int y0 = bin_y(V.G, yh - wy - my), y1 = bin_y(V.G, yh + wy + my);
+    const int z0 = bin_z(V.G, zh - wz - mz), z1 = bin_z(V.G, zh + wz + mz);
+    c.n = 0;
+    auto test = [&](int k, float2 v) {
+        const float ddy = up ? __fsub_rn(v.x, yh) : __fsub_rn(yh, v.x);
+        const float ddz = up ? __fsub_rn(v.y, zh) : __fsub_rn(zh, v.y);
+        if (fabsf(ddy) <= wy && fabsf(ddz) <= wz)
+            push(c, __fmul_rn(ddy, inv), __fmul_rn(ddz, inv), k);
+    };
+    if (z1 - z0 < 4) {
+        int a[4], n[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int bz = z0 + j;
+            a[j] = 0;
+            n[j] = 0;
+            if (bz <= z1) {
+                a[j] = V.bins[bz * V.G.ny + y0];
+                n[j] = V.bins[bz * V.G.ny + y1 + 1] - a[j];
+            }
+        }
+        const int c1 = n[0], c2 = c1 + n[1], c3 = c2 + n[2], tot = c3 + n[3];
+        for (int q = 0; q < tot; q += 4) {
+            int kk[4];
+            float2 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int qj = q + j < tot ? q + j : q;
+                kk[j] = qj < c1 ? a[0] + qj : qj < c2 ? a[1] + (qj - c1)
+                                          : qj < c3 ? a[2] + (qj - c2) : a[3] + (qj - c3);
+                v[j] = V.yz[kk[j]];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (q + j < tot) test(kk[j], v[j]);
+        }
+    } else {
+        for (int bz = z0; bz <= z1; ++bz) {
+            const int ka = V.bins[bz * V.G.ny + y0], kb = V.bins[bz * V.G.ny + y1 + 1];
+            for (int k = ka; k < kb; ++k) test(k, V.yz[k]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kList; ++j)
+        if (j < c.n) c.cid[j] = V.cid[c.k[j]];
+}
+
+__device__ __forceinline__ void consider(float syu, float szu, int cu, int ku, float syd, float szd,
+                                         int cd, int kd, float& bestD, int& bcu, int& bcd,
+                                         int& biu, int& bid)
+{
+    const float ey = __fsub_rn(syu, syd), ez = __fsub_rn(szu, szd);
+    const float Dv = __fadd_rn(__fmul_rn(ey, ey), __fmul_rn(ez, ez));
+    const bool better = bcu < 0 || Dv < bestD || (Dv == bestD && (cu < bcu || (cu == bcu && cd < bcd)));
+    if (better) {
+        bestD = Dv;
+        bcu = cu;
+        bcd = cd;
+        biu = ku;
+        bid = kd;
+    }
+}
+
 // The candidates of one side lie in the window's y-z bins: for each z-bin
 // from z0 to z1 the sorted hits [bins[bz*ny + y0], bins[bz*ny + y1 + 1]).
 // BinWalk enumerates them bin after bin, four indices at a time, so that the
@@ -60,23 +155,7 @@ __device__ __forceinline__ int walk_next(const RowView& V, int y0, int y1, BinWa
     return w.k++;
 }
 
-__device__ __forceinline__ void consider(float syu, float szu, int cu, int ku, float syd, float szd,
-                                         int cd, int kd, float& bestD, int& bcu, int& bcd,
-                                         int& biu, int& bid)
-{
-    const float ey = __fsub_rn(syu, syd), ez = __fsub_rn(szu, szd);
-    const float Dv = __fadd_rn(__fmul_rn(ey, ey), __fmul_rn(ez, ez));
-    const bool better = bcu < 0 || Dv < bestD || (Dv == bestD && (cu < bcu || (cu == bcu && cd < bcd)));
-    if (better) {
-        bestD = Dv;
-        bcu = cu;
-        bcd = cd;
-        biu = ku;
-        bid = kd;
-    }
-}
-
-// Admissible up candidates are gathered in registers in chunks of up to
+// Crowded windows: admissible up candidates are gathered in registers in chunks of up to
 // kUpChunk (slopes, cid, index; batches of four loads until the chunk holds
 // more than kUpChunk - 4); for each chunk every down candidate is streamed
 // from the bins and scored against the whole chunk.  Any number of
@@ -84,8 +163,10 @@ __device__ __forceinline__ void consider(float syu, float szu, int cu, int ku, f
 // down side).
 constexpr int kUpChunk = 8;
 
-// Best (down, up) pair of hit (yh, zh): least D over all admissible pairs.
-__device__ __forceinline__ void best_pair(const RowView& U, const RowView& D, float yh, float zh,
+// Best (down, up) pair when a window holds more admissible candidates than
+// the register lists of best_pair (run by k_neighbours_crowded, a kernel of
+// its own, so that its registers do not weigh on the common path).
+__device__ __forceinline__ void best_pair_crowded(const RowView& U, const RowView& D, float yh, float zh,
                                           float iu, float id, float wyu, float wzu, float wyd,
                                           float wzd, float& bestD, int& bcu, int& bcd, int& biu,
                                           int& bid)
@@ -170,6 +251,44 @@ __device__ __forceinline__ void best_pair(const RowView& U, const RowView& D, fl
     }
 }
 
+// Best (down, up) pair of hit (yh, zh): least D over all admissible pairs.
+// Returns false, with nothing decided, when a side has more admissible
+// candidates than its list holds (the hit goes to k_neighbours_crowded).
+__device__ __forceinline__ bool best_pair(const RowView& U, const RowView& D, float yh, float zh,
+                                          float iu, float id, float wyu, float wzu, float wyd,
+                                          float wzd, float& bestD, int& bcu, int& bcd, int& biu,
+                                          int& bid)
+{
+    CandList cu, cd;
+    collect(U, yh, zh, iu, wyu, wzu, true, cu);
+    collect(D, yh, zh, id, wyd, wzd, false, cd);
+    if (cu.n <= kList && cd.n <= kList) {
+#pragma unroll
+        for (int a = 0; a < kList; ++a) {
+            if (a >= cu.n) break;
+#pragma unroll
+            for (int b = 0; b < kList; ++b) {
+                if (b >= cd.n) break;
+                consider(cu.sy[a], cu.sz[a], cu.cid[a], cu.k[a], cd.sy[b], cd.sz[b], cd.cid[b],
+                         cd.k[b], bestD, bcu, bcd, biu, bid);
+            }
+        }
+        return true;
+    }
+    return false;  // more candidates than the lists hold
+}
+
+// Hand hit i to k_neighbours_crowded (warp-aggregated append).
+__device__ __forceinline__ void push_crowded(const Launch& L, int i)
+{
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int b = 0;
+    if (lane == leader) b = atomicAdd(&L.cnt->n_crowded, __popc(m));
+    b = __shfl_sync(m, b, leader);
+    L.crowded[b + __popc(m & ((1u << lane) - 1))] = i;
+}
+
 // One thread per sorted hit; the adjacent rows' hits, bins and grids are read
 // through the L1 cache (the hits of a block share one or two rows).
 __global__ void __launch_bounds__(kNbThreads) k_neighbours(Launch L)
@@ -205,7 +324,47 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbours(Launch L)
         const float yh = ch.x, zh = ch.y;
         float bestD = 0.0f;
         int bcu = -1, bcd = -1, biu = -1, bid = -1;
-        best_pair(U, D, yh, zh, iu, id, wyu, wzu, wyd, wzd, bestD, bcu, bcd, biu, bid);
+        if (!best_pair(U, D, yh, zh, iu, id, wyu, wzu, wyd, wzd, bestD, bcu, bcd, biu, bid)) {
+            push_crowded(L, i);
+            continue;
+        }
+        const bool link = bcu >= 0 && bestD <= L.d_max;
+        L.up[i] = link ? (int16_t)biu : (int16_t)-1;
+        L.dn[i] = link ? (int16_t)bid : (int16_t)-1;
+    }
+}
+
+// The hits whose windows held more admissible candidates than the lists of
+// best_pair: the same decision with the chunked search (one thread per hit).
+__global__ void __launch_bounds__(kNbThreads) k_neighbours_crowded(Launch L)
+{
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
+    const int n = min(L.cnt->n_crowded, L.n_total > 0x7fffffff ? 0x7fffffff : (int)L.n_total);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int i = L.crowded[q];
+        const int hr = L.hrow[i];
+        const int gs = hr >> 8, r = hr & 255;
+        const int g = gs * L.R + r;
+        const float xh = __ldg(&L.xr[r]), xu = __ldg(&L.xr[r + 1]), xd = __ldg(&L.xr[r - 1]);
+        const float iu = __frcp_rn(__fsub_rn(xu, xh)), id = __frcp_rn(__fsub_rn(xh, xd));
+        const float wyu = __fmul_rn(L.slope_win_y, fabsf(__fsub_rn(xu, xh)));
+        const float wzu = __fmul_rn(L.slope_win_z, fabsf(__fsub_rn(xu, xh)));
+        const float wyd = __fmul_rn(L.slope_win_y, fabsf(__fsub_rn(xd, xh)));
+        const float wzd = __fmul_rn(L.slope_win_z, fabsf(__fsub_rn(xd, xh)));
+        RowView U, D;
+        U.G = L.grid[g + 1];
+        D.G = L.grid[g - 1];
+        const int bu = L.row_off[g + 1], bd = L.row_off[g - 1];
+        U.yz = L.hyz + bu;
+        U.cid = L.hcid + bu;
+        U.bins = L.bin_start + U.G.bin_off;
+        D.yz = L.hyz + bd;
+        D.cid = L.hcid + bd;
+        D.bins = L.bin_start + D.G.bin_off;
+        const float2 ch = L.hyz[i];
+        float bestD = 0.0f;
+        int bcu = -1, bcd = -1, biu = -1, bid = -1;
+        best_pair_crowded(U, D, ch.x, ch.y, iu, id, wyu, wzu, wyd, wzd, bestD, bcu, bcd, biu, bid);
         const bool link = bcu >= 0 && bestD <= L.d_max;
         L.up[i] = link ? (int16_t)biu : (int16_t)-1;
         L.dn[i] = link ? (int16_t)bid : (int16_t)-1;
@@ -283,7 +442,10 @@ __global__ void __launch_bounds__(kNrThreads) k_neighbours_rows(Launch L)
             const float2 ch = L.hyz[i];
             float bestD = 0.0f;
             int bcu = -1, bcd = -1, biu = -1, bid = -1;
-            best_pair(U, D, ch.x, ch.y, iu, id, wyu, wzu, wyd, wzd, bestD, bcu, bcd, biu, bid);
+            if (!best_pair(U, D, ch.x, ch.y, iu, id, wyu, wzu, wyd, wzd, bestD, bcu, bcd, biu, bid)) {
+                push_crowded(L, i);
+                continue;
+            }
             const bool link = bcu >= 0 && bestD <= L.d_max;
             L.up[i] = link ? (int16_t)biu : (int16_t)-1;
             L.dn[i] = link ? (int16_t)bid : (int16_t)-1;
@@ -421,6 +583,12 @@ void launch_finder(const Launch& L, const Schedule& S, void* stream_, const Kern
         if (nb > (long long)S.n_sm * 64) nb = (long long)S.n_sm * 64;
         if (nb < 1) nb = 1;
         k_neighbours<<<(int)nb, th, 0, stream>>>(L);
+    }
+    {
+        long long nc = (L.n_total + 255) / 256;
+        if (nc > (long long)S.n_sm * 8) nc = (long long)S.n_sm * 8;
+        if (nc < 1) nc = 1;
+        k_neighbours_crowded<<<(int)nc, 256, 0, stream>>>(L);
     }
     hook_after(hook, "k_neighbours");
     k_clean_starts<<<L.n_hit_tiles, kCsThreads, 0, stream>>>(L);

@@ -75,6 +75,7 @@ struct Counters {
     int n_track_hits;
     int n_bins;
     int ticket_rows, ticket_hits, ticket_sectors;
+    int n_crowded;        // hits whose neighbour windows overflow the register lists
     int tl_next;          // work counters of the persistent constructor passes
     int tl_next2;
     int n_dominated;      // chains whose tracklet is not built (dominated)
@@ -138,6 +139,7 @@ struct Launch {
     int* upg;                   // [N] cleaned up link, global index or -1
     unsigned long long* weight;
     unsigned char* mark;        // [N] hit taken by a forward extension search (or null)
+    int* crowded;               // [N] hits for the chunked neighbour search
     int* starts;                // [t_cap] global sorted index
     TrackletHdr* tl;            // [t_cap]
     int4* tl_chain;             // [t_cap] start hit, its sector << 8 | row, chain end hit, end row

@@ -44,7 +44,7 @@ constexpr size_t kNaBytes =
     up256(4 * kNaBins) + 8 * up256(4 * kNaMaxClusters) /* tmp yz cid rank, hyz hcid hrow */ +
     2 * up256(4 * kNaMaxClusters) /* up dn */ + 2 * up256(4 * kNaMaxClusters) /* upc dnc */ +
     up256(4 * kNaMaxClusters) /* upg */ + up256(8 * kNaMaxClusters) /* weight */ +
-    up256(4 * kNaMaxClusters) /* starts */;
+    up256(4 * kNaMaxClusters) /* starts */ + up256(4 * kNaMaxClusters) /* crowded */;
 
 // The scratch: shared by every call on a device and holding the last call's
 // contents; whatever must start at zero is cleared at the start of a call.
@@ -193,6 +193,7 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
     L.upg = (int*)take(4 * kNaMaxClusters);
     L.weight = (unsigned long long*)take(8 * kNaMaxClusters);
     L.starts = (int*)take(4 * kNaMaxClusters);
+    L.crowded = (int*)take(4 * kNaMaxClusters);
     if (off > kNaBytes) return TPC_EINVAL;  // layout and size disagree (cannot happen)
     if (cudaMemcpyAsync(desc, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return TPC_ECUDA;

@@ -94,6 +94,7 @@ struct Slot {
     int16_t *up, *dn, *upc, *dnc;
     unsigned long long* weight;
     unsigned char* mark;
+    int* crowded;
     int* starts;
     TrackletHdr* tl;
     int4* tl_chain;
@@ -279,6 +280,7 @@ size_t layout(Slot& s, char* base)
     s.dnc = (int16_t*)take(2 * k.n);
     s.weight = (unsigned long long*)take(8 * k.n);
     s.mark = (unsigned char*)take(k.n);
+    s.crowded = (int*)take(4 * k.n);
     s.starts = (int*)take(4 * (size_t)k.t);
     s.tl = (TrackletHdr*)take(sizeof(TrackletHdr) * (size_t)k.t);
     s.tl_chain = (int4*)take(16 * (size_t)k.t);
@@ -614,6 +616,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.dnc = s.dnc;
     L.weight = s.weight;
     L.mark = s.mark;
+    L.crowded = s.crowded;
     L.starts = s.starts;
     L.tl = s.tl;
     L.tl_chain = s.tl_chain;
