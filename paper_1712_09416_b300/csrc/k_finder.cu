@@ -584,13 +584,14 @@ void launch_finder(const Launch& L, const Schedule& S, void* stream_, const Kern
         if (nb < 1) nb = 1;
         k_neighbours<<<(int)nb, th, 0, stream>>>(L);
     }
+    hook_after(hook, "k_neighbours");
     {
         long long nc = (L.n_total + 255) / 256;
         if (nc > (long long)S.n_sm * 8) nc = (long long)S.n_sm * 8;
         if (nc < 1) nc = 1;
         k_neighbours_crowded<<<(int)nc, 256, 0, stream>>>(L);
     }
-    hook_after(hook, "k_neighbours");
+    hook_after(hook, "k_neighbours_crowded");
     k_clean_starts<<<L.n_hit_tiles, kCsThreads, 0, stream>>>(L);
     hook_after(hook, "k_clean_starts");
 }

@@ -67,7 +67,7 @@ __device__ __forceinline__ void scan_range(const Fit& f, float yref, float zref,
             const float r1 = c[j].y - f.p[1];
             const float chi2 = (S11 * r0 * r0 - 2.0f * S01 * r0 * r1 + S00 * r1 * r1) * id;
             // exact ties (rare) go to the lower cid; the cid is read only then
-            if (chi2 < best || (chi2 == best && L.hcid[k + j] < L.hcid[bk])) {
+            if (chi2 < best || (chi2 == best && bk >= 0 && L.hcid[k + j] < L.hcid[bk])) {
                 best = chi2;
                 bk = k + j;
                 by = c[j].x;
@@ -122,7 +122,7 @@ __device__ __forceinline__ int search(const Fit& f, float yref, float zref, cons
                 const float r0 = c[j].x - f.p[0];
                 const float r1 = c[j].y - f.p[1];
                 const float chi2 = (S11 * r0 * r0 - 2.0f * S01 * r0 * r1 + S00 * r1 * r1) * id;
-                if (chi2 < best || (chi2 == best && L.hcid[kk[j]] < L.hcid[bk])) {
+                if (chi2 < best || (chi2 == best && bk >= 0 && L.hcid[kk[j]] < L.hcid[bk])) {
                     best = chi2;
                     bk = kk[j];
                     by = c[j].x;
@@ -140,10 +140,6 @@ __device__ __forceinline__ int search(const Fit& f, float yref, float zref, cons
     mz = bzv;
     return (bk >= 0 && best <= L.chi2_hit) ? bk : -1;
 }
-
-// Seed covariance at the current direction: diagonal, cluster variances for
-// (y, z), slope variances of dy/dx and dz/dx carried over to sin(phi) and
-// tan(lambda) (factors cos^6 phi and cos^2 phi), seed_var_q for q/pT.
 
 // One thread per start hit: follow its chain of cleaned up-links, record the
 // chain's hits in the tracklet's rowhit slot and the chain in tl_chain
