@@ -103,13 +103,13 @@ F_A = 0.9
 STAGE_BYTES = {"a1": 40, "a2": 14, "a3": 12, "a4": 4, "a5": 43, "a6": 15}
 PATH_BYTES = sum(STAGE_BYTES.values())
 KERNEL_STAGE = {"k_count": "a1", "k_rowscan": "a1", "k_scatter": "a1", "k_rowsort": "a1",
-                "k_rowsort_big": "a1", "k_neighbours": "a2", "k_neighbours_crowded": "a2",
+                "k_rowsort_big": "a1", "k_rowsort_big4k": "a1", "k_neighbours": "a2", "k_neighbours_crowded": "a2",
                 "k_clean_starts": "a3+a4",
                 "k_chains": "a5", "k_constructor_fwd": "a5", "k_dominance": "a5",
                 "k_constructor_bwd": "a5", "k_weights": "a5",
                 "k_sel_decide": "a6", "k_sel_sort": "a6", "k_sel_write": "a6"}
 KERNEL_BYTES = {"k_count": 12, "k_rowscan": 4, "k_scatter": 24, "k_rowsort": 0,
-                "k_rowsort_big": 0, "k_neighbours": 14, "k_neighbours_crowded": 0,
+                "k_rowsort_big": 0, "k_rowsort_big4k": 0, "k_neighbours": 14, "k_neighbours_crowded": 0,
                 "k_clean_starts": 16,
                 "k_chains": 2 * F_A, "k_constructor_fwd": 12 * F_A, "k_dominance": 0,
                 "k_constructor_bwd": 8.7 * F_A, "k_weights": 8 + 16 * F_A,
@@ -146,6 +146,7 @@ def kernel_bytes(c: dict) -> dict:
         "k_scatter": 12 * N + 12 * N,
         "k_rowsort": 12 * N + 16 * N + 8 * N + 4 * (B + RS) + 32 * RS,
         "k_rowsort_big": 0,  # its rows' bytes are counted in k_rowsort
+        "k_rowsort_big4k": 0,
         "k_neighbours": 8 * N + 4 * N + 4 * B,
         "k_neighbours_crowded": 0,  # its hits' bytes are counted in k_neighbours
         "k_clean_starts": 4 * N + 4 * N + 4 * N + 4 * N + 4 * T,

@@ -360,7 +360,7 @@ int tpc_track_kernel_times(tpc_track_ctx* ctx, tpc_kernel_time* out, int cap, in
  * speed only, never the results.  n_sm and tl_max_per_sm describe the device
  * and the constructor's occupancy limit (read-only); the others are:
  *   bin_blocks_per_sm  blocks per SM of the count and scatter kernels (1..32)
- *   sort_threads       threads of a row-sort block (256 or 512)
+ *   sort_threads       threads of a block of the large-row sort (rows above 1024 hits; 256 or 512)
  *   nb_threads         threads of a neighbour-finder block (64, 128 or 256)
  *   tl_blocks_per_sm   persistent constructor blocks per SM (1..tl_max_per_sm)
  *   streams            slots that consecutive direct launches go to in turn,

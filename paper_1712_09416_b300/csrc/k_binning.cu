@@ -11,11 +11,15 @@
 //              counts (single pass, decoupled look-back), and the y-z grid
 //              of each row sized for about two hits per bin
 //   k_scatter  moves every cluster to row offset + rank
-//   k_rowsort  one block per row: counting sort by bin in shared memory,
-//              cid order inside a bin, writes the sorted hits and the bin
-//              offsets (and clears the hit weights for the fit); rows above
-//              1024 hits are listed and sorted by a second launch with a
-//              larger shared-memory footprint
+//   k_rowsort  counting sort of each row by bin in shared memory, cid order
+//              inside a bin; writes the sorted hits and the bin offsets (and
+//              clears the hit weights for the fit).  Rows of up to 256 hits
+//              (most rows of peripheral events) take one warp each, with no
+//              block barriers; rows of up to 1024 hits, listed by k_rowscan,
+//              one block each, taken in turn from the list by the same
+//              blocks first; larger rows are sorted by k_rowsort_big with
+//              larger shared-memory footprints (up to 2048 hits, and up to
+//              4096)
 // Bytes per cluster (read + write): count 12, scatter 12 + 12, rowsort 12 +
 // 16 + 8 (weights), plus the row and bin tables.
 #include <cuda_runtime.h>
@@ -27,6 +31,14 @@ namespace tpc {
 namespace {
 
 constexpr int kEvSmem = 1024;
+
+// Row sorts: rows of up to kWarpRowHits hits take one warp, rows of up to
+// kSmallRowHits one block of k_rowsort, larger rows one block of
+// k_rowsort_big.
+constexpr int kWarpRowHits = 256;
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kWsHist = kWarpRowHits * kBinsPerHitX2 / 2 + 4;  // >= nb + 1, keeps 16-byte regions
 
 __device__ __forceinline__ int find_event(const long long* off, int n_ev, long long i)
 {
@@ -188,6 +200,12 @@ __global__ void __launch_bounds__(kScanThreads) k_rowscan(Launch L)
         if (g < L.RS) {
             const int c = L.row_cnt[g * kCntPad];
             cmax = max(cmax, c);
+            // rows for the block sorts: from the front of big_rows the rows
+            // for k_rowsort, from the back those for k_rowsort_big
+            if (c > kWarpRowHits) {
+                if (c <= kSmallRowHits) L.big_rows[atomicAdd(&L.cnt->n_mid_rows, 1)] = g;
+                else L.big_rows[L.RS - 1 - atomicAdd(&L.cnt->n_big_rows, 1)] = g;
+            }
             RowGrid G = make_grid(L, g, c);
             L.grid[g] = G;
             v = pack2((unsigned)c, (unsigned)(G.ny * G.nz + 1));
@@ -250,121 +268,256 @@ __global__ void k_scatter(Launch L)
     }
 }
 
-constexpr int kSortThreads = 512;
-
-// Shared memory of a row sort for rows of up to cap hits.
+// Shared memory of a block row sort for rows of up to cap hits, and of a
+// warp row sort.
 constexpr size_t sort_smem(int cap)
 {
     return sizeof(int) * (cap * kBinsPerHitX2 / 2 + 2) + sizeof(int) * cap +
            3 * sizeof(int16_t) * cap;
 }
+constexpr size_t kWarpSortSmem = sizeof(int) * kWsHist + sizeof(int) * kWarpRowHits +
+                                 3 * sizeof(int16_t) * kWarpRowHits;
+constexpr size_t kRowsortSmem = sort_smem(kSmallRowHits) > kRsWarps * kWarpSortSmem
+                                    ? sort_smem(kSmallRowHits)
+                                    : kRsWarps * kWarpSortSmem;
+static_assert(kWarpSortSmem % 16 == 0, "warp regions stay aligned");
 
-// One block per row: counting sort by bin, cid order inside a bin.  BIG =
-// false sorts the rows of up to kSmallRowHits hits and lists the larger ones
-// in big_rows; BIG = true sorts the listed rows (up to kMaxRowHits each).
-template <bool BIG>
-__global__ void __launch_bounds__(kSortThreads) k_rowsort(Launch L)
+// Write the sorted row: hit p of the row is input hit order[p]; every bin's
+// start offset (and the row's end in bin nb).
+__device__ __forceinline__ void write_row(const Launch& L, int base, int n, int nb, int bin_off,
+                                          int hrow, const int16_t* order, const int* cid,
+                                          const int* hist, int t0, int dt)
 {
-    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
-    constexpr int CAP = BIG ? kMaxRowHits : kSmallRowHits;
-    extern __shared__ unsigned char smem[];
-    int* hist = reinterpret_cast<int*>(smem);                           // [nb + 1]
-    int* scid = hist + (CAP * kBinsPerHitX2 / 2 + 2);                   // [n]
-    int16_t* sbin = reinterpret_cast<int16_t*>(scid + CAP);             // [n]
-    int16_t* sslot = sbin + CAP;                                        // [n]
-    int16_t* sorder = sslot + CAP;                                      // [n]
-    const int n_items = BIG ? min(L.cnt->n_big_rows, L.RS) : L.RS;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int g = BIG ? L.big_rows[it] : it;
-        const int base = L.row_off[g];
-        const int n = L.row_off[g + 1] - base;
-        if (!BIG && n > CAP) {
-            if (threadIdx.x == 0) L.big_rows[atomicAdd(&L.cnt->n_big_rows, 1)] = g;
-            continue;
-        }
-        const RowGrid G = L.grid[g];
-        const int nb = G.ny * G.nz;
-        const int gs = g / L.R;
-        const int hrow = (gs << 8) | (g - gs * L.R);
-        if (n > kMaxRowHits) {
-            // capacity error: keep the row in bounds for the later stages
-            // (hits copied unsorted, every bin empty); the launch fails.
-            if (threadIdx.x == 0) atomicExch(&L.cnt->ovf_row, 1);
-            for (int p = threadIdx.x; p < n; p += blockDim.x) {
-                L.hyz[base + p] = L.tmp_yz[base + p];
-                L.hcid[base + p] = L.tmp_cid[base + p];
-                L.hrow[base + p] = hrow;
-                L.weight[base + p] = 0ULL;
-                if (L.mark) L.mark[base + p] = 0;
+    for (int p = t0; p < n; p += dt) {
+        const int i = order[p];
+        L.hyz[base + p] = L.tmp_yz[base + i];
+        L.hcid[base + p] = cid[i];
+        L.hrow[base + p] = hrow;
+        L.weight[base + p] = 0ULL;
+        if (L.mark) L.mark[base + p] = 0;
+    }
+    for (int b = t0; b <= nb; b += dt) L.bin_start[bin_off + b] = hist[b];
+}
+
+// Insertion sort by cid inside each bin (bins hold a few hits); threads t0,
+// t0 + dt, ... take bins in turn.
+__device__ __forceinline__ void cid_order(int nb, const int* hist, const int* scid,
+                                          int16_t* sorder, int t0, int dt)
+{
+    for (int b = t0; b < nb; b += dt) {
+        const int lo = hist[b], hi = hist[b + 1];
+        for (int a = lo + 1; a < hi; ++a) {
+            const int16_t v = sorder[a];
+            const int key = scid[v];
+            int c = a - 1;
+            while (c >= lo && scid[sorder[c]] > key) {
+                sorder[c + 1] = sorder[c];
+                --c;
             }
-            for (int b = threadIdx.x; b <= nb; b += blockDim.x) L.bin_start[G.bin_off + b] = 0;
-            continue;
+            sorder[c + 1] = v;
         }
-        for (int b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const float2 c = L.tmp_yz[base + i];
-            const int b = bin_z(G, c.y) * G.ny + bin_y(G, c.x);
-            sbin[i] = (int16_t)b;
-            scid[i] = L.tmp_cid[base + i];
-            sslot[i] = (int16_t)atomicAdd(&hist[b], 1);
-        }
-        __syncthreads();
-        // exclusive scan of hist[0..nb] (hist[nb] = 0 -> becomes n)
-        {
-            const int per = (nb + 1 + blockDim.x - 1) / blockDim.x;
-            const int lo = threadIdx.x * per;
-            const int hi = min(lo + per, nb + 1);
-            int s = 0;
-            for (int b = lo; b < hi; ++b) s += hist[b];
-            unsigned long long tot;
-            const int ex = (int)block_excl_scan((unsigned long long)s, &tot);
-            int run = ex;
-            for (int b = lo; b < hi; ++b) {
-                const int c = hist[b];
-                hist[b] = run;
-                run += c;
-            }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) sorder[hist[sbin[i]] + sslot[i]] = (int16_t)i;
-        __syncthreads();
-        // cid order inside each bin (bins hold a few hits)
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const int lo = hist[b], hi = hist[b + 1];
-            for (int a = lo + 1; a < hi; ++a) {
-                const int16_t v = sorder[a];
-                const int key = scid[v];
-                int c = a - 1;
-                while (c >= lo && scid[sorder[c]] > key) {
-                    sorder[c + 1] = sorder[c];
-                    --c;
-                }
-                sorder[c + 1] = v;
-            }
-        }
-        __syncthreads();
+    }
+}
+
+// Counting sort of row g (up to CAP hits) by the whole block; every thread
+// calls it.  A row above kMaxRowHits is a capacity error: its hits are
+// copied unsorted and every bin left empty, so that the later stages stay in
+// bounds, and the launch fails.
+template <int CAP>
+__device__ void sort_row_block(const Launch& L, int g, unsigned char* smem)
+{
+    int* hist = reinterpret_cast<int*>(smem);                // [nb + 1]
+    int* scid = hist + (CAP * kBinsPerHitX2 / 2 + 2);        // [n]
+    int16_t* sbin = reinterpret_cast<int16_t*>(scid + CAP);  // [n]
+    int16_t* sslot = sbin + CAP;                             // [n]
+    int16_t* sorder = sslot + CAP;                           // [n]
+    const int base = L.row_off[g];
+    const int n = L.row_off[g + 1] - base;
+    const RowGrid G = L.grid[g];
+    const int nb = G.ny * G.nz;
+    const int gs = g / L.R;
+    const int hrow = (gs << 8) | (g - gs * L.R);
+    if (n > CAP) {
+        if (threadIdx.x == 0) atomicExch(&L.cnt->ovf_row, 1);
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            const int i = sorder[p];
-            L.hyz[base + p] = L.tmp_yz[base + i];
-            L.hcid[base + p] = scid[i];
+            L.hyz[base + p] = L.tmp_yz[base + p];
+            L.hcid[base + p] = L.tmp_cid[base + p];
             L.hrow[base + p] = hrow;
             L.weight[base + p] = 0ULL;
             if (L.mark) L.mark[base + p] = 0;
         }
-        for (int b = threadIdx.x; b <= nb; b += blockDim.x) L.bin_start[G.bin_off + b] = hist[b];
+        for (int b = threadIdx.x; b <= nb; b += blockDim.x) L.bin_start[G.bin_off + b] = 0;
+        return;
+    }
+    for (int b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 c = L.tmp_yz[base + i];
+        const int b = bin_z(G, c.y) * G.ny + bin_y(G, c.x);
+        sbin[i] = (int16_t)b;
+        scid[i] = L.tmp_cid[base + i];
+        sslot[i] = (int16_t)atomicAdd(&hist[b], 1);
+    }
+    __syncthreads();
+    // exclusive scan of hist[0..nb] (hist[nb] = 0 -> becomes n)
+    {
+        const int per = (nb + 1 + blockDim.x - 1) / blockDim.x;
+        const int lo = threadIdx.x * per;
+        const int hi = min(lo + per, nb + 1);
+        int sum = 0;
+        for (int b = lo; b < hi; ++b) sum += hist[b];
+        unsigned long long tot;
+        int run = (int)block_excl_scan((unsigned long long)sum, &tot);
+        for (int b = lo; b < hi; ++b) {
+            const int c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sorder[hist[sbin[i]] + sslot[i]] = (int16_t)i;
+    __syncthreads();
+    cid_order(nb, hist, scid, sorder, threadIdx.x, blockDim.x);
+    __syncthreads();
+    write_row(L, base, n, nb, G.bin_off, hrow, sorder, scid, hist, threadIdx.x, blockDim.x);
+    __syncthreads();
+}
+
+// The same counting sort of row g (base, n <= kWarpRowHits hits) by one
+// warp, with warp-synchronous steps.
+__device__ void sort_row_warp(const Launch& L, int g, int base, int n, unsigned char* ws, int lane)
+{
+    int* hist = reinterpret_cast<int*>(ws);                          // [kWsHist]
+    int* scid = hist + kWsHist;                                      // [n]
+    int16_t* sbin = reinterpret_cast<int16_t*>(scid + kWarpRowHits);  // [n]
+    int16_t* sslot = sbin + kWarpRowHits;                            // [n]
+    int16_t* sorder = sslot + kWarpRowHits;                          // [n]
+    const RowGrid G = L.grid[g];
+    const int nb = G.ny * G.nz;  // <= max(1, 2n) < kWsHist
+    const int gs = g / L.R;
+    const int hrow = (gs << 8) | (g - gs * L.R);
+    for (int b = lane; b <= nb; b += 32) hist[b] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const float2 c = L.tmp_yz[base + i];
+        const int b = bin_z(G, c.y) * G.ny + bin_y(G, c.x);
+        sbin[i] = (int16_t)b;
+        scid[i] = L.tmp_cid[base + i];
+        sslot[i] = (int16_t)atomicAdd(&hist[b], 1);
+    }
+    __syncwarp();
+    // exclusive scan of hist[0..nb], one contiguous chunk of bins per lane
+    {
+        const int per = (nb + 1 + 31) >> 5;
+        const int lo = lane * per;
+        const int hi = min(lo + per, nb + 1);
+        int sum = 0;
+        for (int b = lo; b < hi; ++b) sum += hist[b];
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int run = incl - sum;
+        for (int b = lo; b < hi; ++b) {
+            const int c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) sorder[hist[sbin[i]] + sslot[i]] = (int16_t)i;
+    __syncwarp();
+    cid_order(nb, hist, scid, sorder, lane, 32);
+    __syncwarp();
+    write_row(L, base, n, nb, G.bin_off, hrow, sorder, scid, hist, lane, 32);
+    __syncwarp();
+}
+
+// Every row of up to kSmallRowHits hits.  The blocks first take the listed
+// rows of kWarpRowHits + 1 to kSmallRowHits hits one at a time from the
+// list (a work counter), then their warps sort the rows of up to
+// kWarpRowHits hits, one row per warp, so that the many small rows of a
+// batch of peripheral events are not each paid for with a block's barriers,
+// and the two kinds of row overlap on the GPU.
+__global__ void __launch_bounds__(kRsThreads) k_rowsort(Launch L)
+{
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
+    __shared__ __align__(16) unsigned char smem[kRowsortSmem];
+    __shared__ int item_s;
+    const int n_mid = min(L.cnt->n_mid_rows, L.RS);
+    for (;;) {
+        __syncthreads();  // the last item read by every thread
+        if (threadIdx.x == 0) item_s = atomicAdd(&L.cnt->mid_next, 1);
         __syncthreads();
+        const int it = item_s;
+        if (it >= n_mid) break;
+        sort_row_block<kSmallRowHits>(L, L.big_rows[it], smem);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* ws = smem + w * kWarpSortSmem;
+    const int stride = gridDim.x * kRsWarps;
+    int g = blockIdx.x * kRsWarps + w;
+    // the next row's offsets are read while this one is sorted
+    int nx0 = 0, nx1 = 0;
+    if (g < L.RS) {
+        nx0 = L.row_off[g];
+        nx1 = L.row_off[g + 1];
+    }
+    for (; g < L.RS; g += stride) {
+        const int base = nx0;
+        const int n = nx1 - base;
+        const int gn = g + stride;
+        if (gn < L.RS) {
+            nx0 = L.row_off[gn];
+            nx1 = L.row_off[gn + 1];
+        }
+        if (n <= kWarpRowHits) sort_row_warp(L, g, base, n, ws, lane);
+    }
+}
+
+// The rows above kSmallRowHits hits, one block each: CAP = kMidRowHits
+// sorts those of up to kMidRowHits hits (the pad rows of a pile-up event)
+// with half the shared memory, so twice as many blocks fit on an SM; CAP =
+// kMaxRowHits the larger ones.
+constexpr int kMidRowHits = 2048;
+
+template <int CAP>
+__global__ void __launch_bounds__(512) k_rowsort_big(Launch L)
+{
+    if (L.cnt->timeout) return;  // an earlier bounded wait gave up
+    extern __shared__ __align__(16) unsigned char smem_big[];
+    const int n_big = min(L.cnt->n_big_rows, L.RS);
+    for (int it = blockIdx.x; it < n_big; it += gridDim.x) {
+        const int g = L.big_rows[L.RS - 1 - it];
+        const int n = L.row_off[g + 1] - L.row_off[g];
+        if ((n <= kMidRowHits) == (CAP == kMidRowHits)) sort_row_block<CAP>(L, g, smem_big);
     }
 }
 
 }  // namespace
 
+int g_rowsort_per_sm = 1;       // resident k_rowsort blocks per SM
+int g_big_per_sm[2][2] = {{1, 1}, {1, 1}};  // k_rowsort_big<mid, max> x (256, 512 threads)
+
 void prepare_binning()
 {
-    cudaFuncSetAttribute(k_rowsort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sort_smem(kSmallRowHits));
-    cudaFuncSetAttribute(k_rowsort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_rowsort_per_sm, k_rowsort, kRsThreads, 0);
+    if (g_rowsort_per_sm < 1) g_rowsort_per_sm = 1;
+    cudaFuncSetAttribute(k_rowsort_big<kMidRowHits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem(kMidRowHits));
+    cudaFuncSetAttribute(k_rowsort_big<kMaxRowHits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sort_smem(kMaxRowHits));
+    for (int t = 0; t < 2; ++t) {
+        const int th = t ? 512 : 256;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_big_per_sm[0][t], k_rowsort_big<kMidRowHits>,
+                                                      th, sort_smem(kMidRowHits));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_big_per_sm[1][t], k_rowsort_big<kMaxRowHits>,
+                                                      th, sort_smem(kMaxRowHits));
+        for (int k = 0; k < 2; ++k)
+            if (g_big_per_sm[k][t] < 1) g_big_per_sm[k][t] = 1;
+    }
 }
 
 void launch_binning(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
@@ -377,14 +530,24 @@ void launch_binning(const Launch& L, const Schedule& S, void* stream_, const Ker
     hook_after(hook, "k_rowscan");
     k_scatter<<<blocks, 256, 0, stream>>>(L);
     hook_after(hook, "k_scatter");
-    const int rows_blocks = L.RS < S.n_sm * 16 ? L.RS : S.n_sm * 16;
-    const int threads = S.sort_threads == 256 ? 256 : kSortThreads;
-    k_rowsort<false><<<rows_blocks > 0 ? rows_blocks : 1, threads, sort_smem(kSmallRowHits),
-                       stream>>>(L);
-    hook_after(hook, "k_rowsort");
-    // the rows above kSmallRowHits hits, listed by the first pass
-    k_rowsort<true><<<S.n_sm * 2, kSortThreads, sort_smem(kMaxRowHits), stream>>>(L);
+    {
+        // every block resident at once (the loop over small rows is grid-strided)
+        long long rb = (long long)S.n_sm * g_rowsort_per_sm;
+        if (rb > L.RS) rb = L.RS;
+        if (rb < 1) rb = 1;
+        k_rowsort<<<(int)rb, kRsThreads, 0, stream>>>(L);
+        hook_after(hook, "k_rowsort");
+    }
+    // the rows above kSmallRowHits hits, listed by k_rowscan (every block
+    // resident at once)
+    const int t = S.sort_threads == 256 ? 0 : 1;
+    const int threads = t ? 512 : 256;
+    k_rowsort_big<kMidRowHits><<<S.n_sm * g_big_per_sm[0][t], threads, sort_smem(kMidRowHits),
+                                 stream>>>(L);
     hook_after(hook, "k_rowsort_big");
+    k_rowsort_big<kMaxRowHits><<<S.n_sm * g_big_per_sm[1][t], threads, sort_smem(kMaxRowHits),
+                                 stream>>>(L);
+    hook_after(hook, "k_rowsort_big4k");
 }
 
 }  // namespace tpc

@@ -80,13 +80,15 @@ struct Counters {
     int tl_next2;
     int n_dominated;      // chains whose tracklet is not built (dominated)
     int n_chain_hits;     // hits on the chains of all start hits
-    int n_big_rows;       // rows too large for the small row sort
+    int n_big_rows;       // rows above kSmallRowHits hits (listed for the large row sort)
+    int n_mid_rows;       // rows for the block row sort of k_rowsort
+    int mid_next;         // its work counter
     int n_mg_links;       // merger: links between sector tracks
     int n_mg_chains;      // merger: refitted chains of two or more tracks
     int n_mg_tracks;      // merger: tracks after merging
     int max_row_hits;     // high-water marks: hits of the fullest (sector, row)
     int max_sector_tracks;  // ... and emitted tracks of the fullest sector
-    int pad[6];
+    int pad[4];
 };
 
 // Merger scratch: a sector track's outer state, and the refit of a chain
@@ -126,7 +128,7 @@ struct Launch {
     int* sec_event;             // [S] event of a global sector
     int* row_cnt;               // [RS * kCntPad] hit count of row g at g * kCntPad
     int* ev_invalid;            // [n_events] invalid clusters per event
-    int* big_rows;              // [RS] rows left by the small row sort
+    int* big_rows;              // [RS] rows for the block row sorts (from the front) and the large row sort (from the back)
     int* row_off;               // [RS + 1]
     RowGrid* grid;              // [RS]
     unsigned long long* tile_state;  // look-back states (rows | hits | sectors)
@@ -307,7 +309,7 @@ inline void hook_after(const KernelHook* h, const char* name)
 struct Schedule {
     int n_sm = 148;            // multiprocessors of the device
     int bin_blocks_per_sm = 4; // k_count / k_scatter grid
-    int sort_threads = 512;    // k_rowsort block (256 or 512)
+    int sort_threads = 512;    // k_rowsort_big block (256 or 512)
     int nb_threads = 128;      // k_neighbours block (64, 128 or 256)
     int tl_blocks_per_sm = 0;  // persistent k_constructor blocks per SM (<= tl_max_per_sm)
     int tl_max_per_sm = 0;     // occupancy limit of k_constructor

@@ -1565,7 +1565,7 @@ int tpc_track_autotune(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
     int rc = tune(&Schedule::tl_blocks_per_sm, tl, {"k_constructor_fwd", "k_constructor_bwd"});
     if (!rc) rc = tune(&Schedule::nb_threads, {64, 128, 256}, {"k_neighbours", "k_neighbours_crowded"});
     if (!rc) rc = tune(&Schedule::nb_mode, {0, 1}, {"k_neighbours", "k_neighbours_crowded"});
-    if (!rc) rc = tune(&Schedule::sort_threads, {256, 512}, {"k_rowsort"});
+    if (!rc) rc = tune(&Schedule::sort_threads, {256, 512}, {"k_rowsort_big", "k_rowsort_big4k"});
     if (!rc) rc = tune(&Schedule::bin_blocks_per_sm, {2, 4, 8, 16}, {"k_count", "k_scatter"});
     if (rc) return rc;
     ctx->sched = best;
