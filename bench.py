@@ -103,14 +103,14 @@ F_A = 0.9
 STAGE_BYTES = {"a1": 40, "a2": 14, "a3": 12, "a4": 4, "a5": 43, "a6": 15}
 PATH_BYTES = sum(STAGE_BYTES.values())
 KERNEL_STAGE = {"k_count": "a1", "k_rowscan": "a1", "k_scatter": "a1", "k_rowsort": "a1",
-                "k_rowsort_big": "a1", "k_rowsort_big4k": "a1", "k_neighbours": "a2", "k_neighbours_crowded": "a2",
-                "k_clean_starts": "a3+a4",
+                "k_rowsort_big": "a1", "k_rowsort_big4k": "a1", "k_neighbours": "a2",
+                "k_neighbours_crowded": "a2", "k_clean_starts": "a3+a4",
                 "k_chains": "a5", "k_constructor_fwd": "a5", "k_dominance": "a5",
                 "k_constructor_bwd": "a5", "k_weights": "a5",
                 "k_sel_decide": "a6", "k_sel_sort": "a6", "k_sel_write": "a6"}
 KERNEL_BYTES = {"k_count": 12, "k_rowscan": 4, "k_scatter": 24, "k_rowsort": 0,
-                "k_rowsort_big": 0, "k_rowsort_big4k": 0, "k_neighbours": 14, "k_neighbours_crowded": 0,
-                "k_clean_starts": 16,
+                "k_rowsort_big": 0, "k_rowsort_big4k": 0, "k_neighbours": 14,
+                "k_neighbours_crowded": 0, "k_clean_starts": 16,
                 "k_chains": 2 * F_A, "k_constructor_fwd": 12 * F_A, "k_dominance": 0,
                 "k_constructor_bwd": 8.7 * F_A, "k_weights": 8 + 16 * F_A,
                 "k_sel_decide": 12 * F_A, "k_sel_sort": 0.7, "k_sel_write": 4 * F_A}
@@ -1143,7 +1143,7 @@ def run_ours(args):
                              f"({N_COPIES * 12 * n / 1e6:.0f} MB) > 126 MB L2; each step also "
                              "writes ~150 MB of intermediate arrays",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "launch": f"one CUDA graph per step (13 kernels); consecutive steps "
+                       "launch": f"one CUDA graph per step ({len(ktimes)} kernels); consecutive steps "
                                  f"spread over {n_streams} stream(s) so that their kernels run "
                                  "concurrently (autotuned); kernel times from a separate pass "
                                  "with kernels launched one by one on one stream",
