@@ -336,6 +336,7 @@ typedef struct {
     int64_t n_sector_tracks;                /* tracks before merging (= n_tracks without merge) */
     int64_t max_row_hits;       /* high-water marks: clusters of the fullest (sector, row) of the */
     int64_t max_sector_tracks;  /* launch and tracks of its fullest sector (each limited to 4096) */
+    int64_t n_crowded_hits;     /* hits whose neighbour windows held more than four candidates a side */
 } tpc_track_counters;
 int tpc_track_get_counters(const tpc_track_ctx* ctx, tpc_track_counters* c);
 

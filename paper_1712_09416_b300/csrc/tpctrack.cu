@@ -740,6 +740,7 @@ void fill_counters(Slot& s)
     K.n_sector_tracks = c.n_tracks;
     K.max_row_hits = c.max_row_hits;
     K.max_sector_tracks = c.max_sector_tracks;
+    K.n_crowded_hits = c.n_crowded;
     if (I.L.merge) {
         K.n_tracks = c.n_mg_tracks;
         K.n_merge_links = c.n_mg_links;

@@ -83,7 +83,8 @@ class tpc_track_counters(C.Structure):
         "n_clusters", "n_rows_total", "n_bins", "n_links", "n_starts", "n_tracklets",
         "n_valid_tracklets", "n_tracklet_hits", "n_tracks", "n_track_hits", "n_chain_hits",
         "n_dominated_chains",
-        "n_merge_links", "n_merge_chains", "n_sector_tracks", "max_row_hits", "max_sector_tracks")]
+        "n_merge_links", "n_merge_chains", "n_sector_tracks", "max_row_hits", "max_sector_tracks",
+        "n_crowded_hits")]
 
 
 class tpc_kernel_time(C.Structure):
