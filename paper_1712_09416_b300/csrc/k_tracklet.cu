@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(kChThreads) k_chains(Launch L)
 // forward passes (chain hits, then search) of every chain, marks the hits its
 // extension search takes and leaves the forward state at the last hit in the
 // header; PASS 2 (after k_dominance) runs the backward passes (assigned hits,
-// then search below the chain) of the chains that were not dominated.
+// then search below the chain) of the chains k_dominance listed (those not
+// dominated).
 template <int PASS>
 __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
 {
@@ -215,7 +216,8 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
     __syncthreads();
 #define BEST(i) best_s[i][threadIdx.x]
 #define PL(i) pl_s[i][threadIdx.x]
-    const int n_st = min(L.cnt->n_starts, L.t_cap);
+    // PASS 1 takes every chain, PASS 2 the chains k_dominance listed
+    const int n_st = min(PASS == 1 ? L.cnt->n_starts : L.cnt->n_bwd, L.t_cap);
     const int lane = threadIdx.x & 31;
     int t = -1;
     int phase = 0;  // 1 forward, 2 backward
@@ -273,6 +275,8 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
                 if (t >= n_st) {
                     t = -1;
                     exhausted = true;
+                } else if (PASS == 2) {
+                    t = L.tl_list[t];
                 }
             }
         }
@@ -294,11 +298,7 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             rowhit = L.tl_rowhit + (size_t)t * L.R;
             const float2 c0 = L.hyz[ch.x];
             if (PASS == 2) {
-                TrackletHdr& H = L.tl[t];
-                if (H.dominated) {  // header written by k_dominance
-                    t = -1;
-                    continue;
-                }
+                const TrackletHdr& H = L.tl[t];
                 // backward from the last hit with the covariance reset to the
                 // seed, starting from the forward state left in the header
                 yref = c0.x;
@@ -463,32 +463,61 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
 // Dominance: one warp per chain, lanes over its rows.  A chain all of whose
 // hits were taken by forward extension searches (of other tracklets: a
 // tracklet's own extension starts above its chain) gets no tracklet; its
-// header is made final here and the backward pass skips it.
-__global__ void k_dominance(Launch L)
+// header is made final here.  The other chains long enough for a tracklet
+// are listed for the backward pass (one atomic per block of eight chains):
+// its warps then hold only tracklets to refit, which issues fewer warp
+// instructions when several events share the GPU (one event alone gets
+// slightly slower, as full warps diverge more per row step).
+constexpr int kDomWarps = 8;
+
+__global__ void __launch_bounds__(32 * kDomWarps) k_dominance(Launch L)
 {
     if (L.cnt->timeout) return;  // an earlier bounded wait gave up
+    __shared__ int keep_s[kDomWarps];
+    __shared__ int base_s;
     const int n_st = min(L.cnt->n_starts, L.t_cap);
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int n_dom = 0;
-    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_st; t += warps) {
-        const int4 ch = L.tl_chain[t];
-        const int r0 = ch.y & 255, rk = ch.w;
-        if (rk - r0 + 1 < L.min_chain) continue;
-        const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
-        bool all = true;
-        for (int r = r0 + lane; r <= rk; r += 32) all = all && L.mark[rowhit[r]];
-        if (!__all_sync(0xffffffffu, all)) continue;
-        if (lane == 0) {
-            TrackletHdr& H = L.tl[t];
-            H.dominated = 1;
-            H.valid = 0;
-            H.nhits = 0;
-            H.first = -1;
-            H.last = -1;
-            H.ndf = 0;
-            ++n_dom;
+    for (int t0 = blockIdx.x * kDomWarps; t0 < n_st; t0 += gridDim.x * kDomWarps) {
+        const int t = t0 + w;
+        int keep = 0;
+        if (t < n_st) {
+            const int4 ch = L.tl_chain[t];
+            const int r0 = ch.y & 255, rk = ch.w;
+            if (rk - r0 + 1 >= L.min_chain) {
+                const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
+                bool all = true;
+                for (int r = r0 + lane; r <= rk; r += 32) all = all && L.mark[rowhit[r]];
+                if (__all_sync(0xffffffffu, all)) {
+                    if (lane == 0) {
+                        TrackletHdr& H = L.tl[t];
+                        H.dominated = 1;
+                        H.valid = 0;
+                        H.nhits = 0;
+                        H.first = -1;
+                        H.last = -1;
+                        H.ndf = 0;
+                        ++n_dom;
+                    }
+                } else {
+                    keep = 1;
+                }
+            }
         }
+        if (lane == 0) keep_s[w] = keep;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int c = 0;
+            for (int i = 0; i < kDomWarps; ++i) c += keep_s[i];
+            base_s = c ? atomicAdd(&L.cnt->n_bwd, c) : 0;
+        }
+        __syncthreads();
+        if (lane == 0 && keep) {
+            int off = base_s;
+            for (int i = 0; i < w; ++i) off += keep_s[i];
+            L.tl_list[off] = t;
+        }
+        __syncthreads();  // keep_s is rewritten by the next round
     }
     if (n_dom) {
         atomicAdd(&L.cnt->n_dominated, n_dom);
@@ -550,10 +579,10 @@ void launch_constructor(const Launch& L, const Schedule& S, void* stream_, const
     k_constructor<1><<<blocks, kTlThreads, 0, stream>>>(L);
     hook_after(hook, "k_constructor_fwd");
     {
-        int db = (L.t_cap + 7) / 8;
+        int db = (L.t_cap + kDomWarps - 1) / kDomWarps;
         if (db > n_sm * 16) db = n_sm * 16;
         if (db < 1) db = 1;
-        k_dominance<<<db, 256, 0, stream>>>(L);
+        k_dominance<<<db, 32 * kDomWarps, 0, stream>>>(L);
         hook_after(hook, "k_dominance");
     }
     k_constructor<2><<<blocks, kTlThreads, 0, stream>>>(L);

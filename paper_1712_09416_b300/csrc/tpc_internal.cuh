@@ -79,6 +79,7 @@ struct Counters {
     int tl_next;          // work counters of the persistent constructor passes
     int tl_next2;
     int n_dominated;      // chains whose tracklet is not built (dominated)
+    int n_bwd;            // chains listed for the backward pass
     int n_chain_hits;     // hits on the chains of all start hits
     int n_big_rows;       // rows above kSmallRowHits hits (listed for the large row sort)
     int n_mid_rows;       // rows for the block row sort of k_rowsort
@@ -88,7 +89,7 @@ struct Counters {
     int n_mg_tracks;      // merger: tracks after merging
     int max_row_hits;     // high-water marks: hits of the fullest (sector, row)
     int max_sector_tracks;  // ... and emitted tracks of the fullest sector
-    int pad[4];
+    int pad[3];
 };
 
 // Merger scratch: a sector track's outer state, and the refit of a chain
@@ -146,6 +147,7 @@ struct Launch {
     TrackletHdr* tl;            // [t_cap]
     int4* tl_chain;             // [t_cap] start hit, its sector << 8 | row, chain end hit, end row
     int* tl_rowhit;             // [t_cap * R] global hit index or -1
+    int* tl_list;               // [t_cap] chains listed for the backward pass
     unsigned long long* tl_key; // [t_cap] sector-local sort key or ~0
     int* tl_nown;               // [t_cap]
     unsigned* tl_own;           // [t_cap * kOwnWords] owned-row bits, 32 rows per word from first

@@ -99,6 +99,7 @@ struct Slot {
     TrackletHdr* tl;
     int4* tl_chain;
     int* tl_rowhit;
+    int* tl_list;
     int* upg;
     unsigned long long* tl_key;
     int *tl_nown, *tl_out, *tl_hitoff, *sec_trk_off, *sec_hit_off;
@@ -285,6 +286,7 @@ size_t layout(Slot& s, char* base)
     s.tl = (TrackletHdr*)take(sizeof(TrackletHdr) * (size_t)k.t);
     s.tl_chain = (int4*)take(16 * (size_t)k.t);
     s.tl_rowhit = (int*)take(4 * (size_t)k.t * k.r);
+    s.tl_list = (int*)take(4 * (size_t)k.t);
     s.upg = (int*)take(4 * k.n);
     s.tl_key = (unsigned long long*)take(8 * (size_t)k.t);
     s.tl_nown = (int*)take(4 * (size_t)k.t);
@@ -621,6 +623,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.tl = s.tl;
     L.tl_chain = s.tl_chain;
     L.tl_rowhit = s.tl_rowhit;
+    L.tl_list = s.tl_list;
     L.upg = s.upg;
     L.tl_key = s.tl_key;
     L.tl_nown = s.tl_nown;
