@@ -192,10 +192,14 @@ int tpc_track_batch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
  * results of the launch K before it (same slot), and the context's stream
  * does not wait for the launches until tpc_track_join.  While profiling is on
  * (tpc_track_set_profiling), launches run one at a time on the context's
- * stream.  tpc_track_batch drops every uncollected launch first. */
+ * stream.  tpc_track_batch drops every uncollected launch first.
+ * tpc_track_results writes one tpc_tracks per event of the collected launch
+ * into outs[0 .. cap-1]: a launch of more than cap events returns TPC_EINVAL
+ * and stays pending (outs may be NULL with any cap, to collect the status
+ * only). */
 int tpc_track_launch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev,
                      const tpc_geometry* geom, float bz_tesla);
-int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs);
+int tpc_track_results(tpc_track_ctx* ctx, int cap, tpc_tracks* outs);
 
 /* Make the context's stream wait for every launch enqueued so far (on all
  * slots); never blocks the host.  Work the caller enqueues on the context's

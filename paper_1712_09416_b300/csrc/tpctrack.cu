@@ -1267,12 +1267,15 @@ int tpc_track_join(tpc_track_ctx* ctx)
     return TPC_OK;
 }
 
-int tpc_track_results(tpc_track_ctx* ctx, tpc_tracks* outs)
+int tpc_track_results(tpc_track_ctx* ctx, int cap, tpc_tracks* outs)
 {
     if (!ctx) return TPC_EINVAL;
     cudaSetDevice(ctx->cfg.device);
     if (ctx->direct.empty()) return fail(ctx, TPC_EINVAL, "no launch pending");
     const int j = ctx->direct.front();
+    if (outs && cap < ctx->slots[j]->info.n_ev)
+        return fail(ctx, TPC_EINVAL, "outs holds fewer entries than the launch has events (" +
+                                         std::to_string(ctx->slots[j]->info.n_ev) + ")");
     ctx->direct.pop_front();
     ctx->last_slot = j;
     Slot& s = *ctx->slots[j];
@@ -1296,7 +1299,7 @@ int tpc_track_batch(tpc_track_ctx* ctx, int n_ev, const tpc_clusters* ev, const 
             for (int e = 0; e < n_ev; ++e) outs[e] = tpc_tracks{};
         return rc;
     }
-    return tpc_track_results(ctx, outs);
+    return tpc_track_results(ctx, n_ev, outs);
 }
 
 int tpc_track_event(tpc_track_ctx* ctx, const tpc_clusters* ev, const tpc_geometry* geom, float bz,

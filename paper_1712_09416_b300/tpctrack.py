@@ -149,7 +149,7 @@ def lib():
                                       C.c_float, C.POINTER(tpc_tracks)]
         L.tpc_track_launch.argtypes = [P, C.c_int, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry),
                                        C.c_float]
-        L.tpc_track_results.argtypes = [P, C.POINTER(tpc_tracks)]
+        L.tpc_track_results.argtypes = [P, C.c_int, C.POINTER(tpc_tracks)]
         L.tpc_track_join.argtypes = [P]
         L.tpc_track_submit.argtypes = [P, C.POINTER(tpc_clusters), C.POINTER(tpc_geometry), C.c_float,
                                        C.POINTER(C.c_uint64)]
@@ -353,8 +353,10 @@ def tpc_track_launch(ctx, clusters: list[tpc_clusters], geom: tpc_geometry, bz: 
 
 
 def tpc_track_results(ctx, n_ev: int, *, copy: bool = True):
+    """Tracks of the oldest pending launch, which must have n_ev events or
+    fewer (TPC_EINVAL otherwise, the launch staying pending)."""
     outs = (tpc_tracks * n_ev)()
-    _check(ctx, lib().tpc_track_results(ctx, outs))
+    _check(ctx, lib().tpc_track_results(ctx, n_ev, outs))
     return [tracks_to_numpy(o) for o in outs] if copy else outs
 
 

@@ -326,6 +326,15 @@ def test_launches_on_several_streams_give_the_same_tracks(tp):
         done.synchronize()  # after the join: every launch has finished
         for k in (1, 2, 3):
             same(ref[k], tp.tpc_track_results(t.ctx, 1)[0], ("after join", k))
+        # a two-event launch collected into room for one event: refused, and
+        # the launch stays pending until collected with room for both
+        tp.tpc_track_launch(t.ctx, [cs[1][0], cs[2][0]], g, bz)
+        with pytest.raises(tp.TpcError) as err:
+            tp.tpc_track_results(t.ctx, 1)
+        assert err.value.code == tp.TPC_EINVAL
+        two = tp.tpc_track_results(t.ctx, 2)
+        same(ref[1], two[0], "two events, first")
+        same(ref[2], two[1], "two events, second")
         # batch and single-event calls still work and drop nothing they need
         same(ref[5], t.event(evs[5]), "event")
         tuned = tp.tpc_track_autotune(t.ctx, [cs[6][0]], g, bz, reps=1)
