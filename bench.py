@@ -115,6 +115,7 @@ KERNEL_BYTES = {"k_count": 12, "k_rowscan": 4, "k_scatter": 24, "k_rowsort": 0,
                 "k_constructor_bwd": 8.7 * F_A, "k_weights": 8 + 16 * F_A,
                 "k_sel_decide": 12 * F_A, "k_sel_sort": 0.7, "k_sel_write": 4 * F_A}
 ROOFLINE_TARGET = 0.40  # share of the HBM roofline asked of the path
+EPL_CANDIDATES = (1, 2, 4, 8)  # central events per launch tried for the timed step
 
 
 def stage_bytes_per_cluster(kernel: str) -> float:
@@ -927,23 +928,66 @@ def run_ours(args):
     # are recorded on it (torch's default stream is the legacy stream 0, for
     # which the library would create a separate non-blocking stream)
     stream = torch.cuda.Stream()
-    # four slots: the autotuner may spread consecutive steps over up to four
-    # streams, so that one event's kernels overlap the next one's
-    ctx = tp.tpc_track_create(n + 65536, max_events_per_launch=1, max_events_in_flight=8,
-                              cuda_stream=stream.cuda_stream)
-    # launch schedule picked by the autotuner on this workload (untimed)
+
+    def make_ctx(epl):
+        # up to eight slots in all: the autotuner may spread consecutive
+        # launches over several streams, so that one launch's kernels overlap
+        # the next one's
+        return tp.tpc_track_create(epl * n + 65536, max_events_per_launch=epl,
+                                   max_events_in_flight=max(2, 8 // epl),
+                                   cuda_stream=stream.cuda_stream)
+
+    def launch_events(epl, i):
+        # launch i takes the device copies i*epl .. i*epl+epl-1 (in turn)
+        return [cls[(i * epl + j) % N_COPIES][0] for j in range(epl)]
+
+    # events per launch (the batched form on central events, Sect. 2: many
+    # events in flight): each candidate's context is autotuned, then timed on
+    # a burst of launches; the fastest is the step of the timed region
+    epl_sweep = {}
     if args.no_autotune:
+        epl = 1
+        ctx = make_ctx(1)
         schedule = tp.tpc_track_get_schedule(ctx)
     else:
-        schedule = tp.tpc_track_autotune(ctx, [cls[0][0]], geom, bz, reps=3)
+        best = None
+        for cand in EPL_CANDIDATES:
+            c = make_ctx(cand)
+            sch = tp.tpc_track_autotune(c, launch_events(cand, 0), geom, bz, reps=3)
+            for i in range(4):
+                tp.tpc_track_launch(c, launch_events(cand, i), geom, bz)
+                tp.tpc_track_results(c, cand, copy=False)
+            k_burst = max(16, 96 // cand)
+            torch.cuda.synchronize()
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            for i in range(k_burst):
+                tp.tpc_track_launch(c, launch_events(cand, i), geom, bz)
+            tp.tpc_track_join(c)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            for _ in range(sch["streams"]):
+                tp.tpc_track_results(c, cand, copy=False)
+            rate = k_burst * cand * n / (b0.elapsed_time(b1) * 1e-3)
+            epl_sweep[cand] = {"clusters_per_s": rate, "streams": sch["streams"],
+                               "tl_blocks_per_sm": sch["tl_blocks_per_sm"]}
+            if best is None or rate > best[0]:
+                if best is not None:
+                    tp.tpc_track_destroy(best[1])
+                best = (rate, c, cand, sch)
+            else:
+                tp.tpc_track_destroy(c)
+        _, ctx, epl, schedule = best
     n_streams = schedule["streams"]
+    n_step = epl * n  # clusters of one step (one launch)
 
     def step(i):
-        tp.tpc_track_launch(ctx, [cls[i % N_COPIES][0]], geom, bz)
+        tp.tpc_track_launch(ctx, launch_events(epl, i), geom, bz)
 
     for i in range(args.warmup):
         step(i)
-        tp.tpc_track_results(ctx, 1, copy=False)
+        tp.tpc_track_results(ctx, epl, copy=False)
     counters = tp.tpc_track_get_counters(ctx)
 
     def barrier():
@@ -968,7 +1012,7 @@ def run_ours(args):
     clk.mark("timed_end")
     ms_total = e0.elapsed_time(e1)
     for _ in range(n_streams):  # status of the last step of every slot
-        tp.tpc_track_results(ctx, 1, copy=False)
+        tp.tpc_track_results(ctx, epl, copy=False)
     # hold: the same steps for about a second more (untimed), so that the
     # clock record covers the load even when the timed region is shorter
     # than nvidia-smi's 200 ms sampling period
@@ -981,7 +1025,7 @@ def run_ours(args):
         tp.tpc_track_join(ctx)
         torch.cuda.synchronize()
         for _ in range(min(16, n_streams)):
-            tp.tpc_track_results(ctx, 1, copy=False)
+            tp.tpc_track_results(ctx, epl, copy=False)
     clk.mark("end")
     clk.__exit__()
     # the same steps on 1..max streams with the tuned grid shapes (outside the
@@ -1004,20 +1048,20 @@ def run_ours(args):
             s1.record(stream)
             torch.cuda.synchronize()
             for _ in range(k):
-                tp.tpc_track_results(ctx, 1, copy=False)
-            streams_sweep[k] = s0.elapsed_time(s1) / n_sw
+                tp.tpc_track_results(ctx, epl, copy=False)
+            streams_sweep[k] = s0.elapsed_time(s1) / n_sw / epl
         tp.tpc_track_set_schedule(ctx, **schedule)
     # per-kernel device times: the same steps again, kernels launched one by
     # one with a CUDA event after each (outside the timed region)
     tp.tpc_track_set_profiling(ctx, True)
     for i in range(args.steps):
         step(i)
-    tp.tpc_track_results(ctx, 1, copy=False)
+    tp.tpc_track_results(ctx, epl, copy=False)
     ktimes = tp.tpc_track_kernel_times(ctx)
     tp.tpc_track_set_profiling(ctx, False)
     ms_total = replica_time(ms_total, world)
     ms_step = ms_total / args.steps
-    value = job_throughput(n * args.steps, world, ms_total)
+    value = job_throughput(n_step * args.steps, world, ms_total)
     launches = sum(v[1] for v in ktimes.values())
 
     # roofline of the dominant kernel: the algorithmic bytes of its step of
@@ -1028,11 +1072,11 @@ def run_ours(args):
     peak, peak_src = peaks()
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     dom_ms = ktimes[dom][0] / ktimes[dom][1]
-    dom_bytes = stage_bytes_per_cluster(dom) * n
+    dom_bytes = stage_bytes_per_cluster(dom) * n_step
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    b_impl = sum(kb.values()) / n
+    b_impl = sum(kb.values()) / n_step
     # I/O-only lower bound: the clusters in (12 B) and the tracks out
-    io_b = (12 * n + 100 * counters["n_tracks"] + 4 * counters["n_track_hits"]) / n
+    io_b = (12 * n_step + 100 * counters["n_tracks"] + 4 * counters["n_track_hits"]) / n_step
 
     # end to end through the C ABI with pinned host inputs
     pinned = [torch.from_numpy(ev.y).pin_memory(), torch.from_numpy(ev.z).pin_memory(),
@@ -1116,7 +1160,7 @@ def run_ours(args):
     merged = None
     if not args.no_merge and rank == 0:
         try:
-            merged = merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, ms_step,
+            merged = merge_section(tp, torch, synth, stream, cls, ev, geom, bz, n, ms_step / epl,
                                    steps=max(20, min(200, args.steps)), tune=not args.no_autotune)
         except Exception as e:  # reported, the bench line still goes out
             merged = {"error": repr(e)}
@@ -1139,17 +1183,21 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "clusters_per_event": n,
+                       "events_per_launch": epl, "clusters_per_step": n_step,
+                       "events_per_launch_sweep": epl_sweep,
                        "l2": f"inputs rotate over {N_COPIES} device copies "
-                             f"({N_COPIES * 12 * n / 1e6:.0f} MB) > 126 MB L2; each step also "
-                             "writes ~150 MB of intermediate arrays",
+                             f"({N_COPIES * 12 * n / 1e6:.0f} MB) > 126 MB L2; each event "
+                             "also writes ~150 MB of intermediate arrays",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "launch": f"one CUDA graph per step ({len(ktimes)} kernels); consecutive steps "
-                                 f"spread over {n_streams} stream(s) so that their kernels run "
-                                 "concurrently (autotuned); kernel times from a separate pass "
-                                 "with kernels launched one by one on one stream",
+                       "launch": f"one CUDA graph per step ({len(ktimes)} kernels) over {epl} "
+                                 f"central event(s) side by side (events per launch picked "
+                                 f"by a timed burst of each of {list(EPL_CANDIDATES)}); "
+                                 f"consecutive steps spread over {n_streams} stream(s) so that "
+                                 "their kernels run concurrently (autotuned); kernel times from "
+                                 "a separate pass with kernels launched one by one on one stream",
                        "schedule": schedule,
-                       "tracks_per_event": counters["n_tracks"],
-                       "tracklets_per_event": counters["n_tracklets"],
+                       "tracks_per_event": counters["n_tracks"] / epl,
+                       "tracklets_per_event": counters["n_tracklets"] / epl,
                        "fullest_row_hits": counters["max_row_hits"],
                        "fullest_sector_tracks": counters["max_sector_tracks"]},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -1158,7 +1206,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": dom_bytes,
                          "algorithmic_bytes_per_cluster": stage_bytes_per_cluster(dom),
                          "stage": KERNEL_STAGE[dom], "launch_ms": dom_ms,
-                         "stages": stage_rooflines(ktimes, n, peak),
+                         "stages": stage_rooflines(ktimes, n_step, peak),
                          "impl_bytes_per_launch": kb[dom],
                          "frac_impl_bytes": kb[dom] / (dom_ms * 1e-3) / 1e9 / peak},
             "path_roofline": {"bytes_per_cluster": PATH_BYTES,
