@@ -946,12 +946,12 @@ def run_ours(args):
     # a burst of launches; the fastest is the step of the timed region
     epl_sweep = {}
     if args.no_autotune:
-        epl = 1
-        ctx = make_ctx(1)
+        epl = max(1, args.events_per_launch)
+        ctx = make_ctx(epl)
         schedule = tp.tpc_track_get_schedule(ctx)
     else:
         best = None
-        for cand in EPL_CANDIDATES:
+        for cand in ([args.events_per_launch] if args.events_per_launch > 0 else EPL_CANDIDATES):
             c = make_ctx(cand)
             sch = tp.tpc_track_autotune(c, launch_events(cand, 0), geom, bz, reps=3)
             for i in range(4):
@@ -1291,6 +1291,9 @@ def main():
                     help="event-stream sweep: 4 rates x <=300 events (short) or the 8 rates "
                          "10-2000/s with 30 s or 2000 events each (full)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--events-per-launch", type=int, default=0,
+                    help="central events per timed launch (0: pick from %s by a timed burst)"
+                         % (EPL_CANDIDATES,))
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("warmup raised to 3")
