@@ -932,10 +932,11 @@ def run_ours(args):
     def make_ctx(epl):
         # up to eight slots in all: the autotuner may spread consecutive
         # launches over several streams, so that one launch's kernels overlap
-        # the next one's
+        # the next one's (one slot without the autotuner: one stream, and the
+        # least device memory for a profiler capture)
+        slots = 1 if args.no_autotune else max(2, 8 // epl)
         return tp.tpc_track_create(epl * n + 65536, max_events_per_launch=epl,
-                                   max_events_in_flight=max(2, 8 // epl),
-                                   cuda_stream=stream.cuda_stream)
+                                   max_events_in_flight=slots, cuda_stream=stream.cuda_stream)
 
     def launch_events(epl, i):
         # launch i takes the device copies i*epl .. i*epl+epl-1 (in turn)
