@@ -154,7 +154,7 @@ def kernel_bytes(c: dict) -> dict:
         "k_chains": 8 * c["n_chain_hits"] + 32 * T,
         # forward passes of every chain, backward passes of the chains kept
         "k_constructor_fwd": 12 * (c["n_chain_hits"] + Th) + 40 * (Tl + c["n_dominated_chains"]),
-        "k_dominance": 8 * c["n_chain_hits"],
+        "k_dominance": 16 * T + 5 * c["n_chain_hits"],
         "k_constructor_bwd": 16 * Th + 116 * Tl,
         "k_weights": 20 * Th + 32 * Tl,
         "k_sel_decide": 10 * Th + 32 * T,

@@ -12,9 +12,14 @@
 // their track outward).  k_constructor<2> refits the remaining chains
 // backward from the last hit with the covariance reset to the seed, picking
 // up hits below the chain the same way; the result is the state and
-// covariance at the innermost hit.  The 5-vector and the 15 covariance
-// entries live in registers; the forward hit list lives in the tracklet's
-// rowhit slot and the inputs of the next row are loaded one step ahead.
+// covariance at the innermost hit.  The 5-vector and the covariance live in
+// registers: the forward pass carries the 15 entries of C, the backward pass
+// a square-root factor U (C = U U^T, 25 entries; tpc_fit.cuh), which keeps
+// the binary32 result within a small fraction of the parity bars where the
+// update of C itself loses the digits the innermost state depends on.  The
+// forward hit list lives in the tracklet's rowhit slot and the inputs of the
+// next row are loaded one step ahead; the first update of a pass runs inside
+// the common row step, with no transport.
 // k_weights: valid tracklets raise the weight of their hits to the key
 // (nHits << 32 | ~cid(h0)) with atomicMax.
 //
@@ -25,11 +30,15 @@
 //   dS^2 [ (s1/c1) sinc^2(dphi/2) / 2 + (sin dphi - dphi)/dphi^2 ],  dphi = C_k dS,
 // a form without cancellation as C_k -> 0.
 // Bytes: k_chains 8 per chain hit (link read, rowhit write) + 32 per start;
+// k_dominance 16 per chain + 5 per chain hit read (rowhit, mark);
 // forward pass per hit y z 8 + rowhit 4 (+ a mark byte per extension hit),
 // backward pass per hit y z 8 + rowhit 4 (read) + 4 (written), about 116 per
 // tracklet (chain record, header); k_weights per assigned hit rowhit 4 +
 // weight read-modify-write 16.
 #include <cuda_runtime.h>
+
+#include <atomic>
+#include <type_traits>
 
 #include "tpc_internal.cuh"
 #include "tpc_fit.cuh"
@@ -40,14 +49,16 @@ namespace {
 
 constexpr int kTlThreads = 64;
 
-__device__ __forceinline__ bool outside(const Fit& f, float yref, float zref, const Launch& L)
+template <class FitT>
+__device__ __forceinline__ bool outside(const FitT& f, float yref, float zref, const Launch& L)
 {
     return fabsf(f.p[0] + yref) > f.x * L.tan_half + L.edge_margin ||
            fabsf(f.p[1] + zref) > L.z_max + L.edge_margin;
 }
 
 // Candidates ka..kb-1 (global sorted indices) in batches of four loads.
-__device__ __forceinline__ void scan_range(const Fit& f, float yref, float zref, int ka, int kb,
+template <class FitT>
+__device__ __forceinline__ void scan_range(const FitT& f, float yref, float zref, int ka, int kb,
                                            float S00, float S01, float S11, float id,
                                            const Launch& L, float& best, int& bk, float& by,
                                            float& bzv)
@@ -83,11 +94,12 @@ __device__ __forceinline__ void scan_range(const Fit& f, float yref, float zref,
 // bounds the chi2 ellipse is tried.  When the box spans at most two z-bins
 // (nearly always: bins are several cm wide, the box a few mm) the four bin
 // offsets are read at once and the two hit ranges walked as one list.
-__device__ __forceinline__ int search(const Fit& f, float yref, float zref, const RowGrid& G,
+template <class FitT>
+__device__ __forceinline__ int search(const FitT& f, float yref, float zref, const RowGrid& G,
                                       int base, const Launch& L, float& my, float& mz)
 {
-    const float* C = f.C;
-    const float S00 = C[0] + L.sy2, S01 = C[1], S11 = C[2] + L.sz2;
+    float S00, S01, S11;
+    meas_cov(f, L, S00, S01, S11);
     const float id = __fdividef(1.0f, S00 * S11 - S01 * S01);
     const float wy = 1.01f * sqrtf(L.chi2_hit * S00) + 1e-3f;
     const float wz = 1.01f * sqrtf(L.chi2_hit * S11) + 1e-3f;
@@ -139,6 +151,20 @@ __device__ __forceinline__ int search(const Fit& f, float yref, float zref, cons
     my = by;
     mz = bzv;
     return (bk >= 0 && best <= L.chi2_hit) ? bk : -1;
+}
+
+// Result of the backward pass: x, state and covariance (C = U U^T, lower
+// triangle) into the lane's column of the shared array best[21][blockDim].
+template <class FitT>
+__device__ __forceinline__ void save_best(const FitT& f, float (*best)[kTlThreads])
+{
+    float C[15];
+    cov_of(f, C);
+    best[0][threadIdx.x] = f.x;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) best[1 + i][threadIdx.x] = f.p[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) best[6 + i][threadIdx.x] = C[i];
 }
 
 // One thread per start hit: follow its chain of cleaned up-links, record the
@@ -205,8 +231,18 @@ __global__ void __launch_bounds__(kChThreads) k_chains(Launch L)
 // header; PASS 2 (after k_dominance) runs the backward passes (assigned hits,
 // then search below the chain) of the chains k_dominance listed (those not
 // dominated).
+// Minimum resident blocks per SM the register allocation aims at, per pass
+// (the forward pass fits ten 64-thread blocks per SM without spills).
+#ifndef TPC_TL_MINB1
+#define TPC_TL_MINB1 10
+#endif
+#ifndef TPC_TL_MINB2
+#define TPC_TL_MINB2 1
+#endif
+
 template <int PASS>
-__global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
+__global__ void __launch_bounds__(kTlThreads, PASS == 1 ? TPC_TL_MINB1 : TPC_TL_MINB2)
+    k_constructor(Launch L)
 {
     if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     __shared__ float best_s[21][kTlThreads];  // state + covariance at the innermost backward hit
@@ -227,7 +263,12 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
     // small numbers carry the per-step rounding of binary32 far below the
     // resolution; measurements are shifted by the same reference
     float yref = 0.0f, zref = 0.0f;
-    Fit f;
+    // The forward pass carries the covariance itself; the backward pass, whose
+    // state is the result, carries a square-root factor (C = U U^T): for
+    // short tracklets whose seed variances collapse by orders of magnitude
+    // the binary32 update of C itself loses the digits that the parameters
+    // at the innermost hit depend on.
+    typename std::conditional<PASS == 1, Fit, FitSR>::type f;
     // The tracklet's rowhit slot holds the hit of every row the forward pass
     // visits (global index, -1 none); the backward pass reads it ahead and
     // rewrites it in place.
@@ -258,6 +299,15 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
     };
 
     bool exhausted = false;  // no start hit left for this lane
+    // The first step of a pass (row r0 forward, row `last` backward) is an
+    // update at a known hit without a transport; it runs inside the common
+    // row step, so that the warp stays converged through the update.
+    bool skip_tr = false;
+    // f is the state right after the latest update (no transport since).
+    // The result of a pass is that state: it is stored (PL forward, BEST
+    // backward) only before a step that may leave it without an update (a
+    // row to search, or a known row without a hit), and at the end.
+    bool fresh = false;
     for (;;) {
         // every lane stays in the loop until the whole warp is done, and the
         // warp reconverges here at the top of each row step
@@ -297,60 +347,52 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             }
             rowhit = L.tl_rowhit + (size_t)t * L.R;
             const float2 c0 = L.hyz[ch.x];
+            yref = c0.x;
+            zref = c0.y;
+            gap = 0;
+            fresh = false;
+            skip_tr = true;
+            pknown = true;
             if (PASS == 2) {
-                const TrackletHdr& H = L.tl[t];
                 // backward from the last hit with the covariance reset to the
-                // seed, starting from the forward state left in the header
-                yref = c0.x;
-                zref = c0.y;
+                // seed, starting from the forward state left in the header;
+                // the first step updates at the last hit
+                const TrackletHdr& H = L.tl[t];
                 last = H.last;
 #pragma unroll
                 for (int i = 0; i < 5; ++i) f.p[i] = H.p[i];
                 seed_cov(f, L);
                 f.x = xs[last];
-                const float2 c = L.hyz[rowhit[last]];
-                chi2 = update(f, c.x - yref, c.y - zref, L);
-                nupd = 1;
+                ph = rowhit[last];
+                pyz = L.hyz[ph];
+                ph2 = last - 1 >= r0 ? rowhit[last - 1] : -1;
+                chi2 = 0.0f;
+                nupd = 0;
                 first = last;
-                BEST(0) = f.x;
-#pragma unroll
-                for (int i = 0; i < 5; ++i) BEST(1 + i) = f.p[i];
-#pragma unroll
-                for (int i = 0; i < 15; ++i) BEST(6 + i) = f.C[i];
-                gap = 0;
                 phase = 2;
-                r = last - 1;
-                if (r >= 0) {
-                    ph2 = r >= r0 ? rowhit[r] : -1;
-                    stage(r, false);
-                }
-                continue;
+                r = last;
+            } else {
+                // seed from the chord h0 -> hk; the first step updates at h0
+                const int h1 = rk > r0 ? rowhit[r0 + 1] : -1;
+                const float2 ck = L.hyz[ch.z];
+                const float x0 = xs[r0], x1 = xs[rk];
+                const float tphi = (ck.x - c0.x) / (x1 - x0);
+                const float dzdx = (ck.y - c0.y) / (x1 - x0);
+                const float cphi = rsqrtf(1.0f + tphi * tphi);
+                f.x = x0;
+                f.p[0] = 0.0f;
+                f.p[1] = 0.0f;
+                f.p[2] = tphi * cphi;
+                f.p[3] = dzdx * cphi;
+                f.p[4] = 0.0f;
+                seed_cov(f, L);
+                ph = ch.x;
+                pyz = c0;
+                ph2 = h1;
+                last = r0;
+                phase = 1;
+                r = r0;
             }
-            const int h1 = rk > r0 ? rowhit[r0 + 1] : -1;
-            // seed from the chord h0 -> hk, update at h0
-            const float2 ck = L.hyz[ch.z];
-            const float x0 = xs[r0], x1 = xs[rk];
-            const float tphi = (ck.x - c0.x) / (x1 - x0);
-            const float dzdx = (ck.y - c0.y) / (x1 - x0);
-            const float cphi = rsqrtf(1.0f + tphi * tphi);
-            yref = c0.x;
-            zref = c0.y;
-            f.x = x0;
-            f.p[0] = 0.0f;
-            f.p[1] = 0.0f;
-            f.p[2] = tphi * cphi;
-            f.p[3] = dzdx * cphi;
-            f.p[4] = 0.0f;
-            seed_cov(f, L);
-            update(f, 0.0f, 0.0f, L);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) PL(i) = f.p[i];
-            last = r0;
-            gap = 0;
-            r = r0 + 1;
-            phase = 1;
-            ph2 = h1;
-            if (r < L.R) stage(r, true);
         }
         // ---- one row step of the current pass ----
         constexpr bool fwd = PASS == 1;
@@ -363,9 +405,23 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             int h = known ? ph : -1;
             const int rn = fwd ? r + 1 : r - 1;
             if (fwd ? rn < L.R : rn >= 0) stage(rn, fwd);
-            if (!transport(f, xs[r], L)) {
-                end_pass = true;
-            } else {
+            if (!skip_tr) {
+                if (fresh && !(known && h >= 0)) {
+                    // the step may leave the state of the latest update
+                    if (fwd) {
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) PL(i) = f.p[i];
+                    } else {
+                        save_best(f, best_s);
+                    }
+                    fresh = false;
+                }
+                // a failed transport leaves f as it was
+                if (!transport(f, xs[r], L)) end_pass = true;
+                else fresh = false;
+            }
+            skip_tr = false;
+            if (!end_pass) {
                 if (!known) {
                     if (outside(f, yref, zref, L)) end_pass = true;
                     else h = search(f, yref, zref, G, base, L, my, mz);
@@ -373,24 +429,18 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
                 if (!end_pass) {
                     if (h >= 0) {
                         const float dchi2 = update(f, my, mz, L);
+                        fresh = true;
                         if (fwd) {
                             if (!known) {
                                 rowhit[r] = h;
                                 L.mark[h] = 1;  // taken by a forward extension search
                             }
                             last = r;
-#pragma unroll
-                            for (int i = 0; i < 5; ++i) PL(i) = f.p[i];
                         } else {
                             chi2 += dchi2;
                             ++nupd;
-                            rowhit[r] = h;
+                            if (!known) rowhit[r] = h;  // a known row holds h already
                             first = r;
-                            BEST(0) = f.x;
-#pragma unroll
-                            for (int i = 0; i < 5; ++i) BEST(1 + i) = f.p[i];
-#pragma unroll
-                            for (int i = 0; i < 15; ++i) BEST(6 + i) = f.C[i];
                         }
                         if (!known) gap = 0;
                     } else {
@@ -410,13 +460,19 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
             // forward pass done: the state at the last hit (relative to the
             // start hit) and the last row wait in the header for PASS 2
             TrackletHdr& H = L.tl[t];
+            if (fresh) {
 #pragma unroll
-            for (int i = 0; i < 5; ++i) H.p[i] = PL(i);
+                for (int i = 0; i < 5; ++i) H.p[i] = f.p[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 5; ++i) H.p[i] = PL(i);
+            }
             H.last = last;
             t = -1;
             phase = 0;
             continue;
         }
+        if (fresh) save_best(f, best_s);
         // tracklet done: header (the hit weights are raised by k_weights)
         bool fin = isfinite(chi2);
 #pragma unroll
@@ -460,68 +516,67 @@ __global__ void __launch_bounds__(kTlThreads) k_constructor(Launch L)
     }
 }
 
-// Dominance: one warp per chain, lanes over its rows.  A chain all of whose
-// hits were taken by forward extension searches (of other tracklets: a
-// tracklet's own extension starts above its chain) gets no tracklet; its
-// header is made final here.  The other chains long enough for a tracklet
-// are listed for the backward pass (one atomic per block of eight chains):
-// its warps then hold only tracklets to refit, which issues fewer warp
-// instructions when several events share the GPU (one event alone gets
-// slightly slower, as full warps diverge more per row step).
-constexpr int kDomWarps = 8;
-
-__global__ void __launch_bounds__(32 * kDomWarps) k_dominance(Launch L)
+// Dominance: one thread per chain.  A chain long enough for a tracklet all
+// of whose hits were taken by forward extension searches (of other
+// tracklets: a tracklet's own extension starts above its chain) gets no
+// tracklet and its header is made final; the others are listed for the
+// backward pass (warp-aggregated), whose warps then hold only tracklets to
+// refit.  The hits are read four rows at a time (independent loads) and the
+// scan stops at the first hit no extension took.
+__global__ void k_dominance(Launch L)
 {
     if (L.cnt->timeout) return;  // an earlier bounded wait gave up
-    __shared__ int keep_s[kDomWarps];
-    __shared__ int base_s;
     const int n_st = min(L.cnt->n_starts, L.t_cap);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
     int n_dom = 0;
-    for (int t0 = blockIdx.x * kDomWarps; t0 < n_st; t0 += gridDim.x * kDomWarps) {
-        const int t = t0 + w;
-        int keep = 0;
+    // whole warps step together (ballot below)
+    for (int t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n_st; t0 += stride) {
+        const int t = t0 + lane;
+        bool keep = false;
         if (t < n_st) {
             const int4 ch = L.tl_chain[t];
             const int r0 = ch.y & 255, rk = ch.w;
             if (rk - r0 + 1 >= L.min_chain) {
                 const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
-                bool all = true;
-                for (int r = r0 + lane; r <= rk; r += 32) all = all && L.mark[rowhit[r]];
-                if (__all_sync(0xffffffffu, all)) {
-                    if (lane == 0) {
-                        TrackletHdr& H = L.tl[t];
-                        H.dominated = 1;
-                        H.valid = 0;
-                        H.nhits = 0;
-                        H.first = -1;
-                        H.last = -1;
-                        H.ndf = 0;
-                        ++n_dom;
-                    }
-                } else {
-                    keep = 1;
+                for (int r = r0; r <= rk && !keep; r += 4) {
+                    int h[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) h[j] = r + j <= rk ? rowhit[r + j] : -1;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (h[j] >= 0 && !L.mark[h[j]]) keep = true;
+                }
+                if (!keep) {
+                    TrackletHdr& H = L.tl[t];
+                    H.dominated = 1;
+                    H.valid = 0;
+                    H.nhits = 0;
+                    H.first = -1;
+                    H.last = -1;
+                    H.ndf = 0;
+                    ++n_dom;
                 }
             }
         }
-        if (lane == 0) keep_s[w] = keep;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int c = 0;
-            for (int i = 0; i < kDomWarps; ++i) c += keep_s[i];
-            base_s = c ? atomicAdd(&L.cnt->n_bwd, c) : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            int b = 0;
+            if (lane == leader) b = atomicAdd(&L.cnt->n_bwd, __popc(m));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (keep) L.tl_list[b + __popc(m & ((1u << lane) - 1))] = t;
         }
-        __syncthreads();
-        if (lane == 0 && keep) {
-            int off = base_s;
-            for (int i = 0; i < w; ++i) off += keep_s[i];
-            L.tl_list[off] = t;
-        }
-        __syncthreads();  // keep_s is rewritten by the next round
     }
-    if (n_dom) {
-        atomicAdd(&L.cnt->n_dominated, n_dom);
-        atomicSub(&L.cnt->n_tracklets, n_dom);
+    // block totals
+    __shared__ int red;
+    if (threadIdx.x == 0) red = 0;
+    __syncthreads();
+    if (n_dom) atomicAdd(&red, n_dom);
+    __syncthreads();
+    if (threadIdx.x == 0 && red) {
+        atomicAdd(&L.cnt->n_dominated, red);
+        atomicSub(&L.cnt->n_tracklets, red);
     }
 }
 
@@ -548,13 +603,27 @@ __global__ void k_weights(Launch L)
 
 }  // namespace
 
+// Resident blocks per SM of each constructor pass (the passes have
+// different register counts; each is capped by its own).
+static int pass_occupancy(int pass)
+{
+    int a = 0;
+    if (pass == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_constructor<1>, kTlThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_constructor<2>, kTlThreads, 0);
+    return a < 1 ? 1 : a;
+}
+
+// The schedule's range of constructor blocks per SM: up to the larger of
+// the two passes' occupancies.
+// (Queried when a context is created, before any stream capture.)
+static std::atomic<int> g_occ1{0}, g_occ2{0};
+
 int constructor_occupancy()
 {
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_constructor<1>, kTlThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_constructor<2>, kTlThreads, 0);
-    const int per_sm = a < b ? a : b;
-    return per_sm < 1 ? 1 : per_sm;
+    const int a = pass_occupancy(1), b = pass_occupancy(2);
+    g_occ1 = a;
+    g_occ2 = b;
+    return a > b ? a : b;
 }
 
 void launch_constructor(const Launch& L, const Schedule& S, void* stream_, const KernelHook* hook)
@@ -572,20 +641,23 @@ void launch_constructor(const Launch& L, const Schedule& S, void* stream_, const
         k_chains<<<(int)cb, kChThreads, 0, stream>>>(L);
         hook_after(hook, "k_chains");
     }
-    int blocks = per_sm * n_sm;
+    const int occ1 = g_occ1 > 0 ? (int)g_occ1 : per_sm, occ2 = g_occ2 > 0 ? (int)g_occ2 : per_sm;
     const int need = (L.t_cap + kTlThreads - 1) / kTlThreads;
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    k_constructor<1><<<blocks, kTlThreads, 0, stream>>>(L);
+    auto grid = [&](int occ) {
+        int b = (per_sm < occ ? per_sm : occ) * n_sm;
+        if (b > need) b = need;
+        return b < 1 ? 1 : b;
+    };
+    k_constructor<1><<<grid(occ1), kTlThreads, 0, stream>>>(L);
     hook_after(hook, "k_constructor_fwd");
     {
-        int db = (L.t_cap + kDomWarps - 1) / kDomWarps;
-        if (db > n_sm * 16) db = n_sm * 16;
+        int db = (L.t_cap + 255) / 256;
+        if (db > n_sm * 8) db = n_sm * 8;
         if (db < 1) db = 1;
-        k_dominance<<<db, 32 * kDomWarps, 0, stream>>>(L);
+        k_dominance<<<db, 256, 0, stream>>>(L);
         hook_after(hook, "k_dominance");
     }
-    k_constructor<2><<<blocks, kTlThreads, 0, stream>>>(L);
+    k_constructor<2><<<grid(occ2), kTlThreads, 0, stream>>>(L);
     hook_after(hook, "k_constructor_bwd");
     int wblocks = (L.t_cap + 7) / 8;
     if (wblocks > n_sm * 16) wblocks = n_sm * 16;

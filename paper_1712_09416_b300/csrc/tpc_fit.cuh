@@ -29,11 +29,21 @@ __device__ __forceinline__ float cget(const float* C, int i, int j)
     return i >= j ? C[CI(i, j)] : C[CI(j, i)];
 }
 
-__device__ __forceinline__ bool transport(Fit& f, float x1, const Launch& L)
+// Transport of the state (x, p) to the plane x1: the new state and the
+// non-trivial entries of the Jacobian J = d(p1)/d(p0), which differs from
+// the identity in dy/ds = a, dy/d(q/pT) = b, dz/ds = c, dz/dt = d,
+// dz/d(q/pT) = e and ds/d(q/pT) = g.  Returns false, leaving the state as it
+// was, when |sin phi| would reach sin_max.
+struct Jac {
+    float a, b, c, d, e, g;
+};
+
+__device__ __forceinline__ bool transport_state(float& x, float* p, float x1, const Launch& L,
+                                                Jac& J)
 {
-    const float dx = x1 - f.x;
-    const float ck = -L.kB * f.p[4];
-    const float s0 = f.p[2];
+    const float dx = x1 - x;
+    const float ck = -L.kB * p[4];
+    const float s0 = p[2];
     const float s1 = s0 + ck * dx;
     if (!(fabsf(s1) < L.sin_max) || !(fabsf(s0) < L.sin_max)) return false;
     const float q0 = (1.0f - s0) * (1.0f + s0), q1 = (1.0f - s1) * (1.0f + s1);
@@ -54,11 +64,11 @@ __device__ __forceinline__ bool transport(Fit& f, float x1, const Launch& L)
     }
     float dS = ch * ratio;
     if (dx < 0.0f) dS = -dS;
-    const float t = f.p[3];
-    const float a = dx * (2.0f * cc + ss * (s0 * ic0 + s1 * ic1)) * (icc * icc);
-    const float b = -L.kB * dx * dx * (cc + ss * s1 * ic1) * (icc * icc);
-    const float c = t * dx * ss * ic0 * ic1 * icc;
-    const float d = dS;
+    const float t = p[3];
+    J.a = dx * (2.0f * cc + ss * (s0 * ic0 + s1 * ic1)) * (icc * icc);
+    J.b = -L.kB * dx * dx * (cc + ss * s1 * ic1) * (icc * icc);
+    J.c = t * dx * ss * ic0 * ic1 * icc;
+    J.d = dS;
     const float dphi = ck * dS;
     const float u2 = dphi * dphi;
     float sinc2, rest;
@@ -71,14 +81,21 @@ __device__ __forceinline__ bool transport(Fit& f, float x1, const Launch& L)
         rest = __fdividef(sinf(dphi) - dphi, u2);
     }
     const float dSdC = dS * dS * (0.5f * s1 * ic1 * sinc2 + rest);
-    const float e = -L.kB * t * dSdC;
-    const float g = -L.kB * dx;
+    J.e = -L.kB * t * dSdC;
+    J.g = -L.kB * dx;
 
-    f.p[0] += dy;
-    f.p[1] += t * dS;
-    f.p[2] = s1;
-    f.x = x1;
+    p[0] += dy;
+    p[1] += t * dS;
+    p[2] = s1;
+    x = x1;
+    return true;
+}
 
+__device__ __forceinline__ bool transport(Fit& f, float x1, const Launch& L)
+{
+    Jac J;
+    if (!transport_state(f.x, f.p, x1, L, J)) return false;
+    const float a = J.a, b = J.b, c = J.c, d = J.d, e = J.e, g = J.g;
     float* C = f.C;
     const float C00 = C[0], C10 = C[1], C11 = C[2], C20 = C[3], C21 = C[4], C22 = C[5];
     const float C30 = C[6], C31 = C[7], C32 = C[8], C33 = C[9];
@@ -154,6 +171,138 @@ __device__ __forceinline__ void seed_cov(Fit& f, const Launch& L)
     f.C[CI(2, 2)] = L.seed_var_s * c2 * c2 * c2;
     f.C[CI(3, 3)] = L.seed_var_t * c2;
     f.C[CI(4, 4)] = L.seed_var_q;
+}
+
+// (S00, S01, S11) = C[0:2, 0:2] + V
+__device__ __forceinline__ void meas_cov(const Fit& f, const Launch& L, float& S00, float& S01,
+                                         float& S11)
+{
+    S00 = f.C[0] + L.sy2;
+    S01 = f.C[1];
+    S11 = f.C[2] + L.sz2;
+}
+
+__device__ __forceinline__ void cov_of(const Fit& f, float* C)
+{
+#pragma unroll
+    for (int i = 0; i < 15; ++i) C[i] = f.C[i];
+}
+
+// ---- square-root form (backward pass of the tracklet constructor) ----
+// The covariance is carried as a factor U with C = U U^T (5x5, row-major,
+// not triangular).  In binary32 this keeps about twice the significant
+// digits of C itself where the fit pins a parameter down by orders of
+// magnitude from its seed variance (the q/pT variance falls from 100 to
+// ~1e-2): the update C -= K C[0:2,:] cancels there, the factor form does
+// not.  Transport is U <- J U (rows 0..2 change).  The (y, z) measurement
+// is taken as two scalar updates (V is diagonal) in Potter's form: for the
+// measured component i, a = U^T e_i, alpha = a.a + v, w = U a (= C e_i),
+// p += w r / alpha, U <- U - gamma w a^T with gamma = 1 / (alpha +
+// sqrt(alpha v)); the chi2 increment is the sum of r^2 / alpha of the two
+// (equal to r^T S^-1 r of the joint update).
+struct FitSR {
+    float x;
+    float p[5];
+    float U[25];
+};
+
+__device__ __forceinline__ bool transport(FitSR& f, float x1, const Launch& L)
+{
+    Jac J;
+    if (!transport_state(f.x, f.p, x1, L, J)) return false;
+    float* U = f.U;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const float u2 = U[10 + j], u3 = U[15 + j], u4 = U[20 + j];
+        U[j] += J.a * u2 + J.b * u4;
+        U[5 + j] += J.c * u2 + J.d * u3 + J.e * u4;
+        U[10 + j] = u2 + J.g * u4;
+    }
+    return true;
+}
+
+// (S00, S01, S11) = C[0:2, 0:2] + V
+__device__ __forceinline__ void meas_cov(const FitSR& f, const Launch& L, float& S00,
+                                         float& S01, float& S11)
+{
+    const float* U = f.U;
+    float a = 0.0f, b = 0.0f, c = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        a += U[j] * U[j];
+        b += U[j] * U[5 + j];
+        c += U[5 + j] * U[5 + j];
+    }
+    S00 = a + L.sy2;
+    S01 = b;
+    S11 = c + L.sz2;
+}
+
+template <int I>
+__device__ __forceinline__ float update_sr_1(FitSR& f, float m, float v)
+{
+    float* U = f.U;
+    float a[5], w[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) a[j] = U[5 * I + j];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) s += U[5 * k + j] * a[j];
+        w[k] = s;  // w[I] = a.a = C_II
+    }
+    const float al = w[I] + v;
+    const float ial = __fdividef(1.0f, al);
+    const float r = m - f.p[I];
+    const float kr = r * ial;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f.p[k] += w[k] * kr;
+    const float q = v * ial;  // in (0, 1]
+    const float gam = __fdividef(ial, 1.0f + q * rsqrtf(q));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float gk = gam * w[k];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) U[5 * k + j] -= gk * a[j];
+    }
+    return r * kr;
+}
+
+// Kalman update with measurement (my, mz); returns the chi2 increment.
+__device__ __forceinline__ float update(FitSR& f, float my, float mz, const Launch& L)
+{
+    const float c0 = update_sr_1<0>(f, my, L.sy2);
+    return c0 + update_sr_1<1>(f, mz, L.sz2);
+}
+
+// Seed: U = diag of the seed standard deviations (the same seed covariance
+// as seed_cov).
+__device__ __forceinline__ void seed_cov(FitSR& f, const Launch& L)
+{
+    const float c2 = (1.0f - f.p[2]) * (1.0f + f.p[2]);
+    const float c1 = sqrtf(c2);
+#pragma unroll
+    for (int i = 0; i < 25; ++i) f.U[i] = 0.0f;
+    f.U[0] = L.sy;
+    f.U[6] = L.sz;
+    f.U[12] = L.seed_sd_s * c2 * c1;
+    f.U[18] = L.seed_sd_t * c1;
+    f.U[24] = L.seed_sd_q;
+}
+
+// C = U U^T, lower triangle
+__device__ __forceinline__ void cov_of(const FitSR& f, float* C)
+{
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int k = 0; k <= i; ++k) {
+            float s = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) s += f.U[5 * i + j] * f.U[5 * k + j];
+            C[CI(i, k)] = s;
+        }
 }
 
 }  // namespace

@@ -122,6 +122,7 @@ struct Launch {
     float sy2, sz2;              // measurement variances
     float slope_win_y, slope_win_z, d_max, chi2_hit, sin_max, edge_margin;
     float seed_var_s, seed_var_t, seed_var_q;
+    float sy, sz, seed_sd_s, seed_sd_t, seed_sd_q;  // square roots of the above
     int max_gap, min_chain, min_tracklet_hits, min_track_hits;
     // arena
     EventDesc* ev;              // [n_events]

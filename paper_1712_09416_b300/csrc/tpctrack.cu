@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
@@ -557,6 +558,11 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.seed_var_s = P.seed_var_s;
     L.seed_var_t = P.seed_var_t;
     L.seed_var_q = P.seed_var_q;
+    L.sy = std::fabs(P.meas_sigma_y);
+    L.sz = std::fabs(P.meas_sigma_z);
+    L.seed_sd_s = std::sqrt(P.seed_var_s);
+    L.seed_sd_t = std::sqrt(P.seed_var_t);
+    L.seed_sd_q = std::sqrt(P.seed_var_q);
     L.max_gap = P.max_gap;
     L.min_chain = P.min_chain;
     L.min_tracklet_hits = P.min_tracklet_hits;
