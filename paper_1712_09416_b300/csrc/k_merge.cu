@@ -88,6 +88,32 @@ __device__ __forceinline__ bool rotate(Fit& f, float cd, float sd, const Launch&
     return true;
 }
 
+// The same rotation on a square-root factor (C = U U^T): U <- J U.
+__device__ __forceinline__ bool rotate(FitSR& f, float cd, float sd, const Launch& L)
+{
+    const float s = f.p[2];
+    const float c = sqrtf((1.0f - s) * (1.0f + s));
+    const float s1 = s * cd - c * sd;
+    const float c1 = c * cd + s * sd;
+    if (!(c1 > 0.0f) || !(fabsf(s1) < L.sin_max)) return false;
+    const float ck = -L.kB * f.p[4];
+    const float j00 = c / c1, j10 = -f.p[3] * sd / c1, j20 = -ck * sd, j22 = c1 / c;
+    const float x1 = f.x * cd + f.p[0] * sd;
+    const float y1 = -f.x * sd + f.p[0] * cd;
+    f.x = x1;
+    f.p[0] = y1;
+    f.p[2] = s1;
+    float* U = f.U;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const float u0 = U[j];
+        U[j] = j00 * u0;
+        U[5 + j] = j10 * u0 + U[5 + j];
+        U[10 + j] = j20 * u0 + j22 * U[10 + j];
+    }
+    return true;
+}
+
 // r^T (C_f + C_b)^-1 r with r = p_f - p_b, by Cholesky; -1 if not positive definite
 __device__ __forceinline__ float match_chi2(const Fit& f, const Launch& L, int b)
 {
@@ -377,7 +403,10 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_refit(Launch L)
         if (m > T) continue;
         const MgState& O = L.mg_st[so];
         if (!O.ok) continue;
-        Fit f;
+        // square-root factor of the covariance, as in the tracklet
+        // constructor's backward pass (the refit restarts from the seed
+        // covariance, where the binary32 update of C itself cancels)
+        FitSR f;
         f.x = O.x;
 #pragma unroll
         for (int i = 0; i < 5; ++i) f.p[i] = O.p[i];
@@ -417,8 +446,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_refit(Launch L)
         F.x = f.x;
 #pragma unroll
         for (int i = 0; i < 5; ++i) F.p[i] = f.p[i];
-#pragma unroll
-        for (int i = 0; i < 15; ++i) F.C[i] = f.C[i];
+        cov_of(f, F.C);
         F.chi2 = chi2;
         F.ndf = 2 * nh - 5;
         F.nhits = nh;

@@ -10,8 +10,10 @@ and/or chosen covariance entries can be rounded to binary32, which separates
 the effect of binary32 *storage* from that of binary32 arithmetic.
 
 Used to show that some binary64-vs-binary32 differences of the fitted q/pT
-are a property of storing the covariance in binary32 (the tracker's design),
-not of the GPU arithmetic.  Shares no code with the CUDA path or the oracle.
+are a property of storing the covariance itself in binary32, and that
+storing a square-root factor U (C = U U^T) instead, as the tracker's
+backward pass does, removes them.  Shares no code with the CUDA path or the
+oracle.
 """
 import math
 
@@ -20,7 +22,7 @@ import numpy as np
 KAPPA = 0.299792458e-2
 
 
-def _transport(x0, x1, p, C, kB):
+def _transport_j(x0, x1, p, kB):
     dx = x1 - x0
     ck = -kB * p[4]
     s0 = p[2]
@@ -50,6 +52,11 @@ def _transport(x0, x1, p, C, kB):
     q[0] += dy
     q[1] += t * dS
     q[2] = s1
+    return q, J
+
+
+def _transport(x0, x1, p, C, kB):
+    q, J = _transport_j(x0, x1, p, kB)
     return q, J @ C @ J.T
 
 
@@ -65,12 +72,25 @@ def _seed_cov(s, vy, vz, var_s, var_t, var_q):
     return np.diag([vy, vz, var_s * c2 ** 3, var_t * c2, var_q])
 
 
+def _factor_update(p, U, i, m, v):
+    """Scalar measurement of component i in Potter's square-root form:
+    a = U^T e_i, alpha = a.a + v, p += U a r / alpha,
+    U <- U - U a a^T / (alpha + sqrt(alpha v))."""
+    a = U[i].copy()
+    alpha = a @ a + v
+    w = U @ a
+    r = m - p[i]
+    return p + w * (r / alpha), U - np.outer(w, a) / (alpha + math.sqrt(alpha * v))
+
+
 def fit_known_hits(row_x, hy, hz, rowhit, r0, rk, *, bz=0.5, sigma=0.1, seed_var=(1.0, 1.0, 100.0),
-                   round_state=False, round_cov=None):
+                   round_state=False, round_cov=None, backward_factor=False):
     """State at the innermost hit of a tracklet with hit rowhit[r] (cluster
     index or -1) on row r, start row r0 and chain end row rk.  round_cov is a
     5x5 boolean mask of covariance entries rounded to binary32 after every
-    step (None: none); round_state rounds the 5-vector likewise."""
+    step (None: none); round_state rounds the 5-vector likewise.  With
+    backward_factor the backward pass carries a square-root factor U of the
+    covariance (C = U U^T) instead, and round_cov rounds entries of U."""
     kB = KAPPA * bz
     vy = vz = sigma * sigma
     xr = np.asarray(row_x, np.float64)
@@ -97,6 +117,21 @@ def fit_known_hits(row_x, hy, hz, rowhit, r0, rk, *, bz=0.5, sigma=0.1, seed_var
         if rowhit[r] >= 0:
             p, C = _update(p, C, Y[rowhit[r]] - yref, Z[rowhit[r]] - zref, vy, vz)
             p, C = rp(p), rc(C)
+    if backward_factor:
+        U = rc(np.sqrt(_seed_cov(p[2], vy, vz, *seed_var)))
+        x = xr[last]
+        for r in range(last, first - 1, -1):
+            if r != last:
+                p, J = _transport_j(x, xr[r], p, kB)
+                p, U, x = rp(p), rc(J @ U), xr[r]
+            if rowhit[r] >= 0:
+                p, U = _factor_update(p, U, 0, Y[rowhit[r]] - yref, vy)
+                p, U = _factor_update(p, U, 1, Z[rowhit[r]] - zref, vz)
+                p, U = rp(p), rc(U)
+        out = p.copy()
+        out[0] += yref
+        out[1] += zref
+        return out
     C = rc(_seed_cov(p[2], vy, vz, *seed_var))
     p, C = _update(p, C, Y[rowhit[last]] - yref, Z[rowhit[last]] - zref, vy, vz)
     p, C, x = rp(p), rc(C), xr[last]

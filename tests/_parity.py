@@ -20,19 +20,14 @@ Bars (the tracker computes in binary32, the oracle in binary64):
 * parameters at the innermost hit: |dy|, |dz| <= 1e-3 cm; |d sin phi|,
   |d tan lambda| <= 1e-4 (relative to values of order one); q/pT within
   1e-4 relative to max(|q/pT|, 2 (GeV/c)^-1): stiff tracks have |q/pT| near
-  0, where the binary32 fit keeps an absolute error near 1e-4 (under 1% of
-  the statistical error of q/pT).  Budget: at most 0.1% of the compared
-  tracks (rounded up) may exceed these bars, each by at most 3x or else by
-  less than 1e-2 of the oracle's own standard error on every parameter,
-  scaled by sqrt(chi2/ndf) when the oracle's fit has chi2 above ndf (a
-  short track measures q/pT poorly: on the pile-up event an 18-hit tracklet
-  with the oracle's hits differs by 3.7x the q/pT bar, 1.3e-3 of its
-  standard error).  For short,
-  curved tracks the y / sin(phi) block of the covariance is nearly singular
-  and storing it in binary32 alone (exact arithmetic otherwise) moves q/pT
-  past 1e-4 relative (tests/test_fp32_covariance_limit.py); measured in
-  units of each parameter's own statistical error the binary32 deviations
-  stay below 1e-2.  The share of tracks within the plain bars (q/pT 1e-4
+  0, where a purely relative bar has no meaning.  Every compared tracklet
+  and track stays within these bars (no budget).  This holds because the
+  tracker's backward pass carries a square-root factor of the covariance:
+  storing the covariance itself in binary32 moves q/pT of short, curved
+  tracks past the bar (tests/test_fp32_covariance_limit.py), and with the
+  standard update the worst tracklet of the pile-up event sat at 8x to 67x
+  the q/pT bar depending only on how the compiler contracted its binary32
+  arithmetic.  The share of tracks within the plain bars (q/pT 1e-4
   relative with no floor) is reported beside these;
 * tracks: identical hit lists and order for every track whose tracklet
   shares no hit with a tracklet that differs.
@@ -43,9 +38,6 @@ TOL_YZ = 1e-3
 TOL_ANG = 1e-4
 TOL_QPT_REL = 1e-4
 QPT_FLOOR = 2.0
-PARAM_BUDGET_FRAC = 1e-3  # share of compared tracks allowed above the bars
-PARAM_BUDGET_MAX = 3.0    # ... by at most this factor
-PARAM_SIGMA_MAX = 1e-2    # ... or by less than this share of the oracle's standard error
 DIAG = (0, 2, 5, 9, 14)   # variances in the 15-entry lower triangle
 
 
@@ -77,22 +69,15 @@ def sigma_errors(gp, op, oC, chi2=None, ndf=None):
     return d / sd
 
 
-def check_param_bars(scaled, what="tracks", sig=None):
+def check_param_bars(scaled, what="tracks"):
     """Assert the parameter bars on an (n, 5) array of param_errors scales:
-    every row within 1, except at most ceil(0.1% of n) rows, each within 3
-    or (given sig, the sigma_errors of the same rows) below 1e-2 of the
-    oracle's standard error on every parameter."""
+    every row within 1."""
     s = np.asarray(scaled, np.float64).reshape(-1, 5)
     if len(s) == 0:
         return
     worst = s.max(axis=1)
     over = np.nonzero(worst > 1.0)[0]
-    allowed = int(np.ceil(PARAM_BUDGET_FRAC * len(s)))
-    assert len(over) <= allowed, (what, len(over), allowed, s[over].max(axis=0))
-    big = worst > PARAM_BUDGET_MAX
-    if sig is not None:
-        big &= np.asarray(sig, np.float64).reshape(-1, 5).max(axis=1) >= PARAM_SIGMA_MAX
-    assert not big.any(), (what, s.max(axis=0))
+    assert len(over) == 0, (what, len(over), s.max(axis=0))
 
 
 def plain_within(gp, op):
@@ -263,7 +248,7 @@ def check_tracklets(rep, max_diff_frac=1e-3):
         (len(rep["flagged_diff"]), rep["n_oracle"])
     assert rep["valid_mismatch"] == [], rep["valid_mismatch"][:10]
     assert rep["hitset_mismatch"] == [], rep["hitset_mismatch"][:10]
-    check_param_bars(rep["param_scaled"], "tracklets", rep["param_sig"])
+    check_param_bars(rep["param_scaled"], "tracklets")
 
 
 def tainted_hits(ot):

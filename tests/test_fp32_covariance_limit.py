@@ -1,21 +1,23 @@
-"""Why the parameter bar carries a small budget (binary32 covariance storage).
+"""Why the backward pass carries a square-root factor of the covariance.
 
-The tracker keeps the 5x5 covariance in binary32 registers.  For short,
-strongly curved tracks the y / sin(phi) block of the covariance is nearly
-singular, and rounding var(y), cov(y, sin phi) and var(sin phi) to binary32
-after each step moves the fitted q/pT by more than 1e-4 relative.  This test
-re-runs one such tracklet of the pile-up event (sector 20) with float64
-arithmetic throughout and rounds only what is stored:
+Storing the 5x5 covariance itself in binary32 is not enough: for short,
+strongly curved tracks the y / sin(phi) block is nearly singular, and
+rounding var(y), cov(y, sin phi) and var(sin phi) to binary32 after each
+step moves the fitted q/pT by more than 1e-4 relative.  This test re-runs
+one such tracklet of the pile-up event (sector 20) with float64 arithmetic
+throughout and rounds only what is stored:
 
 * no rounding reproduces the oracle to 1e-8 of the bars (the emulation is
-  the oracle's algorithm);
+  the oracle's algorithm), and so does the backward pass in Potter's
+  square-root form (C = U U^T, two scalar updates per hit);
 * rounding the 5-vector alone keeps q/pT within 5% of its bar;
 * rounding the covariance alone (exact arithmetic otherwise) already moves
-  q/pT beyond its bar.
+  q/pT beyond its bar;
+* rounding everything the tracker stores (forward covariance, backward
+  factor U, state) keeps q/pT within 5% of its bar.
 
-So the few tracks above the bar are a property of binary32 covariance
-storage, not of the GPU arithmetic; the parity tests allow them (at most
-0.1% of the compared tracks, each within 3x the bars).
+So the tracker's backward pass carries U, not C (the forward pass, whose
+state only seeds the backward one, keeps C).
 """
 import numpy as np
 import pytest
@@ -64,3 +66,14 @@ def test_binary32_covariance_storage_exceeds_the_qpt_bar(case):
         m[i, j] = True
     s_block = _qpt_scaled(*case, round_cov=m)
     assert s_block[4] > 1.0, s_block
+
+
+def test_factor_form_reproduces_the_oracle(case):
+    s = _qpt_scaled(*case, backward_factor=True)
+    assert s.max() < 1e-6, s
+
+
+def test_binary32_factor_storage_stays_within_the_bar(case):
+    s = _qpt_scaled(*case, round_cov=np.ones((5, 5), bool), round_state=True,
+                    backward_factor=True)
+    assert s.max() < 0.05, s

@@ -84,7 +84,7 @@ def check_merged(tp, t, tr, ev, orc, *, o=None, max_diff_frac=2e-3, what="merged
     assert len(rep["missing"]) + len(rep["extra"]) <= max_diff_frac * n, \
         (len(rep["missing"]), len(rep["extra"]), rep["missing"][:3], rep["extra"][:3])
     assert rep["order_ok"]
-    _parity.check_param_bars(rep["param_scaled"], what, rep["param_sig"])
+    _parity.check_param_bars(rep["param_scaled"], what)
     merged = sum(len(s) > 1 for s in m["sources"])
     assert counters["n_sector_tracks"] == o["n_tracks"]
     assert abs(counters["n_merge_chains"] - merged) <= max_diff_frac * n + 2

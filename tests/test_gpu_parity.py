@@ -58,7 +58,7 @@ def check_event(tp, trk, ev, orc, *, o=None, max_diff_frac=1e-3, what="event"):
     assert trep["missing"] == [] and trep["extra"] == [], (trep["missing"][:3], trep["extra"][:3])
     assert trep["order_ok"]
     assert "meta_mismatch" not in trep
-    _parity.check_param_bars(trep["param_scaled"], "tracks", trep["param_sig"])
+    _parity.check_param_bars(trep["param_scaled"], "tracks")
     c = g["counters"]
     assert abs(c["n_links"] - o["n_links"]) <= n_link_diff
     assert c["n_starts"] == len(g["starts"])
@@ -160,7 +160,7 @@ def test_batched_launch_against_the_oracle(tp, orc):
             trep = _parity.compare_tracks(trs[k], o, rep["taint"])
             assert trep["missing"] == [] and trep["extra"] == [], k
             assert trep["order_ok"] and "meta_mismatch" not in trep, k
-            _parity.check_param_bars(trep["param_scaled"], f"batch event {k}", trep["param_sig"])
+            _parity.check_param_bars(trep["param_scaled"], f"batch event {k}")
             assert trep["compared_share"] >= 0.95 or trep["n_oracle"] < 100, (k, trep["compared_share"])
             print(f"batch event {k}: {ev.n} clusters, {trep['n_oracle']} tracks, compared "
                   f"{trep['compared_share']:.4f}, plain bars {trep['plain_share']:.4f}")
