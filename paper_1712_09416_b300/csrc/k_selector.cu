@@ -28,42 +28,54 @@ namespace {
 
 constexpr unsigned long long kNone = ~0ULL;
 
-// one warp per tracklet, lanes over its rows
+// Two parts in one kernel.  One thread per tracklet slot: the tracklet
+// range of every sector (slots are ordered by sector because start hits
+// are; the sector comes from the chain record), and the "no track" result
+// of every slot without a valid tracklet.  One warp per valid tracklet
+// (those of the backward pass's list), lanes over its rows: owned hits,
+// decision, sort key.  The two parts write disjoint slots.
 __global__ void k_sel_decide(Launch L)
 {
     if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int n_st = min(L.cnt->n_starts, L.t_cap);
+    const int n_list = min(L.cnt->n_bwd, L.t_cap);
     const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_st; t += warps) {
-        const TrackletHdr& H = L.tl[t];
-        const int gs = L.hrow[H.start] >> 8;
-        if (lane == 0) {
-            if (t == 0 || (L.hrow[L.tl[t - 1].start] >> 8) != gs) L.sec_first[gs] = t;
-            if (t == n_st - 1 || (L.hrow[L.tl[t + 1].start] >> 8) != gs) L.sec_end[gs] = t + 1;
+    const int threads = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_st; t += threads) {
+        const int gs = L.tl_chain[t].y >> 8;
+        if (t == 0 || (L.tl_chain[t - 1].y >> 8) != gs) L.sec_first[gs] = t;
+        if (t == n_st - 1 || (L.tl_chain[t + 1].y >> 8) != gs) L.sec_end[gs] = t + 1;
+        if (!L.tl[t].valid) {
+            L.tl_key[t] = kNone;
+            L.tl_nown[t] = 0;
+            L.tl_out[t] = -1;
         }
+    }
+    const int warps = threads >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_list; i += warps) {
+        const int t = L.tl_list[i];
+        const TrackletHdr& H = L.tl[t];
+        if (!H.valid) continue;
         unsigned long long out = kNone;
         int nown = 0;
-        if (H.chain_len >= L.min_chain && H.valid) {
-            const unsigned long long key = ((unsigned long long)H.nhits << 32) |
-                                           (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
-            const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
-            int first_own = -1;
-            for (int r0 = H.first; r0 <= H.last; r0 += 32) {
-                const int r = r0 + lane;
-                bool own = false;
-                if (r <= H.last) {
-                    const int h = rowhit[r];
-                    own = h >= 0 && L.weight[h] == key;
-                }
-                const unsigned b = __ballot_sync(0xffffffffu, own);
-                if (lane == 0) L.tl_own[(size_t)t * kOwnWords + (r0 - H.first) / 32] = b;
-                if (b && first_own < 0) first_own = r0 + __ffs(b) - 1;
-                nown += __popc(b);
+        const unsigned long long key = ((unsigned long long)H.nhits << 32) |
+                                       (unsigned long long)(0xFFFFFFFFu - (unsigned)L.hcid[H.start]);
+        const int* rowhit = L.tl_rowhit + (size_t)t * L.R;
+        int first_own = -1;
+        for (int r0 = H.first; r0 <= H.last; r0 += 32) {
+            const int r = r0 + lane;
+            bool own = false;
+            if (r <= H.last) {
+                const int h = rowhit[r];
+                own = h >= 0 && L.weight[h] == key;
             }
-            if (nown >= L.min_track_hits && 2 * nown >= H.nhits)
-                out = ((unsigned long long)first_own << 32) | (unsigned long long)(unsigned)L.hcid[H.start];
+            const unsigned b = __ballot_sync(0xffffffffu, own);
+            if (lane == 0) L.tl_own[(size_t)t * kOwnWords + (r0 - H.first) / 32] = b;
+            if (b && first_own < 0) first_own = r0 + __ffs(b) - 1;
+            nown += __popc(b);
         }
+        if (nown >= L.min_track_hits && 2 * nown >= H.nhits)
+            out = ((unsigned long long)first_own << 32) | (unsigned long long)(unsigned)L.hcid[H.start];
         if (lane == 0) {
             L.tl_key[t] = out;
             L.tl_nown[t] = nown;
