@@ -38,7 +38,8 @@ __global__ void k_sel_decide(Launch L)
 {
     if (L.cnt->timeout) return;  // an earlier bounded wait gave up
     const int n_st = min(L.cnt->n_starts, L.t_cap);
-    const int n_list = min(L.cnt->n_bwd, L.t_cap);
+    const int n_long = L.cnt->n_bwd;
+    const int n_list = min(n_long + L.cnt->n_bwd_short, L.t_cap);
     const int lane = threadIdx.x & 31;
     const int threads = gridDim.x * blockDim.x;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_st; t += threads) {
@@ -53,7 +54,7 @@ __global__ void k_sel_decide(Launch L)
     }
     const int warps = threads >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_list; i += warps) {
-        const int t = L.tl_list[i];
+        const int t = list_at(L, i, n_long);
         const TrackletHdr& H = L.tl[t];
         if (!H.valid) continue;
         unsigned long long out = kNone;

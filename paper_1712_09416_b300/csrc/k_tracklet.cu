@@ -253,7 +253,10 @@ __global__ void __launch_bounds__(kTlThreads, PASS == 1 ? TPC_TL_MINB1 : TPC_TL_
 #define BEST(i) best_s[i][threadIdx.x]
 #define PL(i) pl_s[i][threadIdx.x]
     // PASS 1 takes every chain, PASS 2 the chains k_dominance listed
-    const int n_st = min(PASS == 1 ? L.cnt->n_starts : L.cnt->n_bwd, L.t_cap);
+    // PASS 1 takes the chains in start-list order (handed out inner-first
+    // they kept more lanes busy but ran slower), PASS 2 longest-first
+    const int n_long = L.cnt->n_bwd;
+    const int n_st = min(PASS == 1 ? L.cnt->n_starts : n_long + L.cnt->n_bwd_short, L.t_cap);
     const int lane = threadIdx.x & 31;
     int t = -1;
     int phase = 0;  // 1 forward, 2 backward
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(kTlThreads, PASS == 1 ? TPC_TL_MINB1 : TPC_TL_
                     t = -1;
                     exhausted = true;
                 } else if (PASS == 2) {
-                    t = L.tl_list[t];
+                    t = list_at(L, t, n_long);
                 }
             }
         }
@@ -516,6 +519,10 @@ __global__ void __launch_bounds__(kTlThreads, PASS == 1 ? TPC_TL_MINB1 : TPC_TL_
     }
 }
 
+// Chains whose forward range (last assigned row - start row) spans at least
+// this many rows are handed to the backward pass first.
+constexpr int kBwdLongRows = 64;
+
 // Dominance: one thread per chain.  A chain long enough for a tracklet all
 // of whose hits were taken by forward extension searches (of other
 // tracklets: a tracklet's own extension starts above its chain) gets no
@@ -533,7 +540,7 @@ __global__ void k_dominance(Launch L)
     // whole warps step together (ballot below)
     for (int t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n_st; t0 += stride) {
         const int t = t0 + lane;
-        bool keep = false;
+        bool keep = false, longr = false;
         if (t < n_st) {
             const int4 ch = L.tl_chain[t];
             const int r0 = ch.y & 255, rk = ch.w;
@@ -547,7 +554,9 @@ __global__ void k_dominance(Launch L)
                     for (int j = 0; j < 4; ++j)
                         if (h[j] >= 0 && !L.mark[h[j]]) keep = true;
                 }
-                if (!keep) {
+                if (keep) {
+                    longr = L.tl[t].last - r0 >= kBwdLongRows;
+                } else {
                     TrackletHdr& H = L.tl[t];
                     H.dominated = 1;
                     H.valid = 0;
@@ -559,13 +568,19 @@ __global__ void k_dominance(Launch L)
                 }
             }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            int b = 0;
-            if (lane == leader) b = atomicAdd(&L.cnt->n_bwd, __popc(m));
-            b = __shfl_sync(0xffffffffu, b, leader);
-            if (keep) L.tl_list[b + __popc(m & ((1u << lane) - 1))] = t;
+        const unsigned ml = __ballot_sync(0xffffffffu, keep && longr);
+        const unsigned ms = __ballot_sync(0xffffffffu, keep && !longr);
+        if (ml | ms) {
+            int bl = 0, bs = 0;
+            if (lane == 0) {
+                if (ml) bl = atomicAdd(&L.cnt->n_bwd, __popc(ml));
+                if (ms) bs = atomicAdd(&L.cnt->n_bwd_short, __popc(ms));
+            }
+            bl = __shfl_sync(0xffffffffu, bl, 0);
+            bs = __shfl_sync(0xffffffffu, bs, 0);
+            const unsigned below = (1u << lane) - 1;
+            if (keep && longr) L.tl_list[bl + __popc(ml & below)] = t;
+            if (keep && !longr) L.tl_list[L.t_cap - 1 - (bs + __popc(ms & below))] = t;
         }
     }
     // block totals

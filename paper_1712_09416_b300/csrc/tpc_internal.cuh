@@ -79,7 +79,8 @@ struct Counters {
     int tl_next;          // work counters of the persistent constructor passes
     int tl_next2;
     int n_dominated;      // chains whose tracklet is not built (dominated)
-    int n_bwd;            // chains listed for the backward pass
+    int n_bwd;            // chains listed for the backward pass: long forward ranges
+    int n_bwd_short;      // ... and short ones (listed from the back of tl_list)
     int n_chain_hits;     // hits on the chains of all start hits
     int n_big_rows;       // rows above kSmallRowHits hits (listed for the large row sort)
     int n_mid_rows;       // rows for the block row sort of k_rowsort
@@ -89,7 +90,7 @@ struct Counters {
     int n_mg_tracks;      // merger: tracks after merging
     int max_row_hits;     // high-water marks: hits of the fullest (sector, row)
     int max_sector_tracks;  // ... and emitted tracks of the fullest sector
-    int pad[3];
+    int pad[2];
 };
 
 // Merger scratch: a sector track's outer state, and the refit of a chain
@@ -148,7 +149,8 @@ struct Launch {
     TrackletHdr* tl;            // [t_cap]
     int4* tl_chain;             // [t_cap] start hit, its sector << 8 | row, chain end hit, end row
     int* tl_rowhit;             // [t_cap * R] global hit index or -1
-    int* tl_list;               // [t_cap] chains listed for the backward pass
+    int* tl_list;               // [t_cap] work order of the backward pass: long chains from
+                                // the front, short ones from the back (list_at)
     unsigned long long* tl_key; // [t_cap] sector-local sort key or ~0
     int* tl_nown;               // [t_cap]
     unsigned* tl_own;           // [t_cap * kOwnWords] owned-row bits, 32 rows per word from first
@@ -295,6 +297,15 @@ __device__ __forceinline__ int bin_z(const RowGrid& G, float z)
 {
     const int b = (int)floorf((z - G.z0) * G.idz);
     return min(max(b, 0), G.nz - 1);
+}
+
+// Position i of the backward pass's work order in tl_list (written by
+// k_dominance): the n_long chains with long forward ranges first (from the
+// front), then the others (from the back); a longest-first hand-out keeps
+// fewer lanes idle at the end of the persistent pass.
+__device__ __forceinline__ int list_at(const Launch& L, int i, int n_long)
+{
+    return i < n_long ? L.tl_list[i] : L.tl_list[L.t_cap - 1 - (i - n_long)];
 }
 
 // Profiling hook: called on the host right after each kernel is enqueued.
