@@ -13,8 +13,8 @@
 //   k_scatter  moves every cluster to row offset + rank
 //   k_rowsort  counting sort of each row by bin in shared memory, cid order
 //              inside a bin; writes the sorted hits and the bin offsets (and
-//              clears the hit weights for the fit).  Rows of up to 256 hits
-//              (most rows of peripheral events) take one warp each, with no
+//              clears the hit weights for the fit).  Rows of up to 384 hits
+//              (most rows of central and peripheral events) take one warp each, with no
 //              block barriers; rows of up to 1024 hits, listed by k_rowscan,
 //              one block each, taken in turn from the list by the same
 //              blocks first; larger rows are sorted by k_rowsort_big with
@@ -35,7 +35,9 @@ constexpr int kEvSmem = 1024;
 // Row sorts: rows of up to kWarpRowHits hits take one warp, rows of up to
 // kSmallRowHits one block of k_rowsort, larger rows one block of
 // k_rowsort_big.
-constexpr int kWarpRowHits = 256;
+// (384: most pad rows of a central event take a warp; rows of up to 512 or
+// only 256 hits per warp were slower on the B300)
+constexpr int kWarpRowHits = 384;
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kWsHist = kWarpRowHits * kBinsPerHitX2 / 2 + 4;  // >= nb + 1, keeps 16-byte regions
@@ -444,7 +446,7 @@ __device__ void sort_row_warp(const Launch& L, int g, int base, int n, unsigned 
 __global__ void __launch_bounds__(kRsThreads) k_rowsort(Launch L)
 {
     if (L.cnt->timeout) return;  // an earlier bounded wait gave up
-    __shared__ __align__(16) unsigned char smem[kRowsortSmem];
+    extern __shared__ __align__(16) unsigned char smem[];  // kRowsortSmem bytes
     __shared__ int item_s;
     const int n_mid = min(L.cnt->n_mid_rows, L.RS);
     for (;;) {
@@ -503,7 +505,9 @@ int g_big_per_sm[2][2] = {{1, 1}, {1, 1}};  // k_rowsort_big<mid, max> x (256, 5
 
 void prepare_binning()
 {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_rowsort_per_sm, k_rowsort, kRsThreads, 0);
+    cudaFuncSetAttribute(k_rowsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsortSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_rowsort_per_sm, k_rowsort, kRsThreads,
+                                                  kRowsortSmem);
     if (g_rowsort_per_sm < 1) g_rowsort_per_sm = 1;
     cudaFuncSetAttribute(k_rowsort_big<kMidRowHits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sort_smem(kMidRowHits));
@@ -535,7 +539,7 @@ void launch_binning(const Launch& L, const Schedule& S, void* stream_, const Ker
         long long rb = (long long)S.n_sm * g_rowsort_per_sm;
         if (rb > L.RS) rb = L.RS;
         if (rb < 1) rb = 1;
-        k_rowsort<<<(int)rb, kRsThreads, 0, stream>>>(L);
+        k_rowsort<<<(int)rb, kRsThreads, kRowsortSmem, stream>>>(L);
         hook_after(hook, "k_rowsort");
     }
     // the rows above kSmallRowHits hits, listed by k_rowscan (every block

@@ -1,7 +1,7 @@
 """Row-sort tiers against the oracle's neighbour links.
 
 The hits of a pad row are sorted by y-z bin and cid by one warp when the row
-holds up to 256 hits, by one block up to 1024 hits (both in k_rowsort), and by
+holds up to 384 hits, by one block up to 1024 hits (both in k_rowsort), and by
 k_rowsort_big up to 2048 and up to 4096 hits.  One sector here carries rows
 whose hit counts sit on and around every boundary (and an empty row and a
 one-hit row), with straight tracks through the rest so that links exist.
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 # pad row -> hits on it (tracks included)
 COUNTS = {10: 257, 13: 256, 16: 1, 19: 0, 22: 1023, 25: 1024, 28: 1025, 31: 2047, 34: 2048,
-          37: 2049, 40: 3000, 43: 4096}
+          37: 2049, 40: 3000, 43: 4096, 46: 384, 49: 385}
 N_TRACKS = 60
 SKIP = {16, 19}  # rows the tracks do not cross
 
@@ -77,6 +77,6 @@ def test_row_sort_tiers_give_the_oracles_links(orc):
     assert np.all(o["c2_tie"][diff] != 0)
     assert len(diff) <= 1e-3 * n_links
     # every boundary row has links to and from it (its sort was used)
-    for r in (10, 13, 25, 28, 34, 37, 40, 43):
+    for r in (10, 13, 25, 28, 34, 37, 40, 43, 46, 49):
         on = ev.row == r
         assert np.sum(up[on] >= 0) >= N_TRACKS // 2, r
