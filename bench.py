@@ -1119,11 +1119,27 @@ def run_ours(args):
         tp.tpc_track_destroy(ctx_s)
         h2d = 12 * n + 4096
         d2h = 256 + n_tr * (4 + 4 + 20 + 60 + 4 + 4 + 4) + 4 * n_hits + 4 * 37
+        # the host->device link: pinned copies of the bytes of eight events,
+        # best of five; the served figure cannot exceed link / 12 B per cluster
+        hbuf = torch.empty(8 * 12 * n, dtype=torch.uint8).pin_memory()
+        dbuf = torch.empty(8 * 12 * n, dtype=torch.uint8, device="cuda")
+        link = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dbuf.copy_(hbuf, non_blocking=True)
+            torch.cuda.synchronize()
+            link.append(hbuf.numel() / (time.perf_counter() - t0) / 1e9)
+        del hbuf, dbuf
+        h2d_gbs = max(link)
         e2e = {"value": world * n * k_e2e / srv_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k_e2e,
                "api": f"tpc_track_submit/poll, {SERVED_SLOTS} slots x {SERVED_PER_LAUNCH} events, "
                       "pinned host inputs, results read from pinned buffers",
                "runs_clusters_per_s": [world * n * k_e2e / x for x in srv_runs],
+               "h2d_link_gbs": h2d_gbs,
+               "link_bound_clusters_per_s": world * h2d_gbs * 1e9 / 12.0,
+               "frac_of_link_bound": (world * n * k_e2e / srv_s) / (world * h2d_gbs * 1e9 / 12.0),
                "one_event_calls": {"value": world * n * k_e2e / seq_s, "unit": UNIT,
                                    "api": "tpc_track_event, one call per event"}}
 

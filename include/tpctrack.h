@@ -463,7 +463,7 @@ int tpc_track_debug_dump_event(tpc_track_ctx* ctx, int stage, int event, void* h
  *   params    slope windows and d_max are used
  *   up_cid, dn_cid  device arrays of ev->n int32 each, written by the call
  *   cuda_stream     stream for the work (NULL = legacy default stream)
- * Scratch memory is a static device array of this library, about 10.7 MB,
+ * Scratch memory is a static device array of this library, about 11.2 MB,
  * held on every device that loads the library until the process exits.  No
  * context, cudaMalloc or cudaFree is involved.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress, with that

@@ -264,8 +264,7 @@ __global__ void k_scatter(Launch L)
 #pragma unroll
         for (int k = 0; k < kBinIlp; ++k) {
             if (pos[k] < 0) continue;
-            L.tmp_yz[pos[k]] = make_float2(y[k], z[k]);
-            L.tmp_cid[pos[k]] = cid[k];
+            L.tmp_rec[pos[k]] = make_float4(y[k], z[k], __int_as_float(cid[k]), 0.0f);
         }
     }
 }
@@ -292,7 +291,8 @@ __device__ __forceinline__ void write_row(const Launch& L, int base, int n, int 
 {
     for (int p = t0; p < n; p += dt) {
         const int i = order[p];
-        L.hyz[base + p] = L.tmp_yz[base + i];
+        const float4 c = L.tmp_rec[base + i];
+        L.hyz[base + p] = make_float2(c.x, c.y);
         L.hcid[base + p] = cid[i];
         L.hrow[base + p] = hrow;
         L.weight[base + p] = 0ULL;
@@ -342,8 +342,9 @@ __device__ void sort_row_block(const Launch& L, int g, unsigned char* smem)
     if (n > CAP) {
         if (threadIdx.x == 0) atomicExch(&L.cnt->ovf_row, 1);
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            L.hyz[base + p] = L.tmp_yz[base + p];
-            L.hcid[base + p] = L.tmp_cid[base + p];
+            const float4 c = L.tmp_rec[base + p];
+            L.hyz[base + p] = make_float2(c.x, c.y);
+            L.hcid[base + p] = __float_as_int(c.z);
             L.hrow[base + p] = hrow;
             L.weight[base + p] = 0ULL;
             if (L.mark) L.mark[base + p] = 0;
@@ -354,10 +355,10 @@ __device__ void sort_row_block(const Launch& L, int g, unsigned char* smem)
     for (int b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float2 c = L.tmp_yz[base + i];
+        const float4 c = L.tmp_rec[base + i];
         const int b = bin_z(G, c.y) * G.ny + bin_y(G, c.x);
         sbin[i] = (int16_t)b;
-        scid[i] = L.tmp_cid[base + i];
+        scid[i] = __float_as_int(c.z);
         sslot[i] = (int16_t)atomicAdd(&hist[b], 1);
     }
     __syncthreads();
@@ -401,10 +402,10 @@ __device__ void sort_row_warp(const Launch& L, int g, int base, int n, unsigned 
     for (int b = lane; b <= nb; b += 32) hist[b] = 0;
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
-        const float2 c = L.tmp_yz[base + i];
+        const float4 c = L.tmp_rec[base + i];
         const int b = bin_z(G, c.y) * G.ny + bin_y(G, c.x);
         sbin[i] = (int16_t)b;
-        scid[i] = L.tmp_cid[base + i];
+        scid[i] = __float_as_int(c.z);
         sslot[i] = (int16_t)atomicAdd(&hist[b], 1);
     }
     __syncwarp();

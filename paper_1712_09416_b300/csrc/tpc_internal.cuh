@@ -137,7 +137,7 @@ struct Launch {
     unsigned long long* tile_state;  // look-back states (rows | hits | sectors)
     int n_row_tiles, n_hit_tiles;
     int* rank;                  // [n_total] arrival rank of a cluster in its row
-    float2* tmp_yz; int* tmp_cid;   // row-scattered (y, z)
+    float4* tmp_rec;            // row-scattered (y, z, cid bits, unused): one 16-byte store each
     float2* hyz; int* hcid; int* hrow; // sorted (y, z), cid, sector << 8 | row
     int* bin_start;
     int16_t* up; int16_t* dn; int16_t* upc; int16_t* dnc;

@@ -41,7 +41,7 @@ constexpr size_t kNaZero = up256(up256(sizeof(Counters)) + 4 * (kNaRS * kCntPad 
                                  8 * (kNaRowTiles + kNaHitTiles + kNaMaxSectors) + 1024);
 constexpr size_t kNaBytes =
     kNaDesc + kNaZero + up256(4 * (kNaRS + 1)) + up256(4 * kNaRS) + up256(sizeof(RowGrid) * kNaRS) +
-    up256(4 * kNaBins) + 8 * up256(4 * kNaMaxClusters) /* tmp yz cid rank, hyz hcid hrow */ +
+    up256(4 * kNaBins) + 9 * up256(4 * kNaMaxClusters) /* tmp rec (4), rank, hyz (2), hcid, hrow */ +
     2 * up256(4 * kNaMaxClusters) /* up dn */ + 2 * up256(4 * kNaMaxClusters) /* upc dnc */ +
     up256(4 * kNaMaxClusters) /* upg */ + up256(8 * kNaMaxClusters) /* weight */ +
     up256(4 * kNaMaxClusters) /* starts */ + up256(4 * kNaMaxClusters) /* crowded */;
@@ -180,8 +180,7 @@ extern "C" int tpc_track_links_noalloc(const tpc_clusters* ev, const tpc_geometr
     L.big_rows = (int*)take(4 * kNaRS);
     L.grid = (RowGrid*)take(sizeof(RowGrid) * kNaRS);
     L.bin_start = (int*)take(4 * kNaBins);
-    L.tmp_yz = (float2*)take(8 * kNaMaxClusters);
-    L.tmp_cid = (int*)take(4 * kNaMaxClusters);
+    L.tmp_rec = (float4*)take(16 * kNaMaxClusters);
     L.rank = (int*)take(4 * kNaMaxClusters);
     L.hyz = (float2*)take(8 * kNaMaxClusters);
     L.hcid = (int*)take(4 * kNaMaxClusters);

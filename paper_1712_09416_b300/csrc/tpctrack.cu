@@ -88,8 +88,8 @@ struct Slot {
     size_t zero_cap = 0;
     int *row_off, *big_rows;
     RowGrid* grid;
-    float2* tmp_yz;
-    int *tmp_cid, *rank;
+    float4* tmp_rec;
+    int* rank;
     float2* hyz;
     int *hcid, *hrow, *bin_start;
     int16_t *up, *dn, *upc, *dnc;
@@ -269,8 +269,7 @@ size_t layout(Slot& s, char* base)
     s.row_off = (int*)take(4 * (k.rs + 1));
     s.big_rows = (int*)take(4 * k.rs);
     s.grid = (RowGrid*)take(sizeof(RowGrid) * k.rs);
-    s.tmp_yz = (float2*)take(8 * k.n);
-    s.tmp_cid = (int*)take(4 * k.n);
+    s.tmp_rec = (float4*)take(16 * k.n);
     s.rank = (int*)take(4 * k.n);
     s.hyz = (float2*)take(8 * k.n);
     s.hcid = (int*)take(4 * k.n);
@@ -611,8 +610,7 @@ int enqueue(tpc_track_ctx* ctx, Slot& s, int n_ev, const tpc_clusters* ev, const
     L.row_off = s.row_off;
     L.big_rows = s.big_rows;
     L.grid = s.grid;
-    L.tmp_yz = s.tmp_yz;
-    L.tmp_cid = s.tmp_cid;
+    L.tmp_rec = s.tmp_rec;
     L.rank = s.rank;
     L.hyz = s.hyz;
     L.hcid = s.hcid;
