@@ -288,7 +288,7 @@ def percentile(v, q):
     return v[k]
 
 
-SERVED_SLOTS, SERVED_PER_LAUNCH = 3, 2
+SERVED_SLOTS, SERVED_PER_LAUNCH = 4, 2
 
 
 def served_ctx(tp, host_events, geom, bz, n_per_event, sizes=None):
