@@ -1086,7 +1086,9 @@ def run_ours(args):
     hc, hkeep = tp.clusters_of(*pinned)
     e2e = None
     if not args.no_e2e:
-        k_e2e = max(8, min(args.steps, 40))
+        # bursts of at least 40 events: the served pipeline (4 slots x 2 events)
+        # fills and drains once per burst
+        k_e2e = max(40, min(args.steps, 80))
         # (a) one event per call (tpc_track_event): copies, launch and result
         # read strictly one after the other
         ctx_h = tp.tpc_track_create(n + 65536, max_events_per_launch=1)
