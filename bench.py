@@ -1014,10 +1014,10 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     for _ in range(n_streams):  # status of the last step of every slot
         tp.tpc_track_results(ctx, epl, copy=False)
-    # hold: the same steps for about a second more (untimed), so that the
-    # clock record covers the load even when the timed region is shorter
-    # than nvidia-smi's 200 ms sampling period
-    t_hold = time.perf_counter() + 1.0
+    # hold: the same steps for about three seconds more (untimed), so that
+    # the clock record has a dozen samples under the same load even when the
+    # timed region is shorter than a few of nvidia-smi's 200 ms periods
+    t_hold = time.perf_counter() + 3.0
     i = 0
     while time.perf_counter() < t_hold:
         for _ in range(16):
