@@ -5,8 +5,10 @@ Workload: the central heavy-ion-like event (10,000 primary helices plus 1,000
 secondaries plus 5% noise, 36 sectors x 159 pad rows, 0.5 T, seed 2, about
 1.73M binary32 clusters).  One step = the whole tracking path (binning,
 neighbours, cleaning, start hits, tracklet construction, selection) over one
-such event, inputs resident in HBM.  Eight device copies of the event are used
-in turn so that the inputs of consecutive steps (168 MB) exceed the 126 MB L2.
+launch of E such events side by side (E picked from 1-16 by a timed burst),
+inputs resident in HBM.  Sixteen device copies of the event are used in turn,
+so that the events of one launch are distinct and the inputs of consecutive
+steps exceed the 126 MB L2.
 
 Also measured: the same metric end to end through the C ABI with pinned host
 buffers (host->device copy of the clusters and device->host copy of the
@@ -40,7 +42,7 @@ METRIC = "clusters/s & central-event p50/p99 latency, served vs one-event, 1 B30
 UNIT = "clusters/s"
 WORKLOAD = ("central event: 10,000 primaries + 1,000 secondaries + 5% noise, 36 sectors x "
             "159 rows (85-247 cm), |z| < 250 cm, 0.5 T, seed 2")
-N_COPIES = 8
+N_COPIES = 16
 
 
 def log(*a):
@@ -115,7 +117,7 @@ KERNEL_BYTES = {"k_count": 12, "k_rowscan": 4, "k_scatter": 24, "k_rowsort": 0,
                 "k_constructor_bwd": 8.7 * F_A, "k_weights": 8 + 16 * F_A,
                 "k_sel_decide": 12 * F_A, "k_sel_sort": 0.7, "k_sel_write": 4 * F_A}
 ROOFLINE_TARGET = 0.40  # share of the HBM roofline asked of the path
-EPL_CANDIDATES = (1, 2, 4, 8)  # central events per launch tried for the timed step
+EPL_CANDIDATES = (1, 2, 4, 8, 16)  # central events per launch tried for the timed step
 
 
 def stage_bytes_per_cluster(kernel: str) -> float:

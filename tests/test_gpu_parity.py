@@ -117,6 +117,22 @@ def test_central_event_whole(tp, orc):
     assert (trep["maha"] > MERGE_TIE_M).sum() <= np.ceil(1e-3 * len(trep["maha"]))
 
 
+def test_eight_central_events_in_one_launch_equal_one_alone(tp):
+    """The benchmark's timed step: eight copies of the central event side by
+    side in one launch (13.9M clusters).  Every event's tracks equal the
+    event tracked alone, bit for bit (compared with the oracle in
+    test_central_event_whole)."""
+    ev = synth.central_event()
+    with tp.Tracker(8 * ev.n + 65536, max_events_per_launch=8) as t:
+        alone = t.event(ev)
+        outs = t.batch([ev] * 8)
+        assert t.counters()["n_clusters"] == 8 * ev.n
+    assert len(outs) == 8
+    for b in outs:
+        for f in ("sector", "x", "param", "cov", "chi2", "ndf", "hit_off", "hit_cid"):
+            assert np.array_equal(getattr(alone, f), getattr(b, f)), f
+
+
 def test_pileup_event_whole(tp, orc):
     """Pile-up stress event (50 collisions, vertex z within +-200 cm, about
     7.4M clusters) in one launch, every stage and every track against the
